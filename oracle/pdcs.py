@@ -1,0 +1,320 @@
+"""Oracle PDCS solver: Algorithm 2 wrapped around Algorithm 1 of the paper, step by
+step, in plain FP64 (test infrastructure only; slow on purpose; recomputes
+G x and G^T y from their definitions at every use).
+
+Paper passages followed (section / equation / algorithm):
+  * one PDHG step, eq. PDHG (Sec. 1.2);
+  * AdaptiveStepPDHG, Function 1 and eq. adaptive_step_size (Sec. 2.1);
+  * reflection parameter, eq. adaptive_reflection with maxErr, eq. tolerance (Sec. 2.2);
+  * reflected Halpern step and weighted average, Algorithm 1 (Sec. 2);
+  * normalized duality gap rho^N, Definition 2.1, and its bisection, Algorithm 3,
+    eqs. compute_rho / compute_zt_2 (Sec. 2.4);
+  * restart candidate and the three restart conditions, KKT_omega fallback (Sec. 2.3);
+  * primal weight initialisation / update / reset (Sec. 2.5);
+  * rescaling and unscaling, Algorithm 2 (Sec. 2.6);
+  * termination, eq. PDCS_terminate_tolerance_rel (Sec. 3.2.3), exit codes Table 1.
+
+Readings where the paper is silent or inconsistent (listed in the design notes):
+  c3  kbar is incremented at the start of every attempt (accepted or rejected)
+      before the step-size formula uses (kbar + 1).
+  c4  eta_bar = +inf when (Delta y)^T G (Delta x) = 0.
+  c5  the average is over the Halpern iterates z^{t,i}, weights eta^{t,i}.
+  c6  method 'average' compares both candidates; 'halpern' always takes z.
+  c7  restart / termination checks every check_freq accepted iterations (global
+      count); beta needs maxErr(zhat) every iteration.
+  c8  in the first restart period there is no reference gap: only condition 3.
+  c9  bisection: t0 = r / sqrt(tau ||b1||^2 + sigma ||b2||^2) (the unconstrained
+      step reaching radius r), at most 64 doublings, bisection until
+      t_right - t_left <= 1e-6 t_right (at most 64 halvings); the value is
+      returned at the last probe; r = 0 or b = 0 give 0.
+  c10 if any gap value used at a check is negative, every gap at that check is
+      replaced by KKT_omega.
+  c11 beta / maxErr / KKT_omega / rho^N use the rescaled problem; termination
+      uses the unscaled problem with infinity norms.
+  c15 the candidate is tested for termination and returned.
+  ref the reference gap of a restart period is the candidate's gap at the check
+      that started the period; N uses the last accepted step size.
+"""
+import time
+
+import numpy as np
+
+from .cones import proj_box, proj_cone_product
+from .kkt import scaled_errors, unscaled_errors, kkt_omega
+from .problem import ScaledProblem, apply_block_T
+
+EXIT_OPTIMAL, EXIT_MAX_ITER, EXIT_TIME_LIMIT, EXIT_NUMERICAL = 0, 1, 6, 8
+
+
+class Options:
+    """Solver options; names follow the paper's direct API (Sec. 3.2.3)."""
+
+    def __init__(self, **kw):
+        self.rel_tol = 1e-6
+        self.abs_tol = 1e-6
+        self.require_abs = False
+        self.time_limit = 1000.0
+        self.max_iter = 1 << 62
+        self.use_preconditioner = True
+        self.ruiz_iters = 10
+        self.pc_alpha = 1.0
+        self.method = "average"
+        self.use_adaptive_restart = True
+        self.check_freq = 64
+        self.bisect_rel_tol = 1e-6
+        for k, v in kw.items():
+            if not hasattr(self, k):
+                raise KeyError(k)
+            setattr(self, k, v)
+
+
+class Oracle:
+    """State and steps of Algorithm 1 on a ScaledProblem."""
+
+    def __init__(self, prob, opts=None):
+        self.opts = opts or Options()
+        o = self.opts
+        self.sp = ScaledProblem(prob, o.use_preconditioner, o.ruiz_iters, o.pc_alpha)
+        sp_ = self.sp
+        # Sec. 2.5 InitializePrimalWeight on the rescaled data.
+        nc = np.linalg.norm(sp_.c)
+        nh = np.linalg.norm(sp_.h)
+        self.omega0 = nc / nh if (nc > 1e-10 and nh > 1e-10) else 1.0
+        # Algorithm 1 Require: eta_hat = 1 / ||G||_inf (reading c2: max |entry|).
+        gmax = np.max(np.abs(sp_.G.data)) if sp_.G.nnz else 1.0
+        self.eta0 = 1.0 / gmax
+
+    # -- projections onto X = [lhat, uhat] x D2^{-1} K_p and Y = (D1 K_r)^* ----
+    def proj_X(self, v):
+        sp_ = self.sp
+        out = np.empty_like(v)
+        out[:sp_.nb] = proj_box(v[:sp_.nb], sp_.lo, sp_.hi)
+        out[sp_.nb:] = proj_cone_product(v[sp_.nb:], sp_.col_cones, 1.0 / sp_.d2[sp_.nb:])
+        return out
+
+    def proj_Y(self, v):
+        sp_ = self.sp
+        return proj_cone_product(v, sp_.row_cones, 1.0 / sp_.d1, dual=True)
+
+    # -- eq. PDHG ---------------------------------------------------------------
+    def one_pdhg(self, x, y, tau, sigma):
+        sp_ = self.sp
+        xh = self.proj_X(x - tau * (sp_.c - sp_.GT @ y))
+        yh = self.proj_Y(y + sigma * (sp_.h - sp_.G @ (2.0 * xh - x)))
+        return xh, yh
+
+    # -- Function 1 ----------------------------------------------------------
+    def adaptive_step(self, x, y, omega, eta, kbar):
+        sp_ = self.sp
+        while True:
+            kbar += 1                                                # reading c3
+            xh, yh = self.one_pdhg(x, y, eta / omega, eta * omega)
+            dx = xh - x
+            dy = yh - y
+            inter = abs(float(dy @ (sp_.G @ dx)))
+            num = 0.5 * (omega * float(dx @ dx) + float(dy @ dy) / omega)
+            eta_bar = num / inter if inter > 0 else np.inf           # reading c4
+            eta_p = min((1.0 - (kbar + 1) ** -0.3) * eta_bar, (1.0 + (kbar + 1) ** -0.6) * eta)
+            if eta < eta_bar:
+                return xh, yh, eta, eta_p, kbar
+            eta = eta_p
+
+    # -- eq. adaptive_reflection ----------------------------------------------
+    @staticmethod
+    def reflection(max_err):
+        if max_err <= 0:
+            return 1.0
+        return float(min(1.0, max(0.0, -0.1 * np.log10(max_err) + 0.2)))
+
+    # -- Definition 2.1 / Algorithm 3 ------------------------------------------
+    def normalized_gap(self, x, y, r, tau, sigma):
+        sp_ = self.sp
+        if r <= 0:
+            return 0.0
+        b1 = sp_.GT @ y - sp_.c
+        b2 = sp_.h - sp_.G @ x
+        scale = np.sqrt(tau * float(b1 @ b1) + sigma * float(b2 @ b2))
+        if scale <= 0:
+            return 0.0
+
+        def z_of(t):
+            return self.proj_X(x + t * tau * b1), self.proj_Y(y + t * sigma * b2)
+
+        def dist(xt, yt):
+            return np.sqrt(float((xt - x) @ (xt - x)) / tau + float((yt - y) @ (yt - y)) / sigma)
+
+        t = r / scale
+        t_left, t_right = 0.0, t
+        for k in range(64):
+            xt, yt = z_of(t)
+            if dist(xt, yt) > r:
+                if k == 0:
+                    t_left, t_right = 0.0, t
+                else:
+                    t_left, t_right = 0.5 * t, t
+                break
+            t = 2.0 * t
+            t_left, t_right = 0.5 * t, t
+        for _ in range(64):
+            if t_right - t_left <= self.opts.bisect_rel_tol * t_right:
+                break
+            t_mid = 0.5 * (t_left + t_right)
+            xt, yt = z_of(t_mid)
+            if dist(xt, yt) < r:
+                t_left = t_mid
+            else:
+                t_right = t_mid
+        return (float(b1 @ (xt - x)) + float(b2 @ (yt - y))) / r
+
+    @staticmethod
+    def n_norm(dx, dy, tau, sigma):
+        return float(np.sqrt(float(dx @ dx) / tau + float(dy @ dy) / sigma))
+
+    # -- Algorithm 1 / 2 --------------------------------------------------------
+    def solve(self, x0=None, y0=None, trace=None, snapshots=None):
+        """Run the solver.  trace: list to append one dict per accepted iteration.
+        snapshots: dict {iteration: None} filled with copies of the scaled
+        Halpern iterate (x, y) after that many accepted iterations."""
+        o = self.opts
+        sp_ = self.sp
+        t_start = time.perf_counter()
+        # Warm start given in the original variables: undo the RSOC rotation
+        # (an involution) and the rescaling (Algorithm 2).
+        x = np.zeros(sp_.n) if x0 is None else apply_block_T(np.asarray(x0, float), sp_.col_T) / sp_.d2
+        y = np.zeros(sp_.m) if y0 is None else apply_block_T(np.asarray(y0, float), sp_.row_T) / sp_.d1
+        xa, ya = x.copy(), y.copy()            # anchor z^{t,0}
+        omega = self.omega0
+        eta_hat = self.eta0
+        kbar = 0
+        it = 0                                  # accepted iterations, all periods
+        t_period = 0
+        k = 0
+        wsum = 0.0
+        xs = np.zeros(sp_.n)
+        ys = np.zeros(sp_.m)
+        rho_ref = None                          # (rho, errs) of the anchor
+        prev = None                             # (rho, errs) of previous candidate
+        restarts = 0
+        xc, yc = x.copy(), y.copy()
+        exit_code = None
+        eta = eta_hat
+        while True:
+            xh, yh, eta, eta_hat, kbar = self.adaptive_step(x, y, omega, eta_hat, kbar)
+            errh = scaled_errors(sp_, xh, yh)
+            beta = self.reflection(errh["max_err"])
+            a = (k + 1.0) / (k + 2.0)
+            x = a * ((1.0 + beta) * xh - beta * x) + xa / (k + 2.0)
+            y = a * ((1.0 + beta) * yh - beta * y) + ya / (k + 2.0)
+            wsum += eta
+            xs += eta * x
+            ys += eta * y
+            k += 1
+            it += 1
+            rec = dict(iter=it, kbar=kbar, period=t_period, eta=eta, eta_hat=eta_hat, beta=beta,
+                       omega=omega, max_err=errh["max_err"], check=0, cand_avg=-1,
+                       restart=0, rho_c=np.nan)
+            if it % o.check_freq == 0:
+                rec["check"] = 1
+                tau, sigma = eta / omega, eta * omega
+                xbar, ybar = xs / wsum, ys / wsum
+                r_h = self.n_norm(x - xa, y - ya, tau, sigma)
+                rho_h = self.normalized_gap(x, y, r_h, tau, sigma)
+                err_h = scaled_errors(sp_, x, y)
+                if o.method == "average":
+                    r_a = self.n_norm(xbar - xa, ybar - ya, tau, sigma)
+                    rho_a = self.normalized_gap(xbar, ybar, r_a, tau, sigma)
+                    err_a = scaled_errors(sp_, xbar, ybar)
+                else:
+                    rho_a, err_a = np.inf, None
+                used = [rho_h] + ([rho_a] if o.method == "average" else [])
+                if rho_ref is not None:
+                    used.append(rho_ref[0])
+                if prev is not None:
+                    used.append(prev[0])
+                fallback = any(v < 0 for v in used)                  # reading c10
+                if fallback:
+                    m_h = kkt_omega(err_h, omega)
+                    m_a = kkt_omega(err_a, omega) if err_a is not None else np.inf
+                else:
+                    m_h, m_a = rho_h, rho_a
+                if m_h <= m_a:
+                    xc, yc, rho_c, err_c, cand_avg = x.copy(), y.copy(), rho_h, err_h, 0
+                    val_c = m_h
+                else:
+                    xc, yc, rho_c, err_c, cand_avg = xbar, ybar, rho_a, err_a, 1
+                    val_c = m_a
+                rec["cand_avg"] = cand_avg
+                rec["rho_c"] = val_c
+                ue = unscaled_errors(sp_, xc, yc)
+                done = ue["max_rel"] <= o.rel_tol and (not o.require_abs or max(
+                    ue["abs_p"], ue["abs_d"], ue["abs_gap"]) <= o.abs_tol)
+                if done:
+                    exit_code = EXIT_OPTIMAL
+                elif not np.isfinite(ue["max_rel"]):
+                    exit_code = EXIT_NUMERICAL
+                if exit_code is None:
+                    do_restart = False
+                    if o.use_adaptive_restart:
+                        cond3 = k >= 0.223 * kbar
+                        if rho_ref is None:
+                            do_restart = cond3                        # reading c8
+                        else:
+                            ref = kkt_omega(rho_ref[1], omega) if fallback else rho_ref[0]
+                            pv = None
+                            if prev is not None:
+                                pv = kkt_omega(prev[1], omega) if fallback else prev[0]
+                            cond1 = val_c <= 0.4 * ref
+                            cond2 = (pv is not None) and val_c <= 0.8 * ref and val_c > pv
+                            do_restart = cond1 or cond2 or cond3
+                    if do_restart:
+                        rec["restart"] = 1
+                        dx = np.linalg.norm(xc - xa)
+                        dy = np.linalg.norm(yc - ya)
+                        if dx > 1e-10 and dy > 1e-10:
+                            omega = float(np.exp(0.5 * np.log(dy / dx) + 0.5 * np.log(omega)))
+                        if omega > 1e5 or omega < 1e-5:
+                            omega = self.omega0
+                        rho_ref = (rho_c, err_c)
+                        prev = None
+                        xa, ya = xc.copy(), yc.copy()
+                        x, y = xc.copy(), yc.copy()
+                        k = 0
+                        wsum = 0.0
+                        xs[:] = 0.0
+                        ys[:] = 0.0
+                        t_period += 1
+                        restarts += 1
+                    else:
+                        prev = (rho_c, err_c)
+            if trace is not None:
+                trace.append(rec)
+            if snapshots is not None and it in snapshots:
+                snapshots[it] = (x.copy(), y.copy())
+            if exit_code is not None:
+                break
+            if it >= o.max_iter:
+                exit_code = EXIT_MAX_ITER
+                break
+            if time.perf_counter() - t_start > o.time_limit:
+                exit_code = EXIT_TIME_LIMIT
+                break
+        if exit_code != EXIT_OPTIMAL:
+            # Return the most recent candidate; before the first check, z itself.
+            if it < o.check_freq:
+                xc, yc = x.copy(), y.copy()
+        ue = unscaled_errors(sp_, xc, yc)
+        xo = apply_block_T(ue["x"], sp_.col_T)
+        yo = apply_block_T(ue["y"], sp_.row_T)
+        prob = sp_.orig
+        s = prob.G @ xo - prob.h
+        return dict(exit_code=exit_code, x=xo, y=yo, s=s, pobj=ue["pobj"], dobj=ue["dobj"],
+                    err_rel_p=ue["rel_p"], err_rel_d=ue["rel_d"], err_rel_gap=ue["rel_gap"],
+                    err_abs_p=ue["abs_p"], err_abs_d=ue["abs_d"], err_abs_gap=ue["abs_gap"],
+                    iters=it, attempts=kbar, restarts=restarts,
+                    solve_time_s=time.perf_counter() - t_start,
+                    x_scaled=x, y_scaled=y, omega=omega, eta_hat=eta_hat)
+
+
+def solve(prob, x0=None, y0=None, trace=None, snapshots=None, **opts):
+    """Convenience wrapper: Oracle(prob, Options(**opts)).solve(...)."""
+    return Oracle(prob, Options(**opts)).solve(x0, y0, trace, snapshots)
