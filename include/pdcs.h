@@ -1,0 +1,222 @@
+/*
+ * pdcs.h -- C ABI of a restarted-PDHG conic solver for one NVIDIA B300 (sm_103a).
+ *
+ * Problem (PDCS technical note, Sec. 1.1, eq. prob_cp):
+ *     min  c^T x   s.t.   G x - h  in  K_r,   l <= x[0:nb] <= u,   x[nb:n] in K_p
+ * K_r (written K_d^* in the paper; the cone G x - h belongs to) and K_p are
+ * ordered products of blocks from pdcs_cone_type.  The dual variable y lies in
+ * the dual cone K_r^* (eq. dual_conic).
+ *
+ * Method: Algorithm 2 (diagonal rescaling, Sec. 2.6) around Algorithm 1 (restarted
+ * PDHG with the adaptive step of Function 1, the adaptive reflected Halpern
+ * iteration of Sec. 2.2, weighted averaging, the normalized-duality-gap restarts
+ * of Sec. 2.3 computed by the bisection of Algorithm 3, and the primal-weight
+ * rule of Sec. 2.5).  Termination uses the relative infinity-norm KKT errors of
+ * Sec. 3.2.3 (eq. PDCS_terminate_tolerance_rel); exit codes follow Table 1.
+ *
+ * Every step after the host-to-device copy runs in this library's CUDA kernels on
+ * the device that is current when pdcs_setup is called.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PDCS_OK (0) or a negative pdcs_error.  Solver outcomes are
+ *     reported in pdcs_result.exit_code, never in the return value.
+ *   - pdcs_last_error() returns a NUL-terminated message for the calling
+ *     thread's most recent failure (valid until the next call from that thread).
+ *   - Array arguments may be host or device pointers (cudaMemcpyDefault
+ *     semantics); device arrays must live on the handle's device.
+ *   - Inputs are copied: the caller may free or reuse them after the call.
+ *   - Indices are 0-based; CSR column indices must be strictly increasing
+ *     within each row.
+ */
+#ifndef PDCS_H
+#define PDCS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Cone block types (Sec. 1.1 list of blocks; Sec. 3.2.3 row ordering).
+ *   ZERO      {0}^d
+ *   NONNEG    R_+^d
+ *   SOC       {(t, w) : ||w||_2 <= t}, dim >= 1 (head first)
+ *   RSOC      {(p, q, w) : 2 p q >= ||w||^2, p, q >= 0}, dim >= 2; handled by the
+ *             orthogonal reformulation ((p+q)/sqrt2, (p-q)/sqrt2, w) -> SOC (Sec. 3)
+ *   EXP       cl{(x, y, z) : y > 0, y exp(x / y) <= z}, dim == 3
+ *   DUAL_EXP  cl{(u, v, w) : u < 0, -u exp(v / u) <= e w}, dim == 3            */
+typedef enum {
+  PDCS_CONE_ZERO = 0,
+  PDCS_CONE_NONNEG = 1,
+  PDCS_CONE_SOC = 2,
+  PDCS_CONE_RSOC = 3,
+  PDCS_CONE_EXP = 4,
+  PDCS_CONE_DUAL_EXP = 5
+} pdcs_cone_type;
+
+typedef struct {
+  int32_t type; /* pdcs_cone_type */
+  int32_t pad;
+  int64_t dim;
+} pdcs_cone;
+
+typedef enum {
+  PDCS_OK = 0,
+  PDCS_ERR_INVALID = -1,  /* bad argument: sizes, cone dims, CSR structure, NaN data */
+  PDCS_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+  PDCS_ERR_NOMEM = -3,    /* device allocation failed */
+  PDCS_ERR_TIMEOUT = -4,  /* a bounded device-side wait gave up */
+  PDCS_ERR_UNSUPPORTED = -5
+} pdcs_error;
+
+/* Exit codes of Table 1. */
+typedef enum {
+  PDCS_EXIT_OPTIMAL = 0,
+  PDCS_EXIT_MAX_ITER = 1,
+  PDCS_EXIT_PRIMAL_INFEASIBLE_LOW_ACC = 2,
+  PDCS_EXIT_PRIMAL_INFEASIBLE_HIGH_ACC = 3,
+  PDCS_EXIT_DUAL_INFEASIBLE_LOW_ACC = 4,
+  PDCS_EXIT_DUAL_INFEASIBLE_HIGH_ACC = 5,
+  PDCS_EXIT_TIME_LIMIT = 6,
+  PDCS_EXIT_CONTINUE = 7,
+  PDCS_EXIT_NUMERICAL_ERROR = 8
+} pdcs_exit_code;
+
+/* Options; names and defaults follow the direct API of Sec. 3.2.3 where the
+ * paper gives them.  Extra fields are this library's. */
+typedef struct {
+  double rel_tol;            /* 1e-6: max relative inf-norm KKT error to stop */
+  double abs_tol;            /* 1e-6: used only when require_abs != 0 */
+  double time_limit;         /* 1000 s (wall clock, checked between check periods) */
+  int64_t max_iter;          /* accepted PDHG iterations; default INT64_MAX */
+  int32_t use_preconditioner;/* 1: Ruiz + Pock-Chambolle rescaling (Sec. 2.6) */
+  int32_t ruiz_iters;        /* 10 */
+  double pc_alpha;           /* 1.0; negative skips the Pock-Chambolle pass */
+  int32_t method;            /* 0 = average (compare both candidates), 1 = halpern */
+  int32_t use_adaptive_restart; /* 1 */
+  int64_t check_freq;        /* restart / termination check period: 64 */
+  int32_t precision;         /* 0 = FP64 throughout, 1 = FP32 bulk with FP64
+                                residuals, decisions, averages and exp Newton */
+  int32_t require_abs;       /* 0: relative criterion only; 1: also abs_tol */
+  double bisect_rel_tol;     /* 1e-6: Algorithm 3 stops when t_r - t_l <= tol * t_r */
+  int32_t verbose;           /* 0 silent, 1 one line per check period on stderr */
+  int32_t trace_capacity;    /* >0: record one trace row per accepted iteration */
+} pdcs_options;
+
+typedef struct {
+  int32_t exit_code;  /* pdcs_exit_code */
+  int32_t pad;
+  double pobj, dobj;  /* c^T x and the dual objective of eq. dual_conic */
+  double err_rel_p, err_rel_d, err_rel_gap;  /* eq. PDCS_terminate_tolerance_rel */
+  double err_abs_p, err_abs_d, err_abs_gap;  /* eq. PDCS_terminate_tolerance_abs */
+  double solve_time_s;   /* wall time of the call (setup excluded) */
+  int64_t iters;         /* accepted PDHG iterations */
+  int64_t attempts;      /* all PDHG attempts (kbar), rejected ones included */
+  int64_t restarts;
+} pdcs_result;
+
+typedef struct pdcs_handle pdcs_handle;
+
+/* Fill *opt with the defaults listed above. */
+void pdcs_default_options(pdcs_options* opt);
+
+/* Build a solver for one problem (Algorithm 2, line 1: rescaled instance data).
+ *   out        receives the handle (NULL on failure).
+ *   m, n       rows and columns of G (m >= 0, n >= 1).
+ *   row_ptr    int64[m+1], col_idx int32[nnz], val float64[nnz]: CSR of G.
+ *   h          float64[m];  c float64[n].
+ *   nb         leading box-bounded columns (0 <= nb <= n).
+ *   lb, ub     float64[nb] bounds (+-INFINITY allowed; lb <= ub); may be NULL
+ *              when nb == 0.
+ *   row_cones  n_row_cones blocks in order; their dims must sum to m.
+ *   col_cones  n_col_cones blocks for x[nb:n]; dims must sum to n - nb.
+ *   opt        options (NULL = defaults); copied.
+ *   cuda_stream  caller's cudaStream_t (may be NULL).  The handle runs its
+ *              kernels and graphs on a stream of its own; each call first makes
+ *              that stream wait for work already queued on cuda_stream, and
+ *              returns only after its own work has finished.
+ * Errors: PDCS_ERR_INVALID for inconsistent sizes, unsorted or out-of-range
+ * column indices, non-finite G/h/c entries, lb > ub, bad cone dims;
+ * PDCS_ERR_NOMEM / PDCS_ERR_CUDA for device failures.  The handle owns all
+ * device memory it allocates. */
+int pdcs_setup(pdcs_handle** out, int64_t m, int64_t n, const int64_t* row_ptr,
+               const int32_t* col_idx, const double* val, const double* h, const double* c,
+               int64_t nb, const double* lb, const double* ub, const pdcs_cone* row_cones,
+               int64_t n_row_cones, const pdcs_cone* col_cones, int64_t n_col_cones,
+               const pdcs_options* opt, void* cuda_stream);
+
+/* Run Algorithm 2 (Algorithm 1 on the rescaled problem, then unscale).
+ *   x0 (n), y0 (m): optional warm start in the original variables (NULL = 0).
+ *   x (n), y (m), s (m): caller-owned outputs (host or device; any may be NULL):
+ *       primal x, dual y and slack s = G x - h of the returned point.
+ *   res: summary (may be NULL).
+ * Each call starts a fresh solve from (x0, y0). */
+int pdcs_solve(pdcs_handle* handle, const double* x0, const double* y0, double* x, double* y,
+               double* s, pdcs_result* res);
+
+/* Complete solver state (checkpoint / resume; the loop variables of Algorithm 1).
+ * Vectors that accompany it are in the solver's scaled, RSOC-reformulated
+ * variables, float64: x, y = current Halpern iterate z^{t,k}; x0, y0 = anchor
+ * z^{t,0}; xs, ys = running sums sum_i eta^{t,i} z^{t,i} of the weighted average. */
+typedef struct {
+  int64_t iter;      /* accepted iterations so far (all periods) */
+  int64_t kbar;      /* attempts so far (accepted and rejected) */
+  int64_t k;         /* accepted iterations in the current restart period */
+  int64_t period;    /* restart period index t */
+  int64_t restarts;
+  double eta_hat;    /* step size of the next attempt */
+  double eta_last;   /* accepted step of the last iteration */
+  double omega;      /* primal weight */
+  double wsum;       /* sum of accepted steps in the current period */
+  int32_t has_ref;   /* a reference gap exists (t > 0) */
+  int32_t has_prev;  /* a previous candidate of this period exists */
+  double ref_rho, ref_abs_p, ref_abs_d, ref_abs_gap;     /* anchor's gap and 2-norm errors */
+  double prev_rho, prev_abs_p, prev_abs_d, prev_abs_gap; /* previous candidate's */
+} pdcs_state;
+
+/* Copy the state left by the last pdcs_solve / pdcs_resume / pdcs_set_state.
+ * Any vector pointer may be NULL; lengths n, m, n, m, n, m; host or device. */
+int pdcs_get_state(pdcs_handle* handle, pdcs_state* state, double* x, double* y, double* x0,
+                   double* y0, double* xs, double* ys);
+
+/* Replace the solver state (all six vectors are required).  G x, G^T y and the
+ * anchor's products are recomputed from the vectors.  Errors: PDCS_ERR_INVALID
+ * for NULL arguments, a non-positive step size or primal weight, negative
+ * counters. */
+int pdcs_set_state(pdcs_handle* handle, const pdcs_state* state, const double* x,
+                   const double* y, const double* x0, const double* y0, const double* xs,
+                   const double* ys);
+
+/* Continue Algorithm 1 from the current state until termination, the time
+ * limit, or max_iter total accepted iterations (max_iter <= 0: the option's
+ * value).  Outputs as in pdcs_solve. */
+int pdcs_resume(pdcs_handle* handle, int64_t max_iter, double* x, double* y, double* s,
+                pdcs_result* res);
+
+/* Copy an internal iterate, in the solver's scaled and RSOC-reformulated
+ * variables, to caller memory (host or device, float64).
+ *   which: 0 = current Halpern iterate z^{t,k}, 1 = anchor z^{t,0},
+ *          2 = last PDHG point zhat, 3 = scaling vectors (x <- D2, y <- D1). */
+int pdcs_get_iterate(pdcs_handle* handle, int32_t which, double* x, double* y);
+
+/* Copy up to cap trace rows (PDCS_TRACE_FIELDS doubles each, one per accepted
+ * iteration, row i = iteration i + 1) to host memory; *count receives the
+ * number of rows available.  Fields: iter, kbar, period, eta, eta_hat, beta,
+ * omega, max_err, check, cand_avg, restart, rho_c. */
+#define PDCS_TRACE_FIELDS 12
+int pdcs_get_trace(pdcs_handle* handle, double* out, int64_t cap, int64_t* count);
+
+/* Sizes after set-up (m, n of the reformulated problem, nnz of G). */
+int pdcs_get_sizes(pdcs_handle* handle, int64_t* m, int64_t* n, int64_t* nnz);
+
+/* Release the handle and its device memory.  NULL-safe. */
+void pdcs_free(pdcs_handle* handle);
+
+/* Message for the calling thread's most recent failure. */
+const char* pdcs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDCS_H */

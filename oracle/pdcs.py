@@ -171,10 +171,12 @@ class Oracle:
         return float(np.sqrt(float(dx @ dx) / tau + float(dy @ dy) / sigma))
 
     # -- Algorithm 1 / 2 --------------------------------------------------------
-    def solve(self, x0=None, y0=None, trace=None, snapshots=None):
+    def solve(self, x0=None, y0=None, trace=None, snapshots=None, states=None):
         """Run the solver.  trace: list to append one dict per accepted iteration.
         snapshots: dict {iteration: None} filled with copies of the scaled
-        Halpern iterate (x, y) after that many accepted iterations."""
+        Halpern iterate (x, y) after that many accepted iterations.
+        states: dict {iteration: None} filled with the complete solver state
+        after that many accepted iterations (0 = before the first one)."""
         o = self.opts
         sp_ = self.sp
         t_start = time.perf_counter()
@@ -198,6 +200,20 @@ class Oracle:
         xc, yc = x.copy(), y.copy()
         exit_code = None
         eta = eta_hat
+
+        def capture():
+            return dict(x=x.copy(), y=y.copy(), x0=xa.copy(), y0=ya.copy(), xs=xs.copy(),
+                        ys=ys.copy(), wsum=wsum, k=k, kbar=kbar, iter=it, period=t_period,
+                        restarts=restarts, eta_hat=eta_hat, eta=eta, omega=omega,
+                        has_ref=rho_ref is not None,
+                        ref=(rho_ref[0], rho_ref[1]["abs_p"], rho_ref[1]["abs_d"],
+                             rho_ref[1]["abs_gap"]) if rho_ref is not None else (0.0,) * 4,
+                        has_prev=prev is not None,
+                        prev=(prev[0], prev[1]["abs_p"], prev[1]["abs_d"], prev[1]["abs_gap"])
+                        if prev is not None else (0.0,) * 4)
+
+        if states is not None and 0 in states:
+            states[0] = capture()
         while True:
             xh, yh, eta, eta_hat, kbar = self.adaptive_step(x, y, omega, eta_hat, kbar)
             errh = scaled_errors(sp_, xh, yh)
@@ -290,6 +306,8 @@ class Oracle:
                 trace.append(rec)
             if snapshots is not None and it in snapshots:
                 snapshots[it] = (x.copy(), y.copy())
+            if states is not None and it in states:
+                states[it] = capture()
             if exit_code is not None:
                 break
             if it >= o.max_iter:
@@ -315,6 +333,6 @@ class Oracle:
                     x_scaled=x, y_scaled=y, omega=omega, eta_hat=eta_hat)
 
 
-def solve(prob, x0=None, y0=None, trace=None, snapshots=None, **opts):
+def solve(prob, x0=None, y0=None, trace=None, snapshots=None, states=None, **opts):
     """Convenience wrapper: Oracle(prob, Options(**opts)).solve(...)."""
-    return Oracle(prob, Options(**opts)).solve(x0, y0, trace, snapshots)
+    return Oracle(prob, Options(**opts)).solve(x0, y0, trace, snapshots, states)

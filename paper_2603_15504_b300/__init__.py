@@ -1,0 +1,284 @@
+"""Python binding of the PDCS C ABI (include/pdcs.h): argument marshalling only.
+
+Every computation runs in libpdcs.so (hand-written CUDA for sm_103a).  Arrays
+may be NumPy arrays (host) or CUDA torch tensors (device); the library detects
+the pointer kind.  There is no CPU fallback: if the library or a GPU is missing
+the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB, build  # noqa: F401
+
+CONE_ZERO, CONE_NONNEG, CONE_SOC, CONE_RSOC, CONE_EXP, CONE_DUAL_EXP = 0, 1, 2, 3, 4, 5
+TRACE_FIELDS = 12
+TRACE_NAMES = ("iter", "kbar", "period", "eta", "eta_hat", "beta", "omega", "max_err", "check",
+               "cand_avg", "restart", "rho_c")
+EXIT_NAMES = {0: "optimal", 1: "max_iter", 2: "primal_infeasible_low_acc",
+              3: "primal_infeasible_high_acc", 4: "dual_infeasible_low_acc",
+              5: "dual_infeasible_high_acc", 6: "time_limit", 7: "continue",
+              8: "numerical_error"}
+
+
+class PdcsCone(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("pad", ctypes.c_int32), ("dim", ctypes.c_int64)]
+
+
+class PdcsOptions(ctypes.Structure):
+    _fields_ = [("rel_tol", ctypes.c_double), ("abs_tol", ctypes.c_double),
+                ("time_limit", ctypes.c_double), ("max_iter", ctypes.c_int64),
+                ("use_preconditioner", ctypes.c_int32), ("ruiz_iters", ctypes.c_int32),
+                ("pc_alpha", ctypes.c_double), ("method", ctypes.c_int32),
+                ("use_adaptive_restart", ctypes.c_int32), ("check_freq", ctypes.c_int64),
+                ("precision", ctypes.c_int32), ("require_abs", ctypes.c_int32),
+                ("bisect_rel_tol", ctypes.c_double), ("verbose", ctypes.c_int32),
+                ("trace_capacity", ctypes.c_int32)]
+
+
+class PdcsResult(ctypes.Structure):
+    _fields_ = [("exit_code", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("pobj", ctypes.c_double), ("dobj", ctypes.c_double),
+                ("err_rel_p", ctypes.c_double), ("err_rel_d", ctypes.c_double),
+                ("err_rel_gap", ctypes.c_double), ("err_abs_p", ctypes.c_double),
+                ("err_abs_d", ctypes.c_double), ("err_abs_gap", ctypes.c_double),
+                ("solve_time_s", ctypes.c_double), ("iters", ctypes.c_int64),
+                ("attempts", ctypes.c_int64), ("restarts", ctypes.c_int64)]
+
+
+class PdcsState(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int64), ("kbar", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("period", ctypes.c_int64), ("restarts", ctypes.c_int64),
+                ("eta_hat", ctypes.c_double), ("eta_last", ctypes.c_double),
+                ("omega", ctypes.c_double), ("wsum", ctypes.c_double),
+                ("has_ref", ctypes.c_int32), ("has_prev", ctypes.c_int32),
+                ("ref_rho", ctypes.c_double), ("ref_abs_p", ctypes.c_double),
+                ("ref_abs_d", ctypes.c_double), ("ref_abs_gap", ctypes.c_double),
+                ("prev_rho", ctypes.c_double), ("prev_abs_p", ctypes.c_double),
+                ("prev_abs_d", ctypes.c_double), ("prev_abs_gap", ctypes.c_double)]
+
+
+EXPORTS = ("pdcs_default_options", "pdcs_setup", "pdcs_solve", "pdcs_resume", "pdcs_get_state",
+           "pdcs_set_state", "pdcs_get_iterate", "pdcs_get_trace", "pdcs_get_sizes", "pdcs_free",
+           "pdcs_last_error")
+
+_LIB = None
+
+
+def lib():
+    """Load libpdcs.so (building it first if it is missing or stale, unless
+    PDCS_AUTOBUILD=0)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if os.environ.get("PDCS_AUTOBUILD", "1") == "1" or not os.path.exists(LIB):
+        try:
+            build()
+        except Exception as e:  # noqa: BLE001
+            if not os.path.exists(LIB):
+                raise RuntimeError("libpdcs.so is missing and could not be built: %s" % e)
+    L = ctypes.CDLL(LIB)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    L.pdcs_default_options.argtypes = [ctypes.POINTER(PdcsOptions)]
+    L.pdcs_default_options.restype = None
+    L.pdcs_setup.argtypes = [ctypes.POINTER(vp), i64, i64, vp, vp, vp, vp, vp, i64, vp, vp,
+                             ctypes.POINTER(PdcsCone), i64, ctypes.POINTER(PdcsCone), i64,
+                             ctypes.POINTER(PdcsOptions), vp]
+    L.pdcs_setup.restype = ctypes.c_int
+    L.pdcs_solve.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(PdcsResult)]
+    L.pdcs_solve.restype = ctypes.c_int
+    L.pdcs_resume.argtypes = [vp, i64, vp, vp, vp, ctypes.POINTER(PdcsResult)]
+    L.pdcs_resume.restype = ctypes.c_int
+    L.pdcs_get_state.argtypes = [vp, ctypes.POINTER(PdcsState), vp, vp, vp, vp, vp, vp]
+    L.pdcs_get_state.restype = ctypes.c_int
+    L.pdcs_set_state.argtypes = [vp, ctypes.POINTER(PdcsState), vp, vp, vp, vp, vp, vp]
+    L.pdcs_set_state.restype = ctypes.c_int
+    L.pdcs_get_iterate.argtypes = [vp, i32, vp, vp]
+    L.pdcs_get_iterate.restype = ctypes.c_int
+    L.pdcs_get_trace.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+    L.pdcs_get_trace.restype = ctypes.c_int
+    L.pdcs_get_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.pdcs_get_sizes.restype = ctypes.c_int
+    L.pdcs_free.argtypes = [vp]
+    L.pdcs_free.restype = None
+    L.pdcs_last_error.argtypes = []
+    L.pdcs_last_error.restype = ctypes.c_char_p
+    _LIB = L
+    return L
+
+
+class PdcsError(RuntimeError):
+    pass
+
+
+def _check(rc):
+    if rc != 0:
+        raise PdcsError("pdcs error %d: %s" % (rc, lib().pdcs_last_error().decode()))
+
+
+def _ptr(a):
+    """Address of a contiguous NumPy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_options(**kw):
+    o = PdcsOptions()
+    lib().pdcs_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "method" and isinstance(v, str):
+            v = {"average": 0, "halpern": 1}[v]
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": 0, "fp32": 1}[v]
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _cones(lst):
+    arr = (PdcsCone * max(1, len(lst)))()
+    for i, (t, d) in enumerate(lst):
+        arr[i].type = int(t)
+        arr[i].dim = int(d)
+    return arr
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class Solver:
+    """One problem set up on the GPU (pdcs_setup); solve() may be called repeatedly.
+
+    `problem` is a dict with m, n, row_ptr, col_idx, val, h, c, nb, lo, hi,
+    row_cones, col_cones (NumPy arrays or CUDA tensors of the C ABI's dtypes)."""
+
+    def __init__(self, problem, stream=None, **options):
+        self._h = ctypes.c_void_p()
+        keep = []
+        L = lib()
+        p = problem
+
+        def arr(key, dtype):
+            a = p[key]
+            if not hasattr(a, "data_ptr"):
+                a = np.ascontiguousarray(a, dtype=dtype)
+            keep.append(a)
+            return a
+
+        self.m, self.n, self.nb = int(p["m"]), int(p["n"]), int(p["nb"])
+        rp = arr("row_ptr", np.int64)
+        ci = arr("col_idx", np.int32)
+        vv = arr("val", np.float64)
+        h = arr("h", np.float64)
+        c = arr("c", np.float64)
+        lo = arr("lo", np.float64) if self.nb else None
+        hi = arr("hi", np.float64) if self.nb else None
+        rc = _cones(p["row_cones"])
+        cc = _cones(p["col_cones"])
+        self.options = default_options(**options)
+        st = stream if stream is not None else _current_stream()
+        _check(L.pdcs_setup(ctypes.byref(self._h), self.m, self.n, _ptr(rp), _ptr(ci), _ptr(vv),
+                            _ptr(h), _ptr(c), self.nb, _ptr(lo), _ptr(hi), rc,
+                            len(p["row_cones"]), cc, len(p["col_cones"]),
+                            ctypes.byref(self.options), st))
+        mm, nn, nz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(L.pdcs_get_sizes(self._h, ctypes.byref(mm), ctypes.byref(nn), ctypes.byref(nz)))
+        self.nnz = nz.value
+
+    def _result(self, res, x, y, s):
+        d = {k: getattr(res, k) for k, _ in PdcsResult._fields_ if k != "pad"}
+        d.update(x=x, y=y, s=s, status=EXIT_NAMES.get(res.exit_code, "?"))
+        return d
+
+    def solve(self, x0=None, y0=None, out=None):
+        """Run one solve.  Returns a dict with x, y, s (NumPy, or the arrays in
+        `out` = (x, y, s) when given) and the pdcs_result fields."""
+        res = PdcsResult()
+        if out is None:
+            x, y, s = np.empty(self.n), np.empty(self.m), np.empty(self.m)
+        else:
+            x, y, s = out
+        if x0 is not None and not hasattr(x0, "data_ptr"):
+            x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        if y0 is not None and not hasattr(y0, "data_ptr"):
+            y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        _check(lib().pdcs_solve(self._h, _ptr(x0), _ptr(y0), _ptr(x), _ptr(y), _ptr(s),
+                                ctypes.byref(res)))
+        return self._result(res, x, y, s)
+
+    def resume(self, max_iter=0):
+        """Continue from the current state (pdcs_resume)."""
+        res = PdcsResult()
+        x, y, s = np.empty(self.n), np.empty(self.m), np.empty(self.m)
+        _check(lib().pdcs_resume(self._h, int(max_iter), _ptr(x), _ptr(y), _ptr(s),
+                                 ctypes.byref(res)))
+        return self._result(res, x, y, s)
+
+    def get_state(self):
+        """Solver state: the pdcs_state scalars plus x, y, x0, y0, xs, ys
+        (scaled, reformulated variables)."""
+        st = PdcsState()
+        v = {k: np.empty(self.n if k in ("x", "x0", "xs") else self.m)
+             for k in ("x", "y", "x0", "y0", "xs", "ys")}
+        _check(lib().pdcs_get_state(self._h, ctypes.byref(st),
+                                    *[_ptr(v[k]) for k in ("x", "y", "x0", "y0", "xs", "ys")]))
+        d = {k: getattr(st, k) for k, _ in PdcsState._fields_}
+        d.update(v)
+        return d
+
+    def set_state(self, state):
+        """Replace the solver state (keys as returned by get_state)."""
+        st = PdcsState()
+        for k, _ in PdcsState._fields_:
+            setattr(st, k, state[k])
+        vec = [np.ascontiguousarray(state[k], dtype=np.float64)
+               for k in ("x", "y", "x0", "y0", "xs", "ys")]
+        _check(lib().pdcs_set_state(self._h, ctypes.byref(st), *[_ptr(a) for a in vec]))
+
+    def get_iterate(self, which=0):
+        """Internal iterate (scaled, reformulated variables) as NumPy arrays."""
+        x, y = np.empty(self.n), np.empty(self.m)
+        _check(lib().pdcs_get_iterate(self._h, int(which), _ptr(x), _ptr(y)))
+        return x, y
+
+    def trace(self):
+        cap = int(self.options.trace_capacity)
+        out = np.zeros((max(cap, 1), TRACE_FIELDS))
+        cnt = ctypes.c_int64()
+        _check(lib().pdcs_get_trace(self._h, _ptr(out), cap, ctypes.byref(cnt)))
+        return out[:cnt.value]
+
+    def close(self):
+        if self._h:
+            lib().pdcs_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def solve(problem, x0=None, y0=None, **options):
+    """Set up, solve once, free."""
+    with Solver(problem, **options) as s:
+        return s.solve(x0, y0)

@@ -1,0 +1,76 @@
+// Shared device helpers for the PDCS kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PDCS_DEV __device__ __forceinline__
+
+namespace pdcs {
+
+PDCS_DEV double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+PDCS_DEV double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum of K values over the CTA; every thread receives the totals.  `sh` must
+// hold K * (blockDim.x / 32) doubles.  Deterministic (fixed tree order).
+template <int K>
+PDCS_DEV void block_sum(double (&v)[K], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * nw + wid] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh[k * nw + w];
+    v[k] = s;
+  }
+  __syncthreads();
+}
+
+template <int K>
+PDCS_DEV void block_max(double (&v)[K], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_max(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * nw + wid] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = sh[k * nw];
+    for (int w = 1; w < nw; ++w) s = fmax(s, sh[k * nw + w]);
+    v[k] = s;
+  }
+  __syncthreads();
+}
+
+// "Last CTA done" protocol: each CTA publishes its partials, then the CTA that
+// observes the final ticket performs the grid-level epilogue.  No CTA waits on
+// another, so this cannot hang.  Returns true in exactly one CTA.
+PDCS_DEV bool last_block_done(unsigned int* counter) {
+  __shared__ unsigned int s_ticket;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  const bool last = (s_ticket == gridDim.x * gridDim.y - 1);
+  if (last) __threadfence();
+  return last;
+}
+
+}  // namespace pdcs

@@ -1,0 +1,309 @@
+// Projections onto diagonally rescaled cones (PDCS note, Sec. 2.6: after the
+// rescaling G -> D1 G D2 the cones D1 K_d^* and D2^{-1} K_p are non-standard and
+// their projections reduce to one-dimensional root finding).
+//
+// Exponential cone K_exp = cl{(x, y, z): y > 0, y e^{x/y} <= z}.  The boundary of
+// E K_exp (E = diag(e), e > 0) is the surface {s E (r, 1, e^r) : s > 0} plus the
+// flat face {(x, 0, z) : x <= 0, z >= 0}.  The nearest surface point to p lies
+// on the ray a(r) = E (r, 1, e^r) that maximises phi(r) = <p, a>/||a||; its
+// stationarity condition phi'(r) = 0 is, after multiplying out and cancelling
+// the e^{3r} terms (with P = e o p, S = e o e),
+//   g(r) = (P0 S1 - P1 S0 r) + P2 S0 e^r (r^2 - r + S1/S0)
+//        + S2 e^{2r} (P0 (1 - r) - P1)                          (= 0),
+// and phi' has the sign of g.  A coarse scan of phi (FP32) locates the two
+// best local maxima on a grid; for each, the sign of g picks the neighbouring
+// interval that holds the true local maximum; a safeguarded Newton iteration
+// on g refines it (FP32, then FP64 polish).  The projection is the nearest of that surface point, the face
+// projection (min(p0,0), 0, max(p2,0)) and the origin, after the membership
+// tests for E K_exp and for the polar -E^{-1} K_exp^*.
+//
+// Second-order cone K_soc = {(t, w): ||w|| <= t}.  For E K_soc with e = (e0, ebar):
+// inside if ||vbar/ebar|| <= v0/e0, zero if ||ebar o vbar|| <= -e0 v0, else
+//   wbar_i = vbar_i b_i / (b_i + 2 mu),  w0 = v0 e0^2 / (e0^2 - 2 mu),  b_i = ebar_i^2,
+// with mu the root of F(mu) = sum a_i/(b_i + 2mu)^2 - v0^2 e0^2/(e0^2 - 2mu)^2,
+// a_i = vbar_i^2 b_i, on (0, e0^2/2) when v0 > 0; when v0 < 0 the variable
+// nu = 1/(2 mu) in (0, 1/e0^2) is used with
+//   H(nu) = sum a_i/(1 + b_i nu)^2 - v0^2 e0^2/(1 - e0^2 nu)^2;
+// both are decreasing from a positive value to -inf, and are solved by a
+// safeguarded Newton iteration.  v0 = 0 gives mu = e0^2/2, w0 = e0 ||wbar/ebar||.
+#pragma once
+#include <math.h>
+
+#include "common.cuh"
+
+namespace pdcs {
+
+#ifdef __CUDA_ARCH__
+#define PDCS_FEXP(x) __expf(x)
+#else
+#define PDCS_FEXP(x) expf(x)
+#endif
+#define PDCS_HD __host__ __device__ __forceinline__
+
+// ------------------------------------------------------------------ K_exp
+PDCS_HD bool exp_member(double x, double y, double z) {
+  if (y > 0.0) {
+    if (z <= 0.0) return false;
+    return x <= y * log(z / y);
+  }
+  return (y == 0.0) && (x <= 0.0) && (z >= 0.0);
+}
+
+PDCS_HD bool exp_dual_member(double u, double v, double w) {
+  if (u < 0.0) {
+    if (w <= 0.0) return false;
+    return log(-u) + v / u <= 1.0 + log(w);
+  }
+  return (u == 0.0) && (v >= 0.0) && (w >= 0.0);
+}
+
+// Coarse grid of ray parameters: r_i = sinh(-14 + 0.25 i), i = 0..kExpGrid-1.
+constexpr int kExpGrid = 113;
+PDCS_HD float exp_grid_r(int i) { return sinhf(-14.0f + 0.25f * (float)i); }
+
+// phi(r) for the coarse scan, in FP32, with the ray scaled by e^{-max(r,0)}.
+PDCS_HD float exp_phi_f(float r, float p0, float p1, float p2, float e0, float e1, float e2) {
+  const float R = fmaxf(r, 0.0f);
+  const float g = PDCS_FEXP(-R);
+  const float a0 = e0 * r * g, a1 = e1 * g, a2 = e2 * PDCS_FEXP(r - R);
+  const float num = p0 * a0 + p1 * a1 + p2 * a2;
+  const float den = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+  return num / den;
+}
+
+// g(r) and g'(r), both multiplied by e^{-2 max(r,0)} (the same factor, so the
+// Newton step g/g' and the sign of g are unchanged).
+template <typename F>
+PDCS_HD void exp_g(F r, F P0, F P1, F P2, F S0, F S1, F S2, F& g, F& dg) {
+  const F R = r > F(0) ? r : F(0);
+  const F E1 = exp(r - R);  // e^{r} e^{-R}
+  const F eR = exp(-R);     // e^{-R}
+  const F E2 = E1 * E1;     // e^{2r} e^{-2R}
+  const F q = r * r - r + S1 / S0;
+  g = (P0 * S1 - P1 * S0 * r) * eR * eR + P2 * S0 * E1 * eR * q + S2 * E2 * (P0 * (F(1) - r) - P1);
+  dg = -P1 * S0 * eR * eR + P2 * S0 * E1 * eR * (r * r + r - F(1) + S1 / S0) +
+       S2 * E2 * (P0 * (F(1) - F(2) * r) - F(2) * P1);
+}
+
+// Safeguarded Newton on g inside [lo, hi] with g(lo) > 0 >= g(hi).
+template <typename F>
+PDCS_HD F exp_newton(F r, F lo, F hi, F P0, F P1, F P2, F S0, F S1, F S2, int iters, F tol) {
+  for (int it = 0; it < iters; ++it) {
+    F g, dg;
+    exp_g<F>(r, P0, P1, P2, S0, S1, S2, g, dg);
+    if (g > F(0)) lo = r; else hi = r;
+    if (g == F(0)) break;
+    const F step = -g / dg;
+    F rn = r + step;
+    // converged: the correction is below tolerance (it may not even move r)
+    if (fabs(step) <= tol * (F(1) + fabs(r))) {
+      if (rn >= lo && rn <= hi) r = rn;
+      break;
+    }
+    if (!(rn > lo && rn < hi)) rn = F(0.5) * (lo + hi);
+    r = rn;
+  }
+  return r;
+}
+
+// Nearest point of the ray through diag(e)(r, 1, e^r) to p; returns the squared
+// distance (+inf when <p, a> <= 0, i.e. the ray is not visible from p).
+PDCS_HD double exp_ray_point(double r, const double p[3], const double e[3], double c[3]) {
+  const double R = fmax(r, 0.0), g = exp(-R);
+  const double a0 = e[0] * r * g, a1 = e[1] * g, a2 = e[2] * exp(r - R);
+  const double pa = p[0] * a0 + p[1] * a1 + p[2] * a2;
+  const double aa = a0 * a0 + a1 * a1 + a2 * a2;
+  if (!(pa > 0.0) || !(aa > 0.0)) return INFINITY;
+  const double s = pa / aa;
+  c[0] = s * a0; c[1] = s * a1; c[2] = s * a2;
+  return (p[0] - c[0]) * (p[0] - c[0]) + (p[1] - c[1]) * (p[1] - c[1]) + (p[2] - c[2]) * (p[2] - c[2]);
+}
+
+// Projection of p onto diag(e) K_exp.
+PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], double q[3]) {
+  const double u0 = p[0] / e[0], u1 = p[1] / e[1], u2 = p[2] / e[2];
+  if (exp_member(u0, u1, u2)) { q[0] = p[0]; q[1] = p[1]; q[2] = p[2]; return; }
+  if (exp_dual_member(-e[0] * p[0], -e[1] * p[1], -e[2] * p[2])) {
+    q[0] = q[1] = q[2] = 0.0;
+    return;
+  }
+  // face candidate, and the origin
+  double best[3] = {fmin(p[0], 0.0), 0.0, fmax(p[2], 0.0)};
+  double bd = (p[0] - best[0]) * (p[0] - best[0]) + p[1] * p[1] + (p[2] - best[2]) * (p[2] - best[2]);
+  const double d0 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+  if (d0 < bd) { best[0] = best[1] = best[2] = 0.0; bd = d0; }
+  if (!(p[0] <= 0.0 && p[1] <= 0.0)) {
+    // Coarse scan: the two largest local maxima of phi on the grid.  The
+    // visible part of the surface (phi > 0) can be narrower than the grid
+    // spacing, so refinement never requires a positive grid value.
+    const float fp0 = (float)p[0], fp1 = (float)p[1], fp2 = (float)p[2];
+    const float fe0 = (float)e[0], fe1 = (float)e[1], fe2 = (float)e[2];
+    float b1 = -3.0e38f, b2 = -3.0e38f;
+    int i1 = -1, i2 = -1;
+    float prev2 = -3.0e38f, prev = exp_phi_f(exp_grid_r(0), fp0, fp1, fp2, fe0, fe1, fe2);
+    for (int i = 0; i < kExpGrid; ++i) {
+      const float nxt = i + 1 < kExpGrid ? exp_phi_f(exp_grid_r(i + 1), fp0, fp1, fp2, fe0, fe1, fe2)
+                                         : -3.0e38f;
+      const float cur = prev;
+      if (cur >= prev2 && cur >= nxt) {
+        if (cur > b1) { b2 = b1; i2 = i1; b1 = cur; i1 = i; }
+        else if (cur > b2) { b2 = cur; i2 = i; }
+      }
+      prev2 = cur;
+      prev = nxt;
+    }
+    const double P0 = e[0] * p[0], P1 = e[1] * p[1], P2 = e[2] * p[2];
+    const double S0 = e[0] * e[0], S1 = e[1] * e[1], S2 = e[2] * e[2];
+    for (int pass = 0; pass < 2; ++pass) {
+      const int bi = pass == 0 ? i1 : i2;
+      if (bi < 0) continue;
+      const double rb = (double)exp_grid_r(bi);
+      double c[3];
+      double dd = exp_ray_point(rb, p, e, c);
+      if (dd < bd) { best[0] = c[0]; best[1] = c[1]; best[2] = c[2]; bd = dd; }
+      // the local maximum lies on the side where phi increases
+      double g, dg;
+      exp_g<double>(rb, P0, P1, P2, S0, S1, S2, g, dg);
+      double lo, hi;
+      if (g > 0.0) { lo = rb; hi = bi < kExpGrid - 1 ? (double)exp_grid_r(bi + 1) : rb; }
+      else { hi = rb; lo = bi > 0 ? (double)exp_grid_r(bi - 1) : rb; }
+      if (!(hi > lo)) continue;
+      const float P0f = (float)P0, P1f = (float)P1, P2f = (float)P2;
+      const float S0f = (float)S0, S1f = (float)S1, S2f = (float)S2;
+      float rf = exp_newton<float>((float)(0.5 * (lo + hi)), (float)lo, (float)hi, P0f, P1f, P2f,
+                                   S0f, S1f, S2f, 40, 1e-6f);
+      double r = (double)rf;
+      if (!(r > lo && r < hi)) r = 0.5 * (lo + hi);
+      r = exp_newton<double>(r, lo, hi, P0, P1, P2, S0, S1, S2, 12, 1e-15);
+      dd = exp_ray_point(r, p, e, c);
+      if (dd < bd) { best[0] = c[0]; best[1] = c[1]; best[2] = c[2]; bd = dd; }
+    }
+  }
+  q[0] = best[0]; q[1] = best[1]; q[2] = best[2];
+}
+
+// Projection onto diag(e) K' where K' = K_exp (dual == false) or K_exp^* (dual ==
+// true, via Moreau: P_{E K*}(v) = v + P_{E^{-1} K}(-v)).
+PDCS_HD void proj_exp_family(const double v[3], const double e[3], bool dual, double out[3]) {
+  if (!dual) { proj_exp_scaled(v, e, out); return; }
+  const double nv[3] = {-v[0], -v[1], -v[2]};
+  const double ie[3] = {1.0 / e[0], 1.0 / e[1], 1.0 / e[2]};
+  double q[3];
+  proj_exp_scaled(nv, ie, q);
+  out[0] = v[0] + q[0]; out[1] = v[1] + q[1]; out[2] = v[2] + q[2];
+}
+
+// ------------------------------------------------------------------ K_soc
+// CTA-wide projection of one block held in registers: each thread owns EPT
+// elements (index = threadIdx.x + k * NT); element 0 is the head.  `sh` is
+// scratch for block reductions (>= 8 + 2 * NT/32 doubles).
+template <int NT, int EPT>
+__device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)[EPT], int dim,
+                                             double* sh) {
+  const int tid = threadIdx.x;
+  if (tid == 0) { sh[0] = v[0]; sh[1] = e[0]; }
+  __syncthreads();
+  const double v0 = sh[0], e0 = sh[1];
+  __syncthreads();
+  double* red = sh + 8;
+  double s[2] = {0.0, 0.0};  // sum (v/e)^2, sum (e v)^2
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int i = tid + k * NT;
+    if (i >= 1 && i < dim) {
+      const double a = v[k] / e[k], b = v[k] * e[k];
+      s[0] += a * a;
+      s[1] += b * b;
+    }
+  }
+  block_sum<2>(s, red);
+  if (sqrt(s[0]) <= v0 / e0) return;  // inside
+  if (sqrt(s[1]) <= -e0 * v0) {       // polar
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) v[k] = 0.0;
+    return;
+  }
+  const double e02 = e0 * e0;
+  if (v0 == 0.0) {
+    double acc[1] = {0.0};
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int i = tid + k * NT;
+      if (i >= 1 && i < dim) {
+        const double b = e[k] * e[k];
+        v[k] = v[k] * b / (b + e02);
+        const double t = v[k] / e[k];
+        acc[0] += t * t;
+      }
+    }
+    block_sum<1>(acc, red);
+    if (tid == 0) v[0] = e0 * sqrt(acc[0]);
+    return;
+  }
+  // normalise by max |v| for range safety (the projection is homogeneous)
+  double mx[1] = {fabs(v0)};
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int i = tid + k * NT;
+    if (i >= 1 && i < dim) mx[0] = fmax(mx[0], fabs(v[k]));
+  }
+  block_max<1>(mx, red);
+  const double sc = mx[0] > 0.0 ? 1.0 / mx[0] : 1.0;
+  const double c0 = (v0 * sc) * (v0 * sc) * e02;
+  const bool pos = v0 > 0.0;
+  double lo = 0.0, hi = pos ? 0.5 * e02 : 1.0 / e02;
+  double x = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    double f[2] = {0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int i = tid + k * NT;
+      if (i >= 1 && i < dim) {
+        const double vv = v[k] * sc, b = e[k] * e[k], a = vv * vv * b;
+        if (pos) {
+          const double r = 1.0 / (b + 2.0 * x);
+          f[0] += a * r * r;
+          f[1] += a * r * r * r;
+        } else {
+          const double r = 1.0 / (1.0 + b * x);
+          f[0] += a * r * r;
+          f[1] += a * b * r * r * r;
+        }
+      }
+    }
+    block_sum<2>(f, red);
+    double F, dF;
+    if (pos) {
+      const double r = 1.0 / (e02 - 2.0 * x);
+      F = f[0] - c0 * r * r;
+      dF = -4.0 * f[1] - 4.0 * c0 * r * r * r;
+    } else {
+      const double r = 1.0 / (1.0 - e02 * x);
+      F = f[0] - c0 * r * r;
+      dF = -2.0 * f[1] - 2.0 * c0 * e02 * r * r * r;
+    }
+    if (F > 0.0) lo = x; else hi = x;
+    if (F == 0.0) break;
+    const double step = -F / dF;
+    double xn = x + step;
+    if (fabs(step) <= 1e-15 * x) {  // converged (the step may not even move x)
+      if (xn >= lo && xn <= hi) x = xn;
+      break;
+    }
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    x = xn;
+    if (hi - lo <= 1e-15 * hi) break;
+  }
+  const double mu2 = pos ? 2.0 * x : 1.0 / x;  // 2 mu
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int i = tid + k * NT;
+    if (i >= 1 && i < dim) {
+      const double b = e[k] * e[k];
+      v[k] = v[k] * (b / (b + mu2));
+    }
+  }
+  if (tid == 0) v[0] = pos ? v0 * e02 / (e02 - mu2) : v0 * e02 * x / (e02 * x - 1.0);
+}
+
+}  // namespace pdcs

@@ -1,0 +1,784 @@
+// Device kernels of one restarted-PDHG solve (PDCS note, Algorithm 1 on the
+// rescaled problem of Sec. 2.6).  All scalars live in one device struct (Ctl)
+// so the loop runs from captured CUDA graphs without host round trips:
+//   attempt   Function 1: primal step, G xhat, dual step, step-size test,
+//             then (accepted) G^T yhat, maxErr(zhat) -> beta (eq.
+//             adaptive_reflection), reflected Halpern step and weighted average
+//             (Algorithm 1);
+//   check     every check_freq accepted iterations: average candidate, KKT
+//             statistics of both candidates, normalized duality gaps by the
+//             bisection of Algorithm 3, restart candidate / conditions / KKT_omega
+//             fallback (Sec. 2.3), primal weight (Sec. 2.5), termination (Sec.
+//             3.2.3).
+// Grid-level sums use a fixed-order two-stage reduction (per-CTA partials, the
+// last CTA to finish adds them in CTA order), so every run is deterministic.
+#pragma once
+#include "common.cuh"
+#include "cones.cuh"
+
+namespace pdcs {
+
+enum : int { kRunning = -1 };
+// Row kinds (the cone G x - h belongs to) and column kinds.
+enum : uint8_t { RK_FREE = 0, RK_NONNEG = 1, RK_SOC = 2, RK_EXP = 3, RK_DEXP = 4 };
+enum : uint8_t { CK_BOX = 0, CK_ZERO = 1, CK_NONNEG = 2, CK_SOC = 3, CK_EXP = 4, CK_DEXP = 5 };
+enum : int { BS_DONE = 0, BS_EXP = 1, BS_BISECT = 2 };
+enum : int { CNT_STEP = 0, CNT_STATS0 = 1, CNT_HALPERN = 5, CNT_PROBE = 6, CNT_NUM = 8 };
+constexpr int kEwThreads = 256;
+constexpr int kStatSums = 8, kStatMax = 5, kStatK = kStatSums + kStatMax;
+
+struct PointStats {
+  double abs_p, abs_d, pobj, dobj, gap, rel_p, rel_d, rel_gap, max_err;
+  double u2, lam2, dx2, dy2;
+  double inf_abs_p, inf_abs_d, inf_rel_p, inf_rel_d, inf_rel_gap, inf_max;
+};
+
+struct Bisect {
+  int phase, k, nb, active;
+  double t, tl, tr, r, tau, sigma, result, last_dot;
+};
+
+struct Ctl {
+  double eta, eta_hat, eta_acc, omega, omega0, eta0, beta, wsum;
+  long long kbar, iter, k, period, restarts;
+  int status, accepted, period_done, cand;
+  int have_cand, has_ref, has_prev, pad0;
+  double ref_rho, ref_ep, ref_ed, ref_eg;
+  double prev_rho, prev_ep, prev_ed, prev_eg;
+  double h1, c1, hinf, cinf;
+  double rel_tol, abs_tol, bisect_tol, pad1;
+  long long check_freq, max_iter;
+  int method, adaptive_restart, require_abs, trace_cap;
+  int guard, guard_cap, probes, probe_cap;
+  int g_attempt, g_accept, g_check, g_restart;
+  PointStats st[4];  // 0 zhat (attempt), 1 z, 2 zbar (check), 3 returned point
+  Bisect bs[2];
+  unsigned int cnt[CNT_NUM];
+};
+
+template <typename T>
+struct Prob {
+  int64_t m, n, nb;
+  const T* h;
+  const T* c;
+  const double* lo;
+  const double* hi;
+  const double* d1;
+  const double* d2;
+  const uint8_t* rk;
+  const uint8_t* ck;
+};
+
+template <typename T>
+struct PointRef {
+  const T* x;
+  const T* y;
+  const T* gx;
+  const T* gty;
+};
+
+struct TmpRef {
+  double* tm;  // scaled projection of u = G x - h on cone rows
+  double* tn;  // scaled projection of lambda = c - G^T y on cone columns
+  double* um;  // unscaled projection of u / d1 on cone rows
+  double* un;  // unscaled projection of lambda / d2 on cone columns
+};
+
+#define PDCS_GRID_LOOP(i, N) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (N); i += (int64_t)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------- attempt
+// xhat = Proj_X(x - tau (c - G^T y)), tau = eta / omega (eq. PDHG); cone columns
+// are projected afterwards by the cone kernels.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_primal(Prob<T> p, const Ctl* __restrict__ ctl,
+                                                       const T* __restrict__ x,
+                                                       const T* __restrict__ gty,
+                                                       T* __restrict__ xh) {
+  if (!ctl->g_attempt) return;
+  const double tau = ctl->eta / ctl->omega;
+  PDCS_GRID_LOOP(j, p.n) {
+    double v = (double)x[j] - tau * ((double)p.c[j] - (double)gty[j]);
+    const uint8_t kd = p.ck[j];
+    if (kd == CK_BOX) v = fmin(fmax(v, p.lo[j]), p.hi[j]);
+    else if (kd == CK_ZERO) v = 0.0;
+    else if (kd == CK_NONNEG) v = fmax(v, 0.0);
+    xh[j] = (T)v;
+  }
+}
+
+// yhat = Proj_Y(y + sigma (h - G (2 xhat - x))), sigma = eta omega.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_dual(Prob<T> p, const Ctl* __restrict__ ctl,
+                                                     const T* __restrict__ y,
+                                                     const T* __restrict__ gxh,
+                                                     const T* __restrict__ gx,
+                                                     T* __restrict__ yh) {
+  if (!ctl->g_attempt) return;
+  const double sigma = ctl->eta * ctl->omega;
+  PDCS_GRID_LOOP(i, p.m) {
+    double v = (double)y[i] + sigma * ((double)p.h[i] - 2.0 * (double)gxh[i] + (double)gx[i]);
+    if (p.rk[i] == RK_NONNEG) v = fmax(v, 0.0);
+    yh[i] = (T)v;
+  }
+}
+
+// Step-size test of Function 1 (eq. adaptive_step_size).  kbar counts every
+// attempt and is incremented before the exponents use (kbar + 1).
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict__ ctl,
+                                                     const T* __restrict__ x,
+                                                     const T* __restrict__ xh,
+                                                     const T* __restrict__ y,
+                                                     const T* __restrict__ yh,
+                                                     const T* __restrict__ gxh,
+                                                     const T* __restrict__ gx,
+                                                     double* __restrict__ part) {
+  if (!ctl->g_attempt) return;
+  __shared__ double sh[3 * kEwThreads / 32];
+  double s[3] = {0.0, 0.0, 0.0};
+  PDCS_GRID_LOOP(j, p.n) {
+    const double d = (double)xh[j] - (double)x[j];
+    s[0] += d * d;
+  }
+  PDCS_GRID_LOOP(i, p.m) {
+    const double d = (double)yh[i] - (double)y[i];
+    s[1] += d * d;
+    s[2] += d * ((double)gxh[i] - (double)gx[i]);
+  }
+  block_sum<3>(s, sh);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) part[blockIdx.x * 3 + k] = s[k];
+  }
+  if (!last_block_done(&ctl->cnt[CNT_STEP])) return;
+  if (threadIdx.x != 0) return;
+  double dx2 = 0.0, dy2 = 0.0, inter = 0.0;
+  const volatile double* vp = part;
+  for (unsigned b = 0; b < gridDim.x; ++b) {
+    dx2 += vp[b * 3 + 0];
+    dy2 += vp[b * 3 + 1];
+    inter += vp[b * 3 + 2];
+  }
+  ctl->cnt[CNT_STEP] = 0u;
+  inter = fabs(inter);
+  const double omega = ctl->omega, eta = ctl->eta;
+  ctl->kbar += 1;
+  const double kb1 = (double)(ctl->kbar + 1);
+  const double num = 0.5 * (omega * dx2 + dy2 / omega);
+  const double eta_bar = inter > 0.0 ? num / inter : INFINITY;
+  const double eta_p = fmin((1.0 - pow(kb1, -0.3)) * eta_bar, (1.0 + pow(kb1, -0.6)) * eta);
+  const int acc = eta < eta_bar ? 1 : 0;
+  ctl->accepted = acc;
+  if (acc) {
+    ctl->eta_acc = eta;
+    ctl->eta_hat = eta_p;
+  }
+  ctl->eta = eta_p;
+  ctl->g_accept = acc;
+  if (!(eta_p > 0.0) || !isfinite(eta_p)) {
+    ctl->status = 8;  // numerical error
+    ctl->g_accept = 0;
+    ctl->g_attempt = 0;
+  }
+}
+
+// ------------------------------------------------------------- cone kernels
+PDCS_DEV double cone_scale(const double* d, int64_t i, int inv) {
+  if (d == nullptr) return 1.0;
+  return inv ? 1.0 / d[i] : d[i];
+}
+
+// Exponential-cone blocks: one thread per 3-vector.  Target cone diag(e) K' with
+// e = d or 1/d (inv) and K' = K_exp or K_exp^* (is_dual_exp[b] xor dual).
+// blockIdx.y selects one of two vectors (each with its own gate).
+template <typename B>
+__global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
+                           const uint8_t* __restrict__ isd, int64_t count,
+                           const double* __restrict__ d, int inv, int dual,
+                           const int* __restrict__ gate0, const int* __restrict__ gate1) {
+  B* v = blockIdx.y == 0 ? v0 : v1;
+  const int* gate = blockIdx.y == 0 ? gate0 : gate1;
+  if (gate != nullptr && *gate == 0) return;
+  PDCS_GRID_LOOP(b, count) {
+    const int64_t s = starts[b];
+    const double in[3] = {(double)v[s], (double)v[s + 1], (double)v[s + 2]};
+    const double e[3] = {cone_scale(d, s, inv), cone_scale(d, s + 1, inv), cone_scale(d, s + 2, inv)};
+    double out[3];
+    proj_exp_family(in, e, (isd[b] != 0) != (dual != 0), out);
+    v[s] = (B)out[0];
+    v[s + 1] = (B)out[1];
+    v[s + 2] = (B)out[2];
+  }
+}
+
+// Second-order-cone blocks: one CTA per block (dims <= NT * EPT); target cone
+// diag(e) K_soc (self-dual, so the same routine serves both modes).
+template <typename B, int NT, int EPT>
+__global__ void __launch_bounds__(NT) k_cone_soc(B* v0, B* v1, const int64_t* __restrict__ starts,
+                                                 const int32_t* __restrict__ dims,
+                                                 const double* __restrict__ d, int inv,
+                                                 const int* __restrict__ gate0,
+                                                 const int* __restrict__ gate1) {
+  B* v = blockIdx.y == 0 ? v0 : v1;
+  const int* gate = blockIdx.y == 0 ? gate0 : gate1;
+  if (gate != nullptr && *gate == 0) return;
+  __shared__ double sh[8 + 2 * (NT / 32) + 8];
+  const int64_t s = starts[blockIdx.x];
+  const int dim = dims[blockIdx.x];
+  double vv[EPT], ee[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int i = threadIdx.x + k * NT;
+    vv[k] = i < dim ? (double)v[s + i] : 0.0;
+    ee[k] = i < dim ? cone_scale(d, s + i, inv) : 1.0;
+  }
+  soc_proj_cta<NT, EPT>(vv, ee, dim, sh);
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int i = threadIdx.x + k * NT;
+    if (i < dim) v[s + i] = (B)vv[k];
+  }
+}
+
+// --------------------------------------------------------- KKT statistics
+// Copy u = G x - h (cone rows) and lambda = c - G^T y (cone columns) into the
+// projection buffers, scaled and (optionally) unscaled.  blockIdx.y selects the
+// point when two are processed together.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_res_prep(Prob<T> p, const int* __restrict__ gate,
+                                                         PointRef<T> a, PointRef<T> b,
+                                                         TmpRef ta, TmpRef tb) {
+  if (gate != nullptr && *gate == 0) return;
+  const PointRef<T> pt = blockIdx.y == 0 ? a : b;
+  const TmpRef tr = blockIdx.y == 0 ? ta : tb;
+  PDCS_GRID_LOOP(i, p.m) {
+    if (p.rk[i] >= RK_SOC) {
+      const double u = (double)pt.gx[i] - (double)p.h[i];
+      tr.tm[i] = u;
+      if (tr.um) tr.um[i] = u / p.d1[i];
+    }
+  }
+  PDCS_GRID_LOOP(j, p.n) {
+    if (p.ck[j] >= CK_SOC) {
+      const double l = (double)p.c[j] - (double)pt.gty[j];
+      tr.tn[j] = l;
+      if (tr.un) tr.un[j] = l / p.d2[j];
+    }
+  }
+}
+
+// Projection onto Lambda_j (Sec. 1.1): {0}, R^-, R^+ or R by bound finiteness.
+PDCS_DEV double proj_lambda(double lam, double lo, double hi) {
+  const bool lf = isfinite(lo), uf = isfinite(hi);
+  if (!lf && !uf) return 0.0;
+  if (!lf) return fmin(lam, 0.0);
+  if (!uf) return fmax(lam, 0.0);
+  return lam;
+}
+
+PDCS_DEV void finish_stats(const Ctl* ctl, PointStats& st, const double* s, const double* mx) {
+  st.abs_p = sqrt(s[0]);
+  st.abs_d = sqrt(s[1]);
+  st.pobj = s[2];
+  st.dobj = s[3];
+  st.u2 = s[4];
+  st.lam2 = s[5];
+  st.dx2 = s[6];
+  st.dy2 = s[7];
+  st.gap = fabs(st.pobj - st.dobj);
+  st.rel_p = st.abs_p / (1.0 + ctl->h1);
+  st.rel_d = st.abs_d / (1.0 + ctl->c1);
+  st.rel_gap = st.gap / (1.0 + fabs(st.pobj) + fabs(st.dobj));
+  st.max_err = fmax(st.rel_p, fmax(st.rel_d, st.rel_gap));
+  st.inf_abs_p = mx[0];
+  st.inf_abs_d = mx[3];
+  st.inf_rel_p = mx[0] / (1.0 + fmax(ctl->hinf, fmax(mx[1], mx[2])));
+  st.inf_rel_d = mx[3] / (1.0 + fmax(ctl->cinf, mx[4]));
+  st.inf_rel_gap = st.gap / (1.0 + fmax(fabs(st.pobj), fabs(st.dobj)));
+  st.inf_max = fmax(st.inf_rel_p, fmax(st.inf_rel_d, st.inf_rel_gap));
+}
+
+// Residual norms (eqs. tolerance-3 / tolerance-2 on the rescaled problem and
+// eq. PDCS_terminate_tolerance_rel on the unscaled one), objectives, and the
+// norms needed by Algorithm 3 and Sec. 2.5, for one point.  slot 0 also sets
+// the reflection parameter beta (eq. adaptive_reflection).
+template <typename T, bool FULL>
+__global__ void __launch_bounds__(kEwThreads) k_point_stats(Prob<T> p, Ctl* __restrict__ ctl,
+                                                            const int* __restrict__ gate, int slot,
+                                                            PointRef<T> pt, const T* __restrict__ x0,
+                                                            const T* __restrict__ y0, TmpRef tr,
+                                                            double* __restrict__ part) {
+  if (gate != nullptr && *gate == 0) return;
+  __shared__ double sh[kStatK * kEwThreads / 32];
+  double s[kStatSums];
+  double mx[kStatMax];
+#pragma unroll
+  for (int k = 0; k < kStatSums; ++k) s[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < kStatMax; ++k) mx[k] = 0.0;
+  PDCS_GRID_LOOP(i, p.m) {
+    const double gx = (double)pt.gx[i], h = (double)p.h[i], y = (double)pt.y[i];
+    const double u = gx - h;
+    const uint8_t kd = p.rk[i];
+    double P;
+    if (kd == RK_FREE) P = 0.0;
+    else if (kd == RK_NONNEG) P = fmax(u, 0.0);
+    else P = tr.tm[i];
+    const double r = u - P;
+    s[0] += r * r;
+    s[3] += h * y;
+    s[4] += u * u;
+    if (FULL) {
+      const double d1 = p.d1[i];
+      const double uu = u / d1;
+      double Pu;
+      if (kd == RK_FREE) Pu = 0.0;
+      else if (kd == RK_NONNEG) Pu = fmax(uu, 0.0);
+      else Pu = tr.um[i];
+      mx[0] = fmax(mx[0], fabs(uu - Pu));
+      mx[1] = fmax(mx[1], fabs(gx / d1));
+      mx[2] = fmax(mx[2], fabs(Pu));
+      if (y0) {
+        const double dy = y - (double)y0[i];
+        s[7] += dy * dy;
+      }
+    }
+  }
+  PDCS_GRID_LOOP(j, p.n) {
+    const double gty = (double)pt.gty[j], c = (double)p.c[j], x = (double)pt.x[j];
+    const double lam = c - gty;
+    const uint8_t kd = p.ck[j];
+    double res;
+    if (kd == CK_BOX) {
+      const double lo = p.lo[j], hi = p.hi[j];
+      res = lam - proj_lambda(lam, lo, hi);
+      if (isfinite(lo)) s[3] += lo * fmax(lam, 0.0);
+      if (isfinite(hi)) s[3] -= hi * fmax(-lam, 0.0);
+    } else if (kd == CK_ZERO) {
+      res = 0.0;
+    } else if (kd == CK_NONNEG) {
+      res = fmin(lam, 0.0);
+    } else {
+      res = lam - tr.tn[j];
+    }
+    s[1] += res * res;
+    s[2] += c * x;
+    s[5] += lam * lam;
+    if (FULL) {
+      const double d2 = p.d2[j];
+      const double resu = kd >= CK_SOC ? lam / d2 - tr.un[j] : res / d2;
+      mx[3] = fmax(mx[3], fabs(resu));
+      mx[4] = fmax(mx[4], fabs(gty / d2));
+      if (x0) {
+        const double dx = x - (double)x0[j];
+        s[6] += dx * dx;
+      }
+    }
+  }
+  block_sum<kStatSums>(s, sh);
+  block_max<kStatMax>(mx, sh);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kStatSums; ++k) part[blockIdx.x * kStatK + k] = s[k];
+    for (int k = 0; k < kStatMax; ++k) part[blockIdx.x * kStatK + kStatSums + k] = mx[k];
+  }
+  if (!last_block_done(&ctl->cnt[CNT_STATS0 + slot])) return;
+  if (threadIdx.x != 0) return;
+  double S[kStatSums], M[kStatMax];
+  for (int k = 0; k < kStatSums; ++k) S[k] = 0.0;
+  for (int k = 0; k < kStatMax; ++k) M[k] = 0.0;
+  const volatile double* vp = part;
+  for (unsigned b = 0; b < gridDim.x; ++b) {
+    for (int k = 0; k < kStatSums; ++k) S[k] += vp[b * kStatK + k];
+    for (int k = 0; k < kStatMax; ++k) M[k] = fmax(M[k], vp[b * kStatK + kStatSums + k]);
+  }
+  ctl->cnt[CNT_STATS0 + slot] = 0u;
+  PointStats& st = ctl->st[slot];
+  finish_stats(ctl, st, S, M);
+  if (slot == 0) {
+    const double me = st.max_err;
+    double beta = me > 0.0 ? -0.1 * log10(me) + 0.2 : 1.0;
+    beta = fmin(1.0, fmax(0.0, beta));
+    if (isnan(me)) beta = 0.0;
+    ctl->beta = beta;
+  }
+}
+
+// ------------------------------------------------------- Halpern + average
+// z^{t,k+1} = (k+1)/(k+2) ((1+beta) zhat - beta z) + z^{t,0}/(k+2) (Algorithm
+// 1), applied to (x, y) and, by linearity, to the maintained products G x and
+// G^T y; the average accumulators add eta * z^{t,k+1} in FP64.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_halpern(
+    Prob<T> p, Ctl* __restrict__ ctl, T* __restrict__ x, T* __restrict__ y, T* __restrict__ gx,
+    T* __restrict__ gty, const T* __restrict__ xh, const T* __restrict__ yh,
+    const T* __restrict__ gxh, const T* __restrict__ gtyh, const T* __restrict__ x0,
+    const T* __restrict__ y0, const T* __restrict__ gx0, const T* __restrict__ gty0,
+    double* __restrict__ xs, double* __restrict__ ys, double* __restrict__ trace) {
+  if (!ctl->g_accept) return;
+  const double kk = (double)ctl->k;
+  const double beta = ctl->beta, eta = ctl->eta_acc;
+  const double a = (kk + 1.0) / (kk + 2.0), b = 1.0 / (kk + 2.0);
+  PDCS_GRID_LOOP(j, p.n) {
+    const T xn = (T)(a * ((1.0 + beta) * (double)xh[j] - beta * (double)x[j]) + b * (double)x0[j]);
+    x[j] = xn;
+    xs[j] += eta * (double)xn;
+    gty[j] = (T)(a * ((1.0 + beta) * (double)gtyh[j] - beta * (double)gty[j]) + b * (double)gty0[j]);
+  }
+  PDCS_GRID_LOOP(i, p.m) {
+    const T yn = (T)(a * ((1.0 + beta) * (double)yh[i] - beta * (double)y[i]) + b * (double)y0[i]);
+    y[i] = yn;
+    ys[i] += eta * (double)yn;
+    gx[i] = (T)(a * ((1.0 + beta) * (double)gxh[i] - beta * (double)gx[i]) + b * (double)gx0[i]);
+  }
+  if (!last_block_done(&ctl->cnt[CNT_HALPERN])) return;
+  if (threadIdx.x != 0) return;
+  ctl->cnt[CNT_HALPERN] = 0u;
+  ctl->k += 1;
+  ctl->iter += 1;
+  ctl->wsum += eta;
+  const long long it = ctl->iter;
+  if (trace != nullptr && it <= ctl->trace_cap) {
+    double* r = trace + (it - 1) * 12;
+    r[0] = (double)it; r[1] = (double)ctl->kbar; r[2] = (double)ctl->period; r[3] = eta;
+    r[4] = ctl->eta_hat; r[5] = beta; r[6] = ctl->omega; r[7] = ctl->st[0].max_err;
+    r[8] = 0.0; r[9] = -1.0; r[10] = 0.0; r[11] = NAN;
+  }
+  if (!isfinite(ctl->st[0].max_err)) {
+    ctl->status = 8;
+    ctl->g_attempt = 0;
+  } else if (it % ctl->check_freq == 0) {
+    ctl->period_done = 1;
+    ctl->g_attempt = 0;
+    ctl->g_check = 1;
+  } else if (it >= ctl->max_iter) {
+    ctl->status = 1;
+    ctl->g_attempt = 0;
+  }
+}
+
+// Body terminator of the attempt loop: continue while the period needs more
+// accepted iterations (bounded by guard_cap bodies per graph launch).
+__global__ void k_loop_ctl(Ctl* ctl, cudaGraphConditionalHandle h) {
+  ctl->guard += 1;
+  const int go = (ctl->status == kRunning && !ctl->period_done && ctl->guard < ctl->guard_cap);
+  ctl->g_attempt = go;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_period_begin(Ctl* ctl, cudaGraphConditionalHandle h) {
+  ctl->guard = 0;
+  const int go = (ctl->status == kRunning && !ctl->period_done);
+  ctl->g_attempt = go;
+  ctl->g_accept = 0;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// ------------------------------------------------------------------ check
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_average(int64_t n, int64_t m, const Ctl* __restrict__ ctl,
+                                                        const double* __restrict__ xs,
+                                                        const double* __restrict__ ys,
+                                                        T* __restrict__ xb, T* __restrict__ yb) {
+  if (!ctl->g_check) return;
+  const double w = ctl->wsum;
+  PDCS_GRID_LOOP(j, n) xb[j] = (T)(xs[j] / w);
+  PDCS_GRID_LOOP(i, m) yb[i] = (T)(ys[i] / w);
+}
+
+// Algorithm 3 set-up for both candidates: r = ||z_c - z^{t,0}||_N, and the first
+// trial t0 = r / sqrt(tau ||b1||^2 + sigma ||b2||^2) (the unconstrained step that
+// reaches radius r).
+__global__ void k_bisect_init(Ctl* ctl, cudaGraphConditionalHandle h) {
+  int any = 0;
+  const double tau = ctl->eta_acc / ctl->omega, sigma = ctl->eta_acc * ctl->omega;
+  for (int c = 0; c < 2; ++c) {
+    Bisect& b = ctl->bs[c];
+    b.phase = BS_DONE;
+    b.active = 0;
+    b.result = c == 0 ? 0.0 : INFINITY;
+    b.k = 0;
+    b.nb = 0;
+    b.tau = tau;
+    b.sigma = sigma;
+    b.last_dot = 0.0;
+    if (!ctl->g_check) continue;
+    if (c == 1 && ctl->method != 0) continue;
+    const PointStats& st = ctl->st[1 + c];
+    const double r = sqrt(st.dx2 / tau + st.dy2 / sigma);
+    const double scale = sqrt(tau * st.lam2 + sigma * st.u2);
+    b.r = r;
+    b.result = 0.0;
+    if (!(r > 0.0) || !(scale > 0.0)) continue;
+    b.t = r / scale;
+    b.tl = 0.0;
+    b.tr = b.t;
+    b.phase = BS_EXP;
+    b.active = 1;
+    any = 1;
+  }
+  ctl->probes = 0;
+  cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+PDCS_DEV double probe_t(const Bisect& b) { return b.phase == BS_EXP ? b.t : 0.5 * (b.tl + b.tr); }
+
+// z(t) = (Proj_X(x + t tau b1), Proj_Y(y + t sigma b2)), b = (G^T y - c, h - G x)
+// (eq. compute_zt_2), elementwise part; blockIdx.y = candidate.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_probe_prep(Prob<T> p, const Ctl* __restrict__ ctl,
+                                                           PointRef<T> a, PointRef<T> bpt,
+                                                           double* __restrict__ px0,
+                                                           double* __restrict__ py0,
+                                                           double* __restrict__ px1,
+                                                           double* __restrict__ py1) {
+  const int c = blockIdx.y;
+  const Bisect& bs = ctl->bs[c];
+  if (!bs.active) return;
+  const PointRef<T> pt = c == 0 ? a : bpt;
+  double* px = c == 0 ? px0 : px1;
+  double* py = c == 0 ? py0 : py1;
+  const double t = probe_t(bs);
+  const double tt = t * bs.tau, ts = t * bs.sigma;
+  PDCS_GRID_LOOP(j, p.n) {
+    const double b1 = (double)pt.gty[j] - (double)p.c[j];
+    double v = (double)pt.x[j] + tt * b1;
+    const uint8_t kd = p.ck[j];
+    if (kd == CK_BOX) v = fmin(fmax(v, p.lo[j]), p.hi[j]);
+    else if (kd == CK_ZERO) v = 0.0;
+    else if (kd == CK_NONNEG) v = fmax(v, 0.0);
+    px[j] = v;
+  }
+  PDCS_GRID_LOOP(i, p.m) {
+    const double b2 = (double)p.h[i] - (double)pt.gx[i];
+    double v = (double)pt.y[i] + ts * b2;
+    if (p.rk[i] == RK_NONNEG) v = fmax(v, 0.0);
+    py[i] = v;
+  }
+}
+
+// ||z(t) - z||_N and b^T (z(t) - z) for both candidates; the last CTA advances
+// the exponential search / bisection state machines of Algorithm 3.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __restrict__ ctl,
+                                                             PointRef<T> a, PointRef<T> bpt,
+                                                             const double* __restrict__ px0,
+                                                             const double* __restrict__ py0,
+                                                             const double* __restrict__ px1,
+                                                             const double* __restrict__ py1,
+                                                             double* __restrict__ part,
+                                                             cudaGraphConditionalHandle h) {
+  const int c = blockIdx.y;
+  const Bisect& bs = ctl->bs[c];
+  __shared__ double sh[4 * kEwThreads / 32];
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  if (bs.active) {
+    const PointRef<T> pt = c == 0 ? a : bpt;
+    const double* px = c == 0 ? px0 : px1;
+    const double* py = c == 0 ? py0 : py1;
+    PDCS_GRID_LOOP(j, p.n) {
+      const double dx = px[j] - (double)pt.x[j];
+      s[0] += dx * dx;
+      s[2] += ((double)pt.gty[j] - (double)p.c[j]) * dx;
+    }
+    PDCS_GRID_LOOP(i, p.m) {
+      const double dy = py[i] - (double)pt.y[i];
+      s[1] += dy * dy;
+      s[3] += ((double)p.h[i] - (double)pt.gx[i]) * dy;
+    }
+  }
+  block_sum<4>(s, sh);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) part[(blockIdx.y * gridDim.x + blockIdx.x) * 4 + k] = s[k];
+  }
+  if (!last_block_done(&ctl->cnt[CNT_PROBE])) return;
+  if (threadIdx.x != 0) return;
+  ctl->cnt[CNT_PROBE] = 0u;
+  const volatile double* vp = part;
+  int any = 0;
+  for (int cc = 0; cc < 2; ++cc) {
+    Bisect& b = ctl->bs[cc];
+    if (!b.active) continue;
+    double S[4] = {0.0, 0.0, 0.0, 0.0};
+    for (unsigned blk = 0; blk < gridDim.x; ++blk)
+      for (int k = 0; k < 4; ++k) S[k] += vp[(cc * gridDim.x + blk) * 4 + k];
+    const double dist = sqrt(S[0] / b.tau + S[1] / b.sigma);
+    b.last_dot = S[2] + S[3];
+    if (b.phase == BS_EXP) {
+      if (dist > b.r) {
+        if (b.k == 0) { b.tl = 0.0; b.tr = b.t; }
+        else { b.tl = 0.5 * b.t; b.tr = b.t; }
+        b.phase = BS_BISECT;
+      } else {
+        b.t *= 2.0;
+        b.k += 1;
+        b.tl = 0.5 * b.t;
+        b.tr = b.t;
+        if (b.k >= 64) b.phase = BS_BISECT;
+      }
+    } else {
+      const double tm = 0.5 * (b.tl + b.tr);
+      if (dist < b.r) b.tl = tm; else b.tr = tm;
+      b.nb += 1;
+    }
+    if (b.phase == BS_BISECT && (b.tr - b.tl <= ctl->bisect_tol * b.tr || b.nb >= 64)) {
+      b.phase = BS_DONE;
+      b.active = 0;
+      b.result = b.last_dot / b.r;
+    }
+    any |= b.active;
+  }
+  ctl->probes += 1;
+  if (ctl->probes >= ctl->probe_cap) {
+    for (int cc = 0; cc < 2; ++cc) {
+      Bisect& b = ctl->bs[cc];
+      if (b.active) { b.active = 0; b.phase = BS_DONE; b.result = b.last_dot / b.r; }
+    }
+    any = 0;
+  }
+  cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+PDCS_DEV double kkt_w(double ep, double ed, double eg, double w) {
+  return sqrt(w * w * ep * ep + ed * ed / (w * w) + eg * eg);
+}
+
+// GetRestartCandidate, termination, restart conditions, KKT_omega fallback,
+// primal-weight update (Secs. 2.3, 2.5, 3.2.3).
+__global__ void k_check_decide(Ctl* ctl, double* trace) {
+  if (!ctl->g_check) return;
+  const bool avg = ctl->method == 0;
+  const double rho_h = ctl->bs[0].result;
+  const double rho_a = avg ? ctl->bs[1].result : INFINITY;
+  const double w = ctl->omega;
+  const bool fb = rho_h < 0.0 || (avg && rho_a < 0.0) || (ctl->has_ref && ctl->ref_rho < 0.0) ||
+                  (ctl->has_prev && ctl->prev_rho < 0.0);
+  const PointStats& s1 = ctl->st[1];
+  const PointStats& s2 = ctl->st[2];
+  const double m_h = fb ? kkt_w(s1.abs_p, s1.abs_d, s1.gap, w) : rho_h;
+  const double m_a = avg ? (fb ? kkt_w(s2.abs_p, s2.abs_d, s2.gap, w) : rho_a) : INFINITY;
+  const int cand = (m_h <= m_a) ? 0 : 1;
+  const double val = cand ? m_a : m_h;
+  const double rho_c = cand ? rho_a : rho_h;
+  const PointStats& sc = ctl->st[1 + cand];
+  ctl->cand = cand;
+  ctl->have_cand = 1;
+  const long long it = ctl->iter;
+  if (trace != nullptr && it >= 1 && it <= ctl->trace_cap) {
+    double* r = trace + (it - 1) * 12;
+    r[8] = 1.0; r[9] = (double)cand; r[11] = val;
+  }
+  bool done = sc.inf_max <= ctl->rel_tol;
+  if (ctl->require_abs) done = done && fmax(sc.inf_abs_p, fmax(sc.inf_abs_d, sc.gap)) <= ctl->abs_tol;
+  ctl->g_restart = 0;
+  if (done) { ctl->status = 0; return; }
+  if (!isfinite(sc.inf_max)) { ctl->status = 8; return; }
+  bool restart = false;
+  if (ctl->adaptive_restart) {
+    const bool cond3 = (double)ctl->k >= 0.223 * (double)ctl->kbar;
+    if (!ctl->has_ref) {
+      restart = cond3;
+    } else {
+      const double ref = fb ? kkt_w(ctl->ref_ep, ctl->ref_ed, ctl->ref_eg, w) : ctl->ref_rho;
+      const bool c1 = val <= 0.4 * ref;
+      bool c2 = false;
+      if (ctl->has_prev) {
+        const double pv = fb ? kkt_w(ctl->prev_ep, ctl->prev_ed, ctl->prev_eg, w) : ctl->prev_rho;
+        c2 = val <= 0.8 * ref && val > pv;
+      }
+      restart = c1 || c2 || cond3;
+    }
+  }
+  if (restart) {
+    if (trace != nullptr && it >= 1 && it <= ctl->trace_cap) trace[(it - 1) * 12 + 10] = 1.0;
+    const double dx = sqrt(sc.dx2), dy = sqrt(sc.dy2);
+    double om = ctl->omega;
+    if (dx > 1e-10 && dy > 1e-10) om = exp(0.5 * log(dy / dx) + 0.5 * log(om));
+    if (om > 1e5 || om < 1e-5) om = ctl->omega0;
+    ctl->omega = om;
+    ctl->has_ref = 1;
+    ctl->ref_rho = rho_c;
+    ctl->ref_ep = sc.abs_p; ctl->ref_ed = sc.abs_d; ctl->ref_eg = sc.gap;
+    ctl->has_prev = 0;
+    ctl->period += 1;
+    ctl->restarts += 1;
+    ctl->k = 0;
+    ctl->wsum = 0.0;
+    ctl->g_restart = 1;
+  } else {
+    ctl->has_prev = 1;
+    ctl->prev_rho = rho_c;
+    ctl->prev_ep = sc.abs_p; ctl->prev_ed = sc.abs_d; ctl->prev_eg = sc.gap;
+  }
+}
+
+// Keep the chosen candidate (the returned point) and, on restart, make it the
+// new anchor and current iterate and clear the average.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_cand_copy(int64_t n, int64_t m, const Ctl* __restrict__ ctl,
+                                                          PointRef<T> z, PointRef<T> zb, T* xc, T* yc,
+                                                          T* gxc, T* gtyc, T* x0, T* y0, T* x, T* y,
+                                                          double* xs, double* ys) {
+  if (!ctl->g_check) return;
+  const PointRef<T> s = ctl->cand ? zb : z;
+  const bool rs = ctl->g_restart != 0;
+  PDCS_GRID_LOOP(j, n) {
+    const T v = s.x[j];
+    gtyc[j] = s.gty[j];
+    xc[j] = v;
+    if (rs) { x0[j] = v; x[j] = v; xs[j] = 0.0; }
+  }
+  PDCS_GRID_LOOP(i, m) {
+    const T v = s.y[i];
+    gxc[i] = s.gx[i];
+    yc[i] = v;
+    if (rs) { y0[i] = v; y[i] = v; ys[i] = 0.0; }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_copy_products(int64_t n, int64_t m, const int* __restrict__ gate,
+                                                              const T* gx0, const T* gty0, T* gx, T* gty) {
+  if (!*gate) return;
+  PDCS_GRID_LOOP(j, n) gty[j] = gty0[j];
+  PDCS_GRID_LOOP(i, m) gx[i] = gx0[i];
+}
+
+__global__ void k_check_end(Ctl* ctl) {
+  if (!ctl->g_check) return;
+  ctl->period_done = 0;
+  ctl->g_restart = 0;
+  ctl->g_check = 0;
+  if (ctl->status == kRunning && ctl->iter >= ctl->max_iter) ctl->status = 1;
+  ctl->g_attempt = ctl->status == kRunning;
+}
+
+// ----------------------------------------------------------- init / output
+template <typename T>
+__global__ void k_fill(T* v, int64_t n, double val) {
+  PDCS_GRID_LOOP(i, n) v[i] = (T)val;
+}
+
+template <typename S, typename D>
+__global__ void k_convert(const S* in, D* out, int64_t n) {
+  PDCS_GRID_LOOP(i, n) out[i] = (D)in[i];
+}
+
+// Warm start (original variables, RSOC rotation already undone) -> solver
+// variables: divide by the scaling (Algorithm 2).
+template <typename T>
+__global__ void k_warm(T* out, const double* in, const double* d, int64_t n) {
+  PDCS_GRID_LOOP(i, n) out[i] = (T)(in[i] / d[i]);
+}
+
+// Unscale the returned point: x = D2 xt, y = D1 yt, s = (G xt - hhat) / D1.
+template <typename T>
+__global__ void k_unscale(Prob<T> p, const T* xt, const T* yt, const T* gxt, double* x, double* y,
+                          double* s) {
+  PDCS_GRID_LOOP(j, p.n) x[j] = p.d2[j] * (double)xt[j];
+  PDCS_GRID_LOOP(i, p.m) {
+    y[i] = p.d1[i] * (double)yt[i];
+    s[i] = ((double)gxt[i] - (double)p.h[i]) / p.d1[i];
+  }
+}
+
+}  // namespace pdcs

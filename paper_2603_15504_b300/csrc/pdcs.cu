@@ -1,0 +1,1118 @@
+// Host side of the PDCS C ABI (include/pdcs.h): problem set-up on the device,
+// the captured-graph solve loop, checkpoint / resume, and result unscaling.
+//
+// Solve loop (PDCS note, Algorithm 1 inside Algorithm 2): one CUDA graph per
+// check period, relaunched by the host until the device status leaves
+// "running":
+//   period_begin
+//   WHILE attempts needed:        Function 1 attempt + (if accepted) Halpern step
+//   [gated on a completed period] check: average candidate, KKT statistics,
+//   WHILE bisection unfinished:   Algorithm 3 probes for both candidates
+//   decide / copy / refresh products / end of period
+// The WHILE nodes are CUDA conditional graph nodes whose condition is written
+// by the last kernel of each body, so the loop runs without host round trips;
+// every loop has a hard per-launch cap.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pdcs.h"
+#include "common.cuh"
+#include "cones.cuh"
+#include "iterate.cuh"
+#include "setup.cuh"
+#include "spmv.cuh"
+
+namespace pdcs {
+
+thread_local std::string g_last_error;
+
+struct Fail {
+  int code;
+  std::string msg;
+};
+
+static void cuda_check(cudaError_t e, const char* what, int line) {
+  if (e != cudaSuccess) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s failed (line %d): %s", what, line, cudaGetErrorString(e));
+    throw Fail{e == cudaErrorMemoryAllocation ? PDCS_ERR_NOMEM : PDCS_ERR_CUDA, buf};
+  }
+}
+#define CK(call) cuda_check((call), #call, __LINE__)
+
+static void invalid(const std::string& msg) { throw Fail{PDCS_ERR_INVALID, msg}; }
+
+// Owner of every device allocation of a handle.
+struct Arena {
+  std::vector<void*> ptrs;
+  template <typename T>
+  T* alloc(int64_t count) {
+    void* p = nullptr;
+    const size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+    CK(cudaMalloc(&p, bytes));
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  void release(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) { cudaFree(q); q = nullptr; }
+  }
+  ~Arena() {
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+};
+
+template <typename T>
+static void copy_in(T* dst, const T* src, int64_t count, cudaStream_t st) {
+  if (count <= 0) return;
+  CK(cudaMemcpyAsync(dst, src, (size_t)count * sizeof(T), cudaMemcpyDefault, st));
+}
+
+template <typename T>
+static std::vector<T> to_host(const T* dptr, int64_t count, cudaStream_t st) {
+  std::vector<T> h((size_t)std::max<int64_t>(count, 0));
+  if (count > 0) CK(cudaMemcpyAsync(h.data(), dptr, (size_t)count * sizeof(T), cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  return h;
+}
+
+static int ew_grid(int64_t n) {
+  const int64_t b = (n + kEwThreads - 1) / kEwThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 148 * 4));
+}
+static int warp_grid(int64_t rows) {
+  const int64_t b = (rows * 32 + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 148 * 16));
+}
+
+// ----------------------------------------------------------- SpMV plans
+struct SpmvPlan {
+  SpmvTask* tasks = nullptr;
+  int ntasks = 0;
+  double* partial = nullptr;
+  unsigned int* counters = nullptr;
+};
+
+// Bin rows into SpMV tasks (see spmv.cuh): short rows one per thread, medium
+// rows one lane group per row, long rows split into kChunk-nonzero chunks.
+static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream_t st) {
+  const int64_t m = (int64_t)rp.size() - 1;
+  std::vector<SpmvTask> tasks;
+  int64_t npart = 0;
+  int ncnt = 0;
+  auto cls = [&](int64_t r) {
+    const int64_t len = rp[r + 1] - rp[r];
+    if (len <= 4) return 0;
+    if (len <= 64) return 1;
+    if (len <= 4096) return 2;
+    return 3;
+  };
+  int64_t r = 0;
+  while (r < m) {
+    const int c = cls(r);
+    if (c == 3) {
+      const int64_t s = rp[r], e = rp[r + 1];
+      const int64_t nch = (e - s + kChunk - 1) / kChunk;
+      for (int64_t k = 0; k < nch; ++k) {
+        SpmvTask t{};
+        t.kind = 2;
+        t.counter = ncnt;
+        t.nchunks = (int32_t)nch;
+        t.a = r;
+        t.b = k;
+        t.c = s + k * kChunk;
+        t.d = std::min(e, s + (k + 1) * kChunk);
+        t.pbase = npart;
+        tasks.push_back(t);
+      }
+      npart += nch;
+      ncnt += 1;
+      ++r;
+      continue;
+    }
+    const int64_t max_rows = c == 0 ? 256 : (c == 1 ? 128 : 32);
+    const int64_t max_nnz = c == 2 ? 16384 : 8192;
+    int64_t e = r, nnz = 0;
+    while (e < m && cls(e) == c && e - r < max_rows && (nnz == 0 || nnz + rp[e + 1] - rp[e] <= max_nnz)) {
+      nnz += rp[e + 1] - rp[e];
+      ++e;
+    }
+    SpmvTask t{};
+    t.kind = c == 0 ? 0 : 1;
+    t.g = c == 1 ? 8 : 32;
+    t.a = r;
+    t.b = e;
+    tasks.push_back(t);
+    r = e;
+  }
+  SpmvPlan p;
+  p.ntasks = (int)tasks.size();
+  if (p.ntasks > 0) {
+    p.tasks = ar.alloc<SpmvTask>(p.ntasks);
+    CK(cudaMemcpyAsync(p.tasks, tasks.data(), tasks.size() * sizeof(SpmvTask), cudaMemcpyHostToDevice, st));
+  }
+  p.partial = ar.alloc<double>(std::max<int64_t>(npart, 1));
+  p.counters = ar.alloc<unsigned int>(std::max(ncnt, 1));
+  CK(cudaMemsetAsync(p.counters, 0, sizeof(unsigned int) * std::max(ncnt, 1), st));
+  CK(cudaStreamSynchronize(st));
+  return p;
+}
+
+template <typename T>
+static void launch_spmv(const SpmvPlan& p, const int64_t* rp, const int32_t* ci, const T* vv,
+                        const T* x, T* y, const int* gate, cudaStream_t st) {
+  if (p.ntasks == 0) return;
+  k_spmv<T><<<p.ntasks, kSpmvThreads, 0, st>>>(p.tasks, rp, ci, vv, x, y, p.partial, p.counters, gate);
+}
+
+// ------------------------------------------------------------- cone tables
+struct ConeTable {
+  // SOC tiers by block dimension: <= 128 (32 threads), <= 4096 (256), <= 8192 (512)
+  int64_t* soc_s[3] = {nullptr, nullptr, nullptr};
+  int32_t* soc_d[3] = {nullptr, nullptr, nullptr};
+  int64_t nsoc[3] = {0, 0, 0};
+  int64_t* exp_s = nullptr;
+  uint8_t* exp_isd = nullptr;
+  int64_t nexp = 0;
+};
+
+static const int kSocTierMax[3] = {128, 4096, 8192};
+
+// Projection of one or two vectors onto a product of cones: the blocks are
+// projected onto diag(e) K_b (dual = 0) or diag(e) K_b^* (dual = 1) with
+// e = d, 1/d (inv) or 1 (d == NULL).  Zero / nonnegative blocks are handled by
+// the producing kernels.
+template <typename B>
+static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d, int inv, int dual,
+                    const int* g0, const int* g1, cudaStream_t st) {
+  if (t.nexp > 0) {
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((t.nexp + 127) / 128, 148 * 8)), nvec);
+    k_cone_exp<B><<<grid, 128, 0, st>>>(v0, v1, t.exp_s, t.exp_isd, t.nexp, d, inv, dual, g0, g1);
+  }
+  if (t.nsoc[0] > 0)
+    k_cone_soc<B, 32, 4><<<dim3((unsigned)t.nsoc[0], nvec), 32, 0, st>>>(v0, v1, t.soc_s[0], t.soc_d[0], d, inv, g0, g1);
+  if (t.nsoc[1] > 0)
+    k_cone_soc<B, 256, 16><<<dim3((unsigned)t.nsoc[1], nvec), 256, 0, st>>>(v0, v1, t.soc_s[1], t.soc_d[1], d, inv, g0, g1);
+  if (t.nsoc[2] > 0)
+    k_cone_soc<B, 512, 16><<<dim3((unsigned)t.nsoc[2], nvec), 512, 0, st>>>(v0, v1, t.soc_s[2], t.soc_d[2], d, inv, g0, g1);
+}
+
+}  // namespace pdcs
+
+using namespace pdcs;
+
+// ------------------------------------------------------------------ handle
+struct SolverBase {
+  virtual ~SolverBase() {}
+  virtual void solve(const double* x0, const double* y0, double* x, double* y, double* s,
+                     pdcs_result* res) = 0;
+  virtual void resume(int64_t max_iter, double* x, double* y, double* s, pdcs_result* res) = 0;
+  virtual void get_state(pdcs_state* st, double* x, double* y, double* x0, double* y0,
+                         double* xs, double* ys) = 0;
+  virtual void set_state(const pdcs_state* st, const double* x, const double* y,
+                         const double* x0, const double* y0, const double* xs,
+                         const double* ys) = 0;
+  virtual void get_iterate(int which, double* x, double* y) = 0;
+  virtual int64_t get_trace(double* out, int64_t cap) = 0;
+  int64_t m = 0, n = 0, nnz = 0;
+};
+
+struct pdcs_handle {
+  int device = 0;
+  SolverBase* solver = nullptr;
+};
+
+namespace pdcs {
+
+template <typename T>
+struct Solver : SolverBase {
+  Arena ar;
+  cudaStream_t st = nullptr;       // this handle's stream (captured graphs run here)
+  cudaStream_t user_st = nullptr;  // caller's stream: work is ordered after it
+  cudaStream_t st2 = nullptr;      // capture of conditional-node bodies
+  pdcs_options opt;
+  int64_t nb = 0;
+  // matrix (scaled) and its transpose
+  int64_t *rp = nullptr, *rpT = nullptr;
+  int32_t *ci = nullptr, *ciT = nullptr;
+  T *vv = nullptr, *vvT = nullptr;
+  SpmvPlan planG, planGT;
+  // problem data
+  T *h = nullptr, *c = nullptr;
+  double *lo = nullptr, *hi = nullptr, *d1 = nullptr, *d2 = nullptr;
+  uint8_t *rk = nullptr, *ck = nullptr;
+  ConeTable rows, cols;
+  int64_t *row_rot = nullptr, *col_rot = nullptr;
+  int64_t nrow_rot = 0, ncol_rot = 0;
+  double eta0 = 1.0, omega0 = 1.0, h1 = 0, c1 = 0, hinf = 0, cinf = 0;
+  // state
+  T *x, *y, *xh, *yh, *x0, *y0, *gx, *gty, *gxh, *gtyh, *gx0, *gty0;
+  T *xb, *yb, *gxb, *gtyb, *xc, *yc, *gxc, *gtyc;
+  double *xs, *ys;
+  double *tm[2], *tn[2], *um[2], *un[2], *px[2], *py[2];
+  double* part = nullptr;
+  double* trace = nullptr;
+  double *obuf_n = nullptr, *obuf_m = nullptr, *obuf_s = nullptr;
+  Ctl* ctl = nullptr;
+  Ctl* hctl = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int64_t trace_rows = 0;
+
+  Prob<T> prob() const {
+    Prob<T> p;
+    p.m = m; p.n = n; p.nb = nb; p.h = h; p.c = c; p.lo = lo; p.hi = hi; p.d1 = d1; p.d2 = d2;
+    p.rk = rk; p.ck = ck;
+    return p;
+  }
+
+  ~Solver() override {
+    if (st) cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (hctl) cudaFreeHost(hctl);
+    if (st2) cudaStreamDestroy(st2);
+    if (st) cudaStreamDestroy(st);
+  }
+
+  // Make this handle's stream wait for work already queued on the caller's stream.
+  void order_after_user() {
+    if (!user_st) return;
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, user_st));
+    CK(cudaStreamWaitEvent(st, ev, 0));
+    CK(cudaEventDestroy(ev));
+  }
+
+  // -------------------------------------------------------------- set-up
+  void setup(int64_t m0, int64_t n0, const int64_t* rp_in, const int32_t* ci_in, const double* v_in,
+             const double* h_in, const double* c_in, int64_t nb_in, const double* lb,
+             const double* ub, const std::vector<pdcs_cone>& rc, const std::vector<pdcs_cone>& cc,
+             const pdcs_options& o, cudaStream_t stream) {
+    user_st = stream;
+    opt = o;
+    m = m0;
+    n = n0;
+    nb = nb_in;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    order_after_user();
+    // ---- row pointer to host for validation and plans
+    std::vector<int64_t> hrp((size_t)m + 1);
+    CK(cudaMemcpy(hrp.data(), rp_in, sizeof(int64_t) * (m + 1), cudaMemcpyDefault));
+    if (hrp[0] != 0) invalid("row_ptr[0] must be 0");
+    for (int64_t r = 0; r < m; ++r)
+      if (hrp[r + 1] < hrp[r]) invalid("row_ptr must be nondecreasing");
+    nnz = hrp[m];
+    if (nnz > INT64_C(2000000000)) invalid("nnz too large");
+    if (nnz > 0 && (!ci_in || !v_in)) invalid("col_idx and val are required");
+    int64_t* drp = ar.alloc<int64_t>(m + 1);
+    int32_t* dci = ar.alloc<int32_t>(nnz);
+    double* dv = ar.alloc<double>(nnz);
+    copy_in(drp, rp_in, m + 1, st);
+    copy_in(dci, ci_in, nnz, st);
+    copy_in(dv, v_in, nnz, st);
+    double* dh = ar.alloc<double>(m);
+    double* dc = ar.alloc<double>(n);
+    copy_in(dh, h_in, m, st);
+    copy_in(dc, c_in, n, st);
+    unsigned int* derr = ar.alloc<unsigned int>(1);
+    CK(cudaMemsetAsync(derr, 0, sizeof(unsigned int), st));
+    if (m > 0) k_validate_csr<<<warp_grid(m), 256, 0, st>>>(drp, dci, dv, m, n, nnz, derr);
+    k_check_finite<<<ew_grid(m), 256, 0, st>>>(dh, m, 16u, derr);
+    k_check_finite<<<ew_grid(n), 256, 0, st>>>(dc, n, 32u, derr);
+    CK(cudaGetLastError());
+    unsigned int herr = 0;
+    CK(cudaMemcpyAsync(&herr, derr, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr & 1u) invalid("row_ptr entries out of range");
+    if (herr & 2u) invalid("column index out of range");
+    if (herr & 4u) invalid("column indices must be strictly increasing within each row");
+    if (herr & 8u) invalid("non-finite matrix value");
+    if (herr & 16u) invalid("non-finite entry in h");
+    if (herr & 32u) invalid("non-finite entry in c");
+    std::vector<double> hlo((size_t)nb), hhi((size_t)nb);
+    if (nb > 0) {
+      if (!lb || !ub) invalid("lb and ub are required when nb > 0");
+      CK(cudaMemcpy(hlo.data(), lb, sizeof(double) * nb, cudaMemcpyDefault));
+      CK(cudaMemcpy(hhi.data(), ub, sizeof(double) * nb, cudaMemcpyDefault));
+      for (int64_t j = 0; j < nb; ++j) {
+        if (std::isnan(hlo[j]) || std::isnan(hhi[j]) || hlo[j] > hhi[j]) invalid("bounds must satisfy lb <= ub");
+        if (hlo[j] == INFINITY || hhi[j] == -INFINITY) invalid("infinite bound on the wrong side");
+      }
+    }
+    // ---- cone layout and RSOC pairs
+    std::vector<int64_t> rpairs, cpairs;
+    std::vector<uint8_t> hrk((size_t)m), hck((size_t)n);
+    std::vector<std::vector<std::pair<int64_t, int32_t>>> rsoc(3), csoc(3);
+    std::vector<int64_t> rexp, cexp;
+    std::vector<uint8_t> rexpd, cexpd;
+    layout(rc, 0, m, true, hrk, rpairs, rsoc, rexp, rexpd);
+    for (int64_t j = 0; j < nb; ++j) hck[j] = CK_BOX;
+    layout(cc, nb, n, false, hck, cpairs, csoc, cexp, cexpd);
+    // ---- RSOC reformulation on rows
+    if (!rpairs.empty()) {
+      merge_row_pairs(hrp, drp, dci, dv, rpairs, m);
+      row_rot = ar.alloc<int64_t>((int64_t)rpairs.size());
+      nrow_rot = (int64_t)rpairs.size();
+      copy_in(row_rot, rpairs.data(), nrow_rot, st);
+      k_rotate_pairs<<<ew_grid(nrow_rot), 256, 0, st>>>(dh, row_rot, nrow_rot);
+    }
+    // ---- transpose
+    std::vector<int64_t> hrpT;
+    int64_t* drpT = nullptr;
+    int32_t* dciT = nullptr;
+    double* dvT = nullptr;
+    transpose(hrp, drp, dci, dv, m, n, hrpT, drpT, dciT, dvT);
+    // ---- RSOC reformulation on columns: row pairs of the transpose
+    if (!cpairs.empty()) {
+      merge_row_pairs(hrpT, drpT, dciT, dvT, cpairs, n);
+      col_rot = ar.alloc<int64_t>((int64_t)cpairs.size());
+      ncol_rot = (int64_t)cpairs.size();
+      copy_in(col_rot, cpairs.data(), ncol_rot, st);
+      k_rotate_pairs<<<ew_grid(ncol_rot), 256, 0, st>>>(dc, col_rot, ncol_rot);
+      ar.release(drp); ar.release(dci); ar.release(dv);
+      transpose(hrpT, drpT, dciT, dvT, n, m, hrp, drp, dci, dv);
+    }
+    nnz = hrp[m];
+    // ---- scaling (Ruiz + Pock-Chambolle), Sec. 2.6
+    d1 = ar.alloc<double>(m);
+    d2 = ar.alloc<double>(n);
+    k_fill<double><<<ew_grid(m), 256, 0, st>>>(d1, m, 1.0);
+    k_fill<double><<<ew_grid(n), 256, 0, st>>>(d2, n, 1.0);
+    if (opt.use_preconditioner && m > 0) {
+      double* rn = ar.alloc<double>(m);
+      double* cn = ar.alloc<double>(n);
+      for (int it = 0; it < opt.ruiz_iters; ++it) {
+        k_row_norms<<<warp_grid(m), 256, 0, st>>>(drp, dci, dv, m, d1, d2, 0, 0, 1.0, rn);
+        k_row_norms<<<warp_grid(n), 256, 0, st>>>(drpT, dciT, dvT, n, d2, d1, 1, 0, 1.0, cn);
+        k_scale_update<<<ew_grid(m), 256, 0, st>>>(d1, rn, m);
+        k_scale_update<<<ew_grid(n), 256, 0, st>>>(d2, cn, n);
+      }
+      if (opt.pc_alpha >= 0) {
+        k_row_norms<<<warp_grid(m), 256, 0, st>>>(drp, dci, dv, m, d1, d2, 0, 1, opt.pc_alpha, rn);
+        k_row_norms<<<warp_grid(n), 256, 0, st>>>(drpT, dciT, dvT, n, d2, d1, 1, 1, 2.0 - opt.pc_alpha, cn);
+        k_scale_update<<<ew_grid(m), 256, 0, st>>>(d1, rn, m);
+        k_scale_update<<<ew_grid(n), 256, 0, st>>>(d2, cn, n);
+      }
+      CK(cudaStreamSynchronize(st));
+      ar.release(rn);
+      ar.release(cn);
+    }
+    unsigned long long* amax = ar.alloc<unsigned long long>(1);
+    CK(cudaMemsetAsync(amax, 0, sizeof(unsigned long long), st));
+    rp = drp; ci = dci; rpT = drpT; ciT = dciT;
+    vv = ar.alloc<T>(nnz);
+    vvT = ar.alloc<T>(nnz);
+    if (m > 0) {
+      k_apply_scale<T><<<warp_grid(m), 256, 0, st>>>(drp, dci, dv, m, d1, d2, 0, vv, amax);
+      k_apply_scale<T><<<warp_grid(n), 256, 0, st>>>(drpT, dciT, dvT, n, d2, d1, 1, vvT, nullptr);
+    }
+    double* sh_ = ar.alloc<double>(m);
+    double* sc_ = ar.alloc<double>(n);
+    k_scale_vec<<<ew_grid(m), 256, 0, st>>>(dh, d1, m, 0, sh_);
+    k_scale_vec<<<ew_grid(n), 256, 0, st>>>(dc, d2, n, 0, sc_);
+    h = ar.alloc<T>(m);
+    c = ar.alloc<T>(n);
+    k_convert<double, T><<<ew_grid(m), 256, 0, st>>>(sh_, h, m);
+    k_convert<double, T><<<ew_grid(n), 256, 0, st>>>(sc_, c, n);
+    lo = ar.alloc<double>(nb);
+    hi = ar.alloc<double>(nb);
+    if (nb > 0) {
+      double* tmp = ar.alloc<double>(nb);
+      copy_in(tmp, hlo.data(), nb, st);
+      k_scale_vec<<<ew_grid(nb), 256, 0, st>>>(tmp, d2, nb, 1, lo);
+      CK(cudaStreamSynchronize(st));
+      copy_in(tmp, hhi.data(), nb, st);
+      k_scale_vec<<<ew_grid(nb), 256, 0, st>>>(tmp, d2, nb, 1, hi);
+      CK(cudaStreamSynchronize(st));
+      ar.release(tmp);
+    }
+    double* nrm = ar.alloc<double>(8);
+    k_vec_norms<<<1, 1024, 0, st>>>(sh_, m, d1, nrm);
+    k_vec_norms<<<1, 1024, 0, st>>>(sc_, n, d2, nrm + 4);
+    CK(cudaGetLastError());
+    double hn[8];
+    unsigned long long hamax = 0;
+    CK(cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hamax, amax, sizeof(hamax), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h1 = hn[0]; hinf = hn[2]; c1 = hn[4]; cinf = hn[6];
+    const double nh2 = std::sqrt(hn[1]), nc2 = std::sqrt(hn[5]);
+    omega0 = (nc2 > 1e-10 && nh2 > 1e-10) ? nc2 / nh2 : 1.0;  // Sec. 2.5
+    double gmax;
+    std::memcpy(&gmax, &hamax, sizeof(double));
+    eta0 = gmax > 0 ? 1.0 / gmax : 1.0;  // Algorithm 1: 1 / ||G||_inf
+    ar.release(dv); ar.release(dvT); ar.release(dh); ar.release(dc);
+    ar.release(sh_); ar.release(sc_); ar.release(nrm); ar.release(amax); ar.release(derr);
+    // ---- kinds, cone tables, plans
+    rk = ar.alloc<uint8_t>(m);
+    ck = ar.alloc<uint8_t>(n);
+    copy_in(rk, hrk.data(), m, st);
+    copy_in(ck, hck.data(), n, st);
+    fill_table(rows, rsoc, rexp, rexpd);
+    fill_table(cols, csoc, cexp, cexpd);
+    planG = build_plan(hrp, ar, st);
+    planGT = build_plan(hrpT, ar, st);
+    alloc_state();
+    capture();
+  }
+
+  // Per-element kinds and cone tables from an ordered cone list starting at off.
+  void layout(const std::vector<pdcs_cone>& cl, int64_t off, int64_t end, bool is_row,
+              std::vector<uint8_t>& kind, std::vector<int64_t>& pairs,
+              std::vector<std::vector<std::pair<int64_t, int32_t>>>& soc, std::vector<int64_t>& ex,
+              std::vector<uint8_t>& exd) {
+    for (const auto& cn : cl) {
+      const int64_t d = cn.dim;
+      if (off + d > end) invalid("cone dimensions exceed the vector length");
+      switch (cn.type) {
+        case PDCS_CONE_ZERO:
+          for (int64_t i = 0; i < d; ++i) kind[off + i] = is_row ? (uint8_t)RK_FREE : (uint8_t)CK_ZERO;
+          break;
+        case PDCS_CONE_NONNEG:
+          for (int64_t i = 0; i < d; ++i) kind[off + i] = is_row ? (uint8_t)RK_NONNEG : (uint8_t)CK_NONNEG;
+          break;
+        case PDCS_CONE_RSOC:
+        case PDCS_CONE_SOC: {
+          if (cn.type == PDCS_CONE_RSOC) pairs.push_back(off);
+          for (int64_t i = 0; i < d; ++i) kind[off + i] = is_row ? (uint8_t)RK_SOC : (uint8_t)CK_SOC;
+          if (d > kSocTierMax[2])
+            throw Fail{PDCS_ERR_UNSUPPORTED, "SOC block dimension above 8192 is not supported"};
+          const int tier = d <= kSocTierMax[0] ? 0 : (d <= kSocTierMax[1] ? 1 : 2);
+          soc[tier].push_back({off, (int32_t)d});
+          break;
+        }
+        case PDCS_CONE_EXP:
+        case PDCS_CONE_DUAL_EXP: {
+          const bool de = cn.type == PDCS_CONE_DUAL_EXP;
+          for (int64_t i = 0; i < 3; ++i)
+            kind[off + i] = is_row ? (uint8_t)(de ? RK_DEXP : RK_EXP) : (uint8_t)(de ? CK_DEXP : CK_EXP);
+          ex.push_back(off);
+          exd.push_back(de ? 1 : 0);
+          break;
+        }
+        default:
+          invalid("unknown cone type");
+      }
+      off += d;
+    }
+  }
+
+  void fill_table(ConeTable& t, const std::vector<std::vector<std::pair<int64_t, int32_t>>>& soc,
+                  const std::vector<int64_t>& ex, const std::vector<uint8_t>& exd) {
+    for (int k = 0; k < 3; ++k) {
+      t.nsoc[k] = (int64_t)soc[k].size();
+      if (t.nsoc[k] == 0) continue;
+      std::vector<int64_t> s;
+      std::vector<int32_t> d;
+      for (auto& pr : soc[k]) { s.push_back(pr.first); d.push_back(pr.second); }
+      t.soc_s[k] = ar.alloc<int64_t>(t.nsoc[k]);
+      t.soc_d[k] = ar.alloc<int32_t>(t.nsoc[k]);
+      copy_in(t.soc_s[k], s.data(), t.nsoc[k], st);
+      copy_in(t.soc_d[k], d.data(), t.nsoc[k], st);
+      CK(cudaStreamSynchronize(st));
+    }
+    t.nexp = (int64_t)ex.size();
+    if (t.nexp > 0) {
+      t.exp_s = ar.alloc<int64_t>(t.nexp);
+      t.exp_isd = ar.alloc<uint8_t>(t.nexp);
+      copy_in(t.exp_s, ex.data(), t.nexp, st);
+      copy_in(t.exp_isd, exd.data(), t.nexp, st);
+    }
+    CK(cudaStreamSynchronize(st));
+  }
+
+  // Merge each listed row pair of a CSR (host row pointer hrp, device arrays)
+  // into ((r_s + r_{s+1})/sqrt2, (r_s - r_{s+1})/sqrt2); replaces the arrays.
+  void merge_row_pairs(std::vector<int64_t>& hrp, int64_t*& drp, int32_t*& dci, double*& dv,
+                       const std::vector<int64_t>& pairs, int64_t rws) {
+    const int64_t np = (int64_t)pairs.size();
+    int64_t* dp = ar.alloc<int64_t>(np);
+    int64_t* dlen = ar.alloc<int64_t>(np);
+    copy_in(dp, pairs.data(), np, st);
+    k_pair_union_len<<<ew_grid(np), 256, 0, st>>>(drp, dci, dp, np, dlen);
+    CK(cudaGetLastError());
+    std::vector<int64_t> len = to_host(dlen, np, st);
+    std::vector<int64_t> rl((size_t)rws);
+    for (int64_t r = 0; r < rws; ++r) rl[r] = hrp[r + 1] - hrp[r];
+    std::vector<int64_t> pair_of((size_t)rws, -1);
+    for (int64_t b = 0; b < np; ++b) {
+      rl[pairs[b]] = len[b];
+      rl[pairs[b] + 1] = len[b];
+      pair_of[pairs[b]] = b;
+      pair_of[pairs[b] + 1] = -2;
+    }
+    std::vector<int64_t> nrp((size_t)rws + 1, 0);
+    for (int64_t r = 0; r < rws; ++r) nrp[r + 1] = nrp[r] + rl[r];
+    const int64_t nnz2 = nrp[rws];
+    int64_t* dnrp = ar.alloc<int64_t>(rws + 1);
+    int32_t* dnci = ar.alloc<int32_t>(nnz2);
+    double* dnv = ar.alloc<double>(nnz2);
+    int64_t* dpo = ar.alloc<int64_t>(rws);
+    copy_in(dnrp, nrp.data(), rws + 1, st);
+    copy_in(dpo, pair_of.data(), rws, st);
+    k_pair_merge<<<warp_grid(rws), 256, 0, st>>>(drp, dci, dv, rws, dnrp, dnci, dnv, dpo);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    ar.release(drp); ar.release(dci); ar.release(dv); ar.release(dp); ar.release(dlen); ar.release(dpo);
+    drp = dnrp; dci = dnci; dv = dnv;
+    hrp.swap(nrp);
+  }
+
+  // CSR (rws x cls) -> CSR of the transpose, entries sorted by row index.
+  void transpose(const std::vector<int64_t>& hrp_, const int64_t* drp, const int32_t* dci,
+                 const double* dv, int64_t rws, int64_t cls, std::vector<int64_t>& hrpT,
+                 int64_t*& drpT, int32_t*& dciT, double*& dvT) {
+    const int64_t nz = hrp_[rws];
+    unsigned long long* cnt = ar.alloc<unsigned long long>(cls);
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * std::max<int64_t>(cls, 1), st));
+    if (nz > 0) k_col_count<<<ew_grid(nz), 256, 0, st>>>(dci, nz, cnt);
+    CK(cudaGetLastError());
+    std::vector<unsigned long long> hc = to_host(cnt, cls, st);
+    hrpT.assign((size_t)cls + 1, 0);
+    for (int64_t j = 0; j < cls; ++j) hrpT[j + 1] = hrpT[j] + (int64_t)hc[j];
+    drpT = ar.alloc<int64_t>(cls + 1);
+    dciT = ar.alloc<int32_t>(nz);
+    dvT = ar.alloc<double>(nz);
+    copy_in(drpT, hrpT.data(), cls + 1, st);
+    copy_in((int64_t*)cnt, hrpT.data(), cls, st);  // cursors start at the segment offsets
+    if (rws > 0) k_transpose_scatter<<<warp_grid(rws), 256, 0, st>>>(drp, dci, dv, rws, cnt, dciT, dvT);
+    if (cls > 0) k_segment_sort<<<(unsigned)std::min<int64_t>(cls, 148 * 32), 256, 0, st>>>(drpT, dciT, dvT, cls);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    ar.release(cnt);
+  }
+
+  void alloc_state() {
+    T** vn[] = {&x, &xh, &x0, &gty, &gtyh, &gty0, &xb, &gtyb, &xc, &gtyc};
+    for (auto p : vn) *p = ar.alloc<T>(n);
+    T** vm[] = {&y, &yh, &y0, &gx, &gxh, &gx0, &yb, &gxb, &yc, &gxc};
+    for (auto p : vm) *p = ar.alloc<T>(m);
+    xs = ar.alloc<double>(n);
+    ys = ar.alloc<double>(m);
+    for (int k = 0; k < 2; ++k) {
+      tm[k] = ar.alloc<double>(m); um[k] = ar.alloc<double>(m); py[k] = ar.alloc<double>(m);
+      tn[k] = ar.alloc<double>(n); un[k] = ar.alloc<double>(n); px[k] = ar.alloc<double>(n);
+    }
+    const int g = ew_grid(std::max(m, n));
+    part = ar.alloc<double>((int64_t)g * kStatK * 2 + 64);
+    ctl = ar.alloc<Ctl>(1);
+    CK(cudaMallocHost(&hctl, sizeof(Ctl)));
+    std::memset(hctl, 0, sizeof(Ctl));
+    obuf_n = ar.alloc<double>(n);
+    obuf_m = ar.alloc<double>(m);
+    obuf_s = ar.alloc<double>(m);
+    if (opt.trace_capacity > 0) trace = ar.alloc<double>((int64_t)opt.trace_capacity * PDCS_TRACE_FIELDS);
+  }
+
+  // ------------------------------------------------------- graph capture
+  cudaGraph_t add_while(cudaStream_t s, cudaGraphConditionalHandle hnd) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hnd;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return p.conditional.phGraph_out[0];
+  }
+
+  cudaGraphConditionalHandle new_handle(cudaStream_t s) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle hnd;
+    CK(cudaGraphConditionalHandleCreate(&hnd, g, 0, cudaGraphCondAssignDefault));
+    return hnd;
+  }
+
+  PointRef<T> pz() const { return PointRef<T>{x, y, gx, gty}; }
+  PointRef<T> pzb() const { return PointRef<T>{xb, yb, gxb, gtyb}; }
+
+  void rec_attempt(cudaStream_t s, cudaGraphConditionalHandle hA) {
+    const Prob<T> p = prob();
+    const int gn = ew_grid(n), gm = ew_grid(m), gmx = ew_grid(std::max(m, n));
+    k_primal<T><<<gn, kEwThreads, 0, s>>>(p, ctl, x, gty, xh);
+    project<T>(cols, xh, xh, 1, d2, 1, 0, &ctl->g_attempt, nullptr, s);
+    launch_spmv<T>(planG, rp, ci, vv, xh, gxh, &ctl->g_attempt, s);
+    k_dual<T><<<gm, kEwThreads, 0, s>>>(p, ctl, y, gxh, gx, yh);
+    project<T>(rows, yh, yh, 1, d1, 1, 1, &ctl->g_attempt, nullptr, s);
+    k_step<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, xh, y, yh, gxh, gx, part);
+    launch_spmv<T>(planGT, rpT, ciT, vvT, yh, gtyh, &ctl->g_accept, s);
+    const PointRef<T> ph{xh, yh, gxh, gtyh};
+    const TmpRef t0{tm[0], tn[0], nullptr, nullptr};
+    k_res_prep<T><<<dim3(gmx, 1), kEwThreads, 0, s>>>(p, &ctl->g_accept, ph, ph, t0, t0);
+    project<double>(rows, tm[0], tm[0], 1, d1, 0, 0, &ctl->g_accept, nullptr, s);
+    project<double>(cols, tn[0], tn[0], 1, d2, 0, 1, &ctl->g_accept, nullptr, s);
+    k_point_stats<T, false><<<gmx, kEwThreads, 0, s>>>(p, ctl, &ctl->g_accept, 0, ph, nullptr, nullptr, t0, part);
+    k_halpern<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, y, gx, gty, xh, yh, gxh, gtyh, x0, y0, gx0, gty0, xs, ys, trace);
+    k_loop_ctl<<<1, 1, 0, s>>>(ctl, hA);
+  }
+
+  void rec_check_stats(cudaStream_t s) {
+    const Prob<T> p = prob();
+    const int gmx = ew_grid(std::max(m, n));
+    int* g = &ctl->g_check;
+    k_average<T><<<gmx, kEwThreads, 0, s>>>(n, m, ctl, xs, ys, xb, yb);
+    launch_spmv<T>(planG, rp, ci, vv, xb, gxb, g, s);
+    launch_spmv<T>(planGT, rpT, ciT, vvT, yb, gtyb, g, s);
+    const TmpRef ta{tm[0], tn[0], um[0], un[0]}, tb{tm[1], tn[1], um[1], un[1]};
+    k_res_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, g, pz(), pzb(), ta, tb);
+    project<double>(rows, tm[0], tm[1], 2, d1, 0, 0, g, g, s);
+    project<double>(cols, tn[0], tn[1], 2, d2, 0, 1, g, g, s);
+    project<double>(rows, um[0], um[1], 2, nullptr, 0, 0, g, g, s);
+    project<double>(cols, un[0], un[1], 2, nullptr, 0, 1, g, g, s);
+    k_point_stats<T, true><<<gmx, kEwThreads, 0, s>>>(p, ctl, g, 1, pz(), x0, y0, ta, part);
+    k_point_stats<T, true><<<gmx, kEwThreads, 0, s>>>(p, ctl, g, 2, pzb(), x0, y0, tb, part + (int64_t)gmx * kStatK);
+  }
+
+  void rec_probe(cudaStream_t s, cudaGraphConditionalHandle hB) {
+    const Prob<T> p = prob();
+    const int gmx = ew_grid(std::max(m, n));
+    k_probe_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pz(), pzb(), px[0], py[0], px[1], py[1]);
+    project<double>(cols, px[0], px[1], 2, d2, 1, 0, &ctl->bs[0].active, &ctl->bs[1].active, s);
+    project<double>(rows, py[0], py[1], 2, d1, 1, 1, &ctl->bs[0].active, &ctl->bs[1].active, s);
+    k_probe_reduce<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pz(), pzb(), px[0], py[0], px[1], py[1], part, hB);
+  }
+
+  void rec_check_end(cudaStream_t s) {
+    const int gmx = ew_grid(std::max(m, n));
+    k_check_decide<<<1, 1, 0, s>>>(ctl, trace);
+    k_cand_copy<T><<<gmx, kEwThreads, 0, s>>>(n, m, ctl, pz(), pzb(), xc, yc, gxc, gtyc, x0, y0, x, y, xs, ys);
+    launch_spmv<T>(planG, rp, ci, vv, x0, gx0, &ctl->g_restart, s);
+    launch_spmv<T>(planGT, rpT, ciT, vvT, y0, gty0, &ctl->g_restart, s);
+    k_copy_products<T><<<gmx, kEwThreads, 0, s>>>(n, m, &ctl->g_restart, gx0, gty0, gx, gty);
+    k_check_end<<<1, 1, 0, s>>>(ctl);
+  }
+
+  void capture() {
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    cudaGraphConditionalHandle hA = new_handle(st);
+    cudaGraphConditionalHandle hB = new_handle(st);
+    k_period_begin<<<1, 1, 0, st>>>(ctl, hA);
+    cudaGraph_t bodyA = add_while(st, hA);
+    CK(cudaStreamBeginCaptureToGraph(st2, bodyA, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    rec_attempt(st2, hA);
+    CK(cudaStreamEndCapture(st2, &bodyA));
+    rec_check_stats(st);
+    k_bisect_init<<<1, 1, 0, st>>>(ctl, hB);
+    cudaGraph_t bodyB = add_while(st, hB);
+    CK(cudaStreamBeginCaptureToGraph(st2, bodyB, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    rec_probe(st2, hB);
+    CK(cudaStreamEndCapture(st2, &bodyB));
+    rec_check_end(st);
+    CK(cudaStreamEndCapture(st, &graph));
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+  }
+
+  // ---------------------------------------------------------------- solve
+  void init_ctl() {
+    Ctl& c0 = *hctl;
+    std::memset(&c0, 0, sizeof(Ctl));
+    c0.eta = eta0; c0.eta_hat = eta0; c0.eta_acc = eta0; c0.omega = omega0; c0.omega0 = omega0;
+    c0.eta0 = eta0;
+    c0.status = kRunning;
+    c0.h1 = h1; c0.c1 = c1; c0.hinf = hinf; c0.cinf = cinf;
+    c0.rel_tol = opt.rel_tol; c0.abs_tol = opt.abs_tol; c0.bisect_tol = opt.bisect_rel_tol;
+    c0.check_freq = std::max<int64_t>(1, opt.check_freq);
+    c0.max_iter = opt.max_iter;
+    c0.method = opt.method;
+    c0.adaptive_restart = opt.use_adaptive_restart;
+    c0.require_abs = opt.require_abs;
+    c0.trace_cap = trace ? opt.trace_capacity : 0;
+    c0.guard_cap = (int)std::min<int64_t>(4 * c0.check_freq + 16, 1 << 20);
+    c0.probe_cap = 256;
+  }
+
+  void upload_ctl() { CK(cudaMemcpyAsync(ctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, st)); }
+
+  void start_point(const double* x0u, const double* y0u) {
+    const int gn = ew_grid(n), gm = ew_grid(m);
+    if (x0u) {
+      copy_in(obuf_n, x0u, n, st);
+      if (ncol_rot) k_rotate_pairs<<<ew_grid(ncol_rot), 256, 0, st>>>(obuf_n, col_rot, ncol_rot);
+      k_warm<T><<<gn, 256, 0, st>>>(x, obuf_n, d2, n);
+    } else {
+      k_fill<T><<<gn, 256, 0, st>>>(x, n, 0.0);
+    }
+    if (y0u) {
+      copy_in(obuf_m, y0u, m, st);
+      if (nrow_rot) k_rotate_pairs<<<ew_grid(nrow_rot), 256, 0, st>>>(obuf_m, row_rot, nrow_rot);
+      k_warm<T><<<gm, 256, 0, st>>>(y, obuf_m, d1, m);
+    } else {
+      k_fill<T><<<gm, 256, 0, st>>>(y, m, 0.0);
+    }
+    k_convert<T, T><<<gn, 256, 0, st>>>(x, x0, n);
+    k_convert<T, T><<<gm, 256, 0, st>>>(y, y0, m);
+    k_fill<double><<<gn, 256, 0, st>>>(xs, n, 0.0);
+    k_fill<double><<<gm, 256, 0, st>>>(ys, m, 0.0);
+    refresh_products();
+  }
+
+  // G x, G^T y, G x0, G^T y0 from the current vectors.
+  void refresh_products() {
+    launch_spmv<T>(planG, rp, ci, vv, x, gx, nullptr, st);
+    launch_spmv<T>(planGT, rpT, ciT, vvT, y, gty, nullptr, st);
+    launch_spmv<T>(planG, rp, ci, vv, x0, gx0, nullptr, st);
+    launch_spmv<T>(planGT, rpT, ciT, vvT, y0, gty0, nullptr, st);
+    CK(cudaGetLastError());
+  }
+
+  void solve(const double* x0u, const double* y0u, double* xo, double* yo, double* so,
+             pdcs_result* res) override {
+    const auto t0 = std::chrono::steady_clock::now();
+    order_after_user();
+    init_ctl();
+    upload_ctl();
+    start_point(x0u, y0u);
+    if (trace) CK(cudaMemsetAsync(trace, 0, sizeof(double) * (size_t)opt.trace_capacity * PDCS_TRACE_FIELDS, st));
+    run(xo, yo, so, res, t0);
+  }
+
+  void resume(int64_t max_iter, double* xo, double* yo, double* so, pdcs_result* res) override {
+    const auto t0 = std::chrono::steady_clock::now();
+    order_after_user();
+    CK(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    hctl->max_iter = max_iter > 0 ? max_iter : opt.max_iter;
+    hctl->status = hctl->iter >= hctl->max_iter ? 1 : kRunning;
+    hctl->period_done = 0;
+    hctl->have_cand = 0;
+    hctl->g_attempt = hctl->g_accept = hctl->g_check = hctl->g_restart = 0;
+    upload_ctl();
+    if (hctl->status != kRunning) {
+      finish(hctl->status, xo, yo, so, res, t0);
+      return;
+    }
+    run(xo, yo, so, res, t0);
+  }
+
+  void run(double* xo, double* yo, double* so, pdcs_result* res,
+           std::chrono::steady_clock::time_point t0) {
+    int status = kRunning;
+    while (true) {
+      CK(cudaGraphLaunch(exec, st));
+      CK(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      status = hctl->status;
+      if (opt.verbose)
+        fprintf(stderr, "[pdcs] iter %lld kbar %lld restarts %lld eta %.3e omega %.3e maxErr %.3e\n",
+                hctl->iter, hctl->kbar, hctl->restarts, hctl->eta_acc, hctl->omega, hctl->st[0].max_err);
+      if (status != kRunning) break;
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > opt.time_limit) {
+        status = 6;
+        break;
+      }
+    }
+    finish(status, xo, yo, so, res, t0);
+  }
+
+  void finish(int status, double* xo, double* yo, double* so, pdcs_result* res,
+              std::chrono::steady_clock::time_point t0) {
+    const Prob<T> p = prob();
+    const int gmx = ew_grid(std::max(m, n));
+    const bool cand = hctl->have_cand != 0;
+    const PointRef<T> pr = cand ? PointRef<T>{xc, yc, gxc, gtyc} : pz();
+    // final statistics of the returned point (slot 3); g_check serves as an
+    // always-on gate here (no graph runs until the next call re-initialises it)
+    int* one = &ctl->g_check;
+    const int hone = 1;
+    CK(cudaMemcpyAsync(one, &hone, sizeof(int), cudaMemcpyHostToDevice, st));
+    const TmpRef ta{tm[0], tn[0], um[0], un[0]};
+    k_res_prep<T><<<dim3(gmx, 1), kEwThreads, 0, st>>>(p, one, pr, pr, ta, ta);
+    project<double>(rows, tm[0], tm[0], 1, d1, 0, 0, one, nullptr, st);
+    project<double>(cols, tn[0], tn[0], 1, d2, 0, 1, one, nullptr, st);
+    project<double>(rows, um[0], um[0], 1, nullptr, 0, 0, one, nullptr, st);
+    project<double>(cols, un[0], un[0], 1, nullptr, 0, 1, one, nullptr, st);
+    k_point_stats<T, true><<<gmx, kEwThreads, 0, st>>>(p, ctl, one, 3, pr, nullptr, nullptr, ta, part);
+    k_unscale<T><<<gmx, 256, 0, st>>>(p, pr.x, pr.y, pr.gx, obuf_n, obuf_m, obuf_s);
+    if (ncol_rot) k_rotate_pairs<<<ew_grid(ncol_rot), 256, 0, st>>>(obuf_n, col_rot, ncol_rot);
+    if (nrow_rot) {
+      k_rotate_pairs<<<ew_grid(nrow_rot), 256, 0, st>>>(obuf_m, row_rot, nrow_rot);
+      k_rotate_pairs<<<ew_grid(nrow_rot), 256, 0, st>>>(obuf_s, row_rot, nrow_rot);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    if (xo) CK(cudaMemcpyAsync(xo, obuf_n, sizeof(double) * n, cudaMemcpyDefault, st));
+    if (yo && m) CK(cudaMemcpyAsync(yo, obuf_m, sizeof(double) * m, cudaMemcpyDefault, st));
+    if (so && m) CK(cudaMemcpyAsync(so, obuf_s, sizeof(double) * m, cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+    trace_rows = std::min<int64_t>(hctl->iter, opt.trace_capacity);
+    if (res) {
+      const PointStats& s3 = hctl->st[3];
+      res->exit_code = status;
+      res->pobj = s3.pobj;
+      res->dobj = s3.dobj;
+      res->err_rel_p = s3.inf_rel_p;
+      res->err_rel_d = s3.inf_rel_d;
+      res->err_rel_gap = s3.inf_rel_gap;
+      res->err_abs_p = s3.inf_abs_p;
+      res->err_abs_d = s3.inf_abs_d;
+      res->err_abs_gap = s3.gap;
+      res->iters = hctl->iter;
+      res->attempts = hctl->kbar;
+      res->restarts = hctl->restarts;
+      res->solve_time_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+  }
+
+  // ------------------------------------------------------ state access
+  void to_user(const T* src, double* buf, double* dst, int64_t cnt) {
+    if (!dst || cnt == 0) return;
+    k_convert<T, double><<<ew_grid(cnt), 256, 0, st>>>(src, buf, cnt);
+    CK(cudaMemcpyAsync(dst, buf, sizeof(double) * cnt, cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+  }
+
+  void get_state(pdcs_state* s, double* xo, double* yo, double* x0o, double* y0o, double* xso,
+                 double* yso) override {
+    CK(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (s) {
+      const Ctl& c0 = *hctl;
+      s->iter = c0.iter; s->kbar = c0.kbar; s->k = c0.k; s->period = c0.period;
+      s->restarts = c0.restarts; s->eta_hat = c0.eta; s->eta_last = c0.eta_acc;
+      s->omega = c0.omega; s->wsum = c0.wsum; s->has_ref = c0.has_ref; s->has_prev = c0.has_prev;
+      s->ref_rho = c0.ref_rho; s->ref_abs_p = c0.ref_ep; s->ref_abs_d = c0.ref_ed;
+      s->ref_abs_gap = c0.ref_eg; s->prev_rho = c0.prev_rho; s->prev_abs_p = c0.prev_ep;
+      s->prev_abs_d = c0.prev_ed; s->prev_abs_gap = c0.prev_eg;
+    }
+    to_user(x, obuf_n, xo, n);
+    to_user(y, obuf_m, yo, m);
+    to_user(x0, obuf_n, x0o, n);
+    to_user(y0, obuf_m, y0o, m);
+    if (xso) CK(cudaMemcpyAsync(xso, xs, sizeof(double) * n, cudaMemcpyDefault, st));
+    if (yso && m) CK(cudaMemcpyAsync(yso, ys, sizeof(double) * m, cudaMemcpyDefault, st));
+    CK(cudaStreamSynchronize(st));
+  }
+
+  void set_state(const pdcs_state* s, const double* xi, const double* yi, const double* x0i,
+                 const double* y0i, const double* xsi, const double* ysi) override {
+    order_after_user();
+    init_ctl();
+    Ctl& c0 = *hctl;
+    c0.iter = s->iter; c0.kbar = s->kbar; c0.k = s->k; c0.period = s->period;
+    c0.restarts = s->restarts; c0.eta = s->eta_hat; c0.eta_hat = s->eta_hat;
+    c0.eta_acc = s->eta_last; c0.omega = s->omega; c0.wsum = s->wsum;
+    c0.has_ref = s->has_ref; c0.has_prev = s->has_prev;
+    c0.ref_rho = s->ref_rho; c0.ref_ep = s->ref_abs_p; c0.ref_ed = s->ref_abs_d;
+    c0.ref_eg = s->ref_abs_gap; c0.prev_rho = s->prev_rho; c0.prev_ep = s->prev_abs_p;
+    c0.prev_ed = s->prev_abs_d; c0.prev_eg = s->prev_abs_gap;
+    upload_ctl();
+    const int gn = ew_grid(n), gm = ew_grid(m);
+    T* dn[2] = {x, x0};
+    const double* sn[2] = {xi, x0i};
+    T* dm[2] = {y, y0};
+    const double* sm[2] = {yi, y0i};
+    for (int k = 0; k < 2; ++k) {
+      copy_in(obuf_n, sn[k], n, st);
+      k_convert<double, T><<<gn, 256, 0, st>>>(obuf_n, dn[k], n);
+      copy_in(obuf_m, sm[k], m, st);
+      k_convert<double, T><<<gm, 256, 0, st>>>(obuf_m, dm[k], m);
+      CK(cudaStreamSynchronize(st));
+    }
+    copy_in(xs, xsi, n, st);
+    copy_in(ys, ysi, m, st);
+    refresh_products();
+    CK(cudaStreamSynchronize(st));
+  }
+
+  void get_iterate(int which, double* xo, double* yo) override {
+    if (which == 3) {
+      if (xo) CK(cudaMemcpyAsync(xo, d2, sizeof(double) * n, cudaMemcpyDefault, st));
+      if (yo && m) CK(cudaMemcpyAsync(yo, d1, sizeof(double) * m, cudaMemcpyDefault, st));
+      CK(cudaStreamSynchronize(st));
+      return;
+    }
+    const T* a = which == 0 ? x : (which == 1 ? x0 : xh);
+    const T* b = which == 0 ? y : (which == 1 ? y0 : yh);
+    to_user(a, obuf_n, xo, n);
+    to_user(b, obuf_m, yo, m);
+  }
+
+  int64_t get_trace(double* out, int64_t cap) override {
+    const int64_t rows_ = std::min(cap, trace_rows);
+    if (rows_ > 0 && trace)
+      CK(cudaMemcpy(out, trace, sizeof(double) * rows_ * PDCS_TRACE_FIELDS, cudaMemcpyDeviceToHost));
+    return std::max<int64_t>(rows_, 0);
+  }
+};
+
+}  // namespace pdcs
+
+// ----------------------------------------------------------------- C ABI
+extern "C" {
+
+void pdcs_default_options(pdcs_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->rel_tol = 1e-6;
+  o->abs_tol = 1e-6;
+  o->time_limit = 1000.0;
+  o->max_iter = INT64_MAX;
+  o->use_preconditioner = 1;
+  o->ruiz_iters = 10;
+  o->pc_alpha = 1.0;
+  o->method = 0;
+  o->use_adaptive_restart = 1;
+  o->check_freq = 64;
+  o->precision = 0;
+  o->require_abs = 0;
+  o->bisect_rel_tol = 1e-6;
+  o->verbose = 0;
+  o->trace_capacity = 0;
+}
+
+const char* pdcs_last_error(void) { return g_last_error.c_str(); }
+
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+static int check_cones(const pdcs_cone* cl, int64_t k, int64_t expect, const char* what) {
+  int64_t sum = 0;
+  for (int64_t i = 0; i < k; ++i) {
+    const pdcs_cone& c = cl[i];
+    if (c.type < 0 || c.type > 5 || c.dim < 1) return fail(PDCS_ERR_INVALID, std::string("bad ") + what + " cone");
+    if ((c.type == PDCS_CONE_EXP || c.type == PDCS_CONE_DUAL_EXP) && c.dim != 3)
+      return fail(PDCS_ERR_INVALID, "exponential cone blocks have dimension 3");
+    if (c.type == PDCS_CONE_RSOC && c.dim < 2) return fail(PDCS_ERR_INVALID, "RSOC needs dim >= 2");
+    sum += c.dim;
+  }
+  if (sum != expect)
+    return fail(PDCS_ERR_INVALID, std::string(what) + (what[0] == 'r' ? " cone dimensions must sum to m"
+                                                                       : " cone dimensions must sum to n - nb"));
+  return PDCS_OK;
+}
+
+int pdcs_setup(pdcs_handle** out, int64_t m, int64_t n, const int64_t* row_ptr,
+               const int32_t* col_idx, const double* val, const double* h, const double* c,
+               int64_t nb, const double* lb, const double* ub, const pdcs_cone* row_cones,
+               int64_t n_row_cones, const pdcs_cone* col_cones, int64_t n_col_cones,
+               const pdcs_options* opt, void* cuda_stream) {
+  if (!out) return fail(PDCS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (m < 0 || n < 1) return fail(PDCS_ERR_INVALID, "need m >= 0 and n >= 1");
+  if (nb < 0 || nb > n) return fail(PDCS_ERR_INVALID, "need 0 <= nb <= n");
+  if (!row_ptr || (m > 0 && !h) || !c) return fail(PDCS_ERR_INVALID, "row_ptr, h and c are required");
+  if (n_row_cones < 0 || n_col_cones < 0) return fail(PDCS_ERR_INVALID, "negative cone count");
+  if ((n_row_cones > 0 && !row_cones) || (n_col_cones > 0 && !col_cones))
+    return fail(PDCS_ERR_INVALID, "cone list is NULL");
+  int rc_ = check_cones(row_cones, n_row_cones, m, "row");
+  if (rc_ != PDCS_OK) return rc_;
+  rc_ = check_cones(col_cones, n_col_cones, n - nb, "column");
+  if (rc_ != PDCS_OK) return rc_;
+  pdcs_options o;
+  if (opt) o = *opt; else pdcs_default_options(&o);
+  if (o.precision != 0 && o.precision != 1) return fail(PDCS_ERR_INVALID, "precision must be 0 or 1");
+  if (o.check_freq < 1) return fail(PDCS_ERR_INVALID, "check_freq must be >= 1");
+  if (o.method != 0 && o.method != 1) return fail(PDCS_ERR_INVALID, "method must be 0 or 1");
+  if (o.max_iter < 1) return fail(PDCS_ERR_INVALID, "max_iter must be >= 1");
+  if (o.ruiz_iters < 0) return fail(PDCS_ERR_INVALID, "ruiz_iters must be >= 0");
+  if (!(o.bisect_rel_tol > 0.0)) return fail(PDCS_ERR_INVALID, "bisect_rel_tol must be > 0");
+  if (o.trace_capacity < 0) return fail(PDCS_ERR_INVALID, "trace_capacity must be >= 0");
+  std::vector<pdcs_cone> rcv(row_cones, row_cones + n_row_cones);
+  std::vector<pdcs_cone> ccv(col_cones, col_cones + n_col_cones);
+  pdcs_handle* hd = new pdcs_handle();
+  try {
+    CK(cudaGetDevice(&hd->device));
+    if (o.precision == 0) {
+      auto* s = new Solver<double>();
+      hd->solver = s;
+      s->setup(m, n, row_ptr, col_idx, val, h, c, nb, lb, ub, rcv, ccv, o, (cudaStream_t)cuda_stream);
+    } else {
+      auto* s = new Solver<float>();
+      hd->solver = s;
+      s->setup(m, n, row_ptr, col_idx, val, h, c, nb, lb, ub, rcv, ccv, o, (cudaStream_t)cuda_stream);
+    }
+  } catch (const Fail& f) {
+    delete hd->solver;
+    delete hd;
+    return fail(f.code, f.msg);
+  }
+  *out = hd;
+  g_last_error.clear();
+  return PDCS_OK;
+}
+
+#define PDCS_API_BODY(call)                                   \
+  if (!hd || !hd->solver) return fail(PDCS_ERR_INVALID, "handle is NULL"); \
+  try {                                                       \
+    CK(cudaSetDevice(hd->device));                            \
+    call;                                                     \
+  } catch (const Fail& f) {                                   \
+    return fail(f.code, f.msg);                               \
+  }                                                           \
+  return PDCS_OK;
+
+int pdcs_solve(pdcs_handle* hd, const double* x0, const double* y0, double* x, double* y,
+               double* s, pdcs_result* res) {
+  PDCS_API_BODY(hd->solver->solve(x0, y0, x, y, s, res))
+}
+
+int pdcs_resume(pdcs_handle* hd, int64_t max_iter, double* x, double* y, double* s,
+                pdcs_result* res) {
+  PDCS_API_BODY(hd->solver->resume(max_iter, x, y, s, res))
+}
+
+int pdcs_get_state(pdcs_handle* hd, pdcs_state* state, double* x, double* y, double* x0,
+                   double* y0, double* xs, double* ys) {
+  PDCS_API_BODY(hd->solver->get_state(state, x, y, x0, y0, xs, ys))
+}
+
+int pdcs_set_state(pdcs_handle* hd, const pdcs_state* state, const double* x, const double* y,
+                   const double* x0, const double* y0, const double* xs, const double* ys) {
+  if (!state || !x || !x0 || !xs || ((!y || !y0 || !ys) && hd && hd->solver && hd->solver->m > 0))
+    return fail(PDCS_ERR_INVALID, "state and all six vectors are required");
+  if (!(state->omega > 0) || !(state->eta_hat > 0) || state->iter < 0 || state->kbar < 0 ||
+      state->k < 0)
+    return fail(PDCS_ERR_INVALID, "state has a non-positive step / weight or negative counter");
+  PDCS_API_BODY(hd->solver->set_state(state, x, y, x0, y0, xs, ys))
+}
+
+int pdcs_get_iterate(pdcs_handle* hd, int32_t which, double* x, double* y) {
+  if (which < 0 || which > 3) return fail(PDCS_ERR_INVALID, "which must be 0..3");
+  PDCS_API_BODY(hd->solver->get_iterate(which, x, y))
+}
+
+int pdcs_get_trace(pdcs_handle* hd, double* out, int64_t cap, int64_t* count) {
+  if (cap > 0 && !out) return fail(PDCS_ERR_INVALID, "out is NULL");
+  PDCS_API_BODY(const int64_t k = hd->solver->get_trace(out, cap); if (count) *count = k)
+}
+
+int pdcs_get_sizes(pdcs_handle* hd, int64_t* m, int64_t* n, int64_t* nnz) {
+  if (!hd || !hd->solver) return fail(PDCS_ERR_INVALID, "handle is NULL");
+  if (m) *m = hd->solver->m;
+  if (n) *n = hd->solver->n;
+  if (nnz) *nnz = hd->solver->nnz;
+  return PDCS_OK;
+}
+
+void pdcs_free(pdcs_handle* hd) {
+  if (!hd) return;
+  if (hd->solver) {
+    cudaSetDevice(hd->device);
+    delete hd->solver;
+  }
+  delete hd;
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// CSR sparse matrix-vector product y = A x for the two products of every PDHG
+// step, G xhat and G^T yhat (PDCS note, eq. PDHG).
+//
+// Rows are binned on the host into tasks, one CTA per task:
+//   kind 0  up to 256 short rows (<= 4 nonzeros), one thread per row;
+//   kind 1  medium rows, one group of G lanes per row (G = 8 or 32), lanes
+//           striding over the row so loads are coalesced;
+//   kind 2  one chunk of <= kChunk nonzeros of a long row; the chunk sums are
+//           written to a partial buffer and the last chunk CTA of the row (an
+//           atomic ticket, no waiting) adds them in chunk order, so the result
+//           is deterministic.
+// Accumulation: FP64 in FP64 mode (one DFMA per nonzero); in FP32 mode FP32
+// products with a compensated (Kahan) FP32 sum per lane, combined in FP64.
+#pragma once
+#include "common.cuh"
+
+namespace pdcs {
+
+constexpr int kSpmvThreads = 256;
+constexpr int64_t kChunk = 8192;
+
+struct SpmvTask {
+  int32_t kind;
+  int32_t g;        // lanes per row (kind 1)
+  int32_t counter;  // kind 2: ticket counter of this long row
+  int32_t nchunks;  // kind 2: chunks of this long row
+  int64_t a, b;     // kinds 0/1: rows [a, b); kind 2: row a, chunk index b
+  int64_t c, d;     // kind 2: nonzero range [c, d)
+  int64_t pbase;    // kind 2: first partial slot of this long row
+  int64_t pad;
+};
+
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  PDCS_DEV void add(double v, double x) { s = fma(v, x, s); }
+  PDCS_DEV double get() const { return s; }
+};
+
+template <>
+struct Acc<float> {
+  float s = 0.0f, comp = 0.0f;
+  PDCS_DEV void add(float v, float x) {
+    const float y = __fmaf_rn(v, x, -comp);
+    const float t = __fadd_rn(s, y);
+    comp = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  PDCS_DEV double get() const { return (double)s - (double)comp; }
+};
+
+// Group sum over G consecutive lanes (G a power of two <= 32).
+template <int G>
+PDCS_DEV double group_sum(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
+template <typename T, int G>
+PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
+                              const int32_t* __restrict__ ci, const T* __restrict__ vv,
+                              const T* __restrict__ x, T* __restrict__ y) {
+  const int gid = threadIdx.x / G, lane = threadIdx.x % G, ng = kSpmvThreads / G;
+  // every group runs the same number of trips so the shuffles stay converged
+  const int64_t trips = (t.b - t.a + ng - 1) / ng;
+  for (int64_t q = 0; q < trips; ++q) {
+    const int64_t row = t.a + gid + q * ng;
+    Acc<T> acc;
+    if (row < t.b) {
+      const int64_t s = rp[row], e = rp[row + 1];
+      for (int64_t k = s + lane; k < e; k += G) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
+    }
+    const double r = group_sum<G>(acc.get());
+    if (lane == 0 && row < t.b) y[row] = (T)r;
+  }
+}
+
+// y = A x over the task list.  When `gate` is non-NULL and *gate == 0 the kernel
+// does nothing (used to skip products inside a captured graph).  partial /
+// counters are the scratch of kind-2 tasks (counters are left at zero).
+template <typename T>
+__global__ void __launch_bounds__(kSpmvThreads)
+k_spmv(const SpmvTask* __restrict__ tasks, const int64_t* __restrict__ rp,
+       const int32_t* __restrict__ ci, const T* __restrict__ vv, const T* __restrict__ x,
+       T* __restrict__ y, double* __restrict__ partial, unsigned int* __restrict__ counters,
+       const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  const SpmvTask t = tasks[blockIdx.x];
+  if (t.kind == 0) {
+    const int64_t row = t.a + threadIdx.x;
+    if (row < t.b) {
+      const int64_t s = rp[row], e = rp[row + 1];
+      Acc<T> acc;
+      for (int64_t k = s; k < e; ++k) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
+      y[row] = (T)acc.get();
+    }
+    return;
+  }
+  if (t.kind == 1) {
+    if (t.g == 8) spmv_group_rows<T, 8>(t, rp, ci, vv, x, y);
+    else spmv_group_rows<T, 32>(t, rp, ci, vv, x, y);
+    return;
+  }
+  // kind 2: chunk of a long row
+  __shared__ double sh[kSpmvThreads / 32 + 1];
+  Acc<T> acc;
+  int64_t k = t.c + threadIdx.x;
+  for (; k + 3 * kSpmvThreads < t.d; k += 4 * kSpmvThreads) {
+    const int32_t c0 = __ldg(ci + k), c1 = __ldg(ci + k + kSpmvThreads);
+    const int32_t c2 = __ldg(ci + k + 2 * kSpmvThreads), c3 = __ldg(ci + k + 3 * kSpmvThreads);
+    const T v0 = __ldg(vv + k), v1 = __ldg(vv + k + kSpmvThreads);
+    const T v2 = __ldg(vv + k + 2 * kSpmvThreads), v3 = __ldg(vv + k + 3 * kSpmvThreads);
+    acc.add(v0, __ldg(x + c0));
+    acc.add(v1, __ldg(x + c1));
+    acc.add(v2, __ldg(x + c2));
+    acc.add(v3, __ldg(x + c3));
+  }
+  for (; k < t.d; k += kSpmvThreads) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
+  double r[1] = {acc.get()};
+  block_sum<1>(r, sh);
+  if (t.nchunks == 1) {
+    if (threadIdx.x == 0) y[t.a] = (T)r[0];
+    return;
+  }
+  if (threadIdx.x == 0) partial[t.pbase + t.b] = r[0];
+  __shared__ unsigned int s_ticket;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(counters + t.counter, 1u);
+  __syncthreads();
+  if (s_ticket == (unsigned)(t.nchunks - 1)) {
+    __threadfence();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      const volatile double* p = partial + t.pbase;
+      for (int j = 0; j < t.nchunks; ++j) s += p[j];
+      y[t.a] = (T)s;
+      counters[t.counter] = 0u;
+    }
+  }
+}
+
+}  // namespace pdcs
