@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the restarted-PDHG conic solver on one B300 per rank.
+
+Workload: the factor-model portfolio SOCP (n = 200,000 assets, k = 200 factors,
+1,000 sparse linear limits, one rotated SOC of dimension k + n + 2), generated
+from a seed; m = 201,203 rows, n = 200,001 columns, 40.6M nonzeros.
+
+A step is one check period of the method: 64 accepted PDHG iterations (each an
+adaptive-step attempt with G xhat, the dual and primal updates and projections,
+G^T yhat, maxErr and the reflected Halpern update) plus one restart / termination
+check (average candidate, KKT statistics, normalized-gap bisection).  The metric
+is PDHG iterations per second over the K timed steps; time to 1e-6 relative KKT
+error is reported beside it.
+
+Multi-GPU (torchrun): each rank solves its own instance (seed + rank); there is
+no data-path collective, only a barrier and a max over ranks of the timed region
+("weak" scaling; a single instance does not shard).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on
+the same workload, rank 0 only.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-6 rel. KKT & PDHG iters/s; batched and warm-start vs plain FP64"
+UNIT = "PDHG iterations/s"
+CHECK_FREQ = 64
+# DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
+# (precision, source digest of spmv.cuh at capture time); see profiles/.
+NCU_TRAFFIC = {}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--k", type=int, default=200)
+    ap.add_argument("--limits", type=int, default=1000)
+    ap.add_argument("--tts-cap", type=float, default=90.0,
+                    help="time limit (s) of the time-to-tolerance solve; 0 skips it")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-iters", type=int, default=12)
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(args, rank):
+    import workloads
+    p = workloads.portfolio(n=args.n, k=args.k, n_limits=args.limits, seed=20260102 + rank)
+    desc = ("factor-model portfolio SOCP n=%d k=%d limits=%d (m=%d, n=%d, nnz=%d), %s"
+            % (args.n, args.k, args.limits, p["m"], p["n"], len(p["val"]), args.precision.upper()))
+    return p, desc
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def _spmv_digest():
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2603_15504_b300", "csrc", "spmv.cuh"), "rb").read()
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def _oracle_sample(prob, iters):
+    """The FP64 CPU oracle, as it stands, on the same instance: set-up, then
+    `iters` accepted PDHG iterations; returns (iterations/s of the loop, setup s)."""
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Oracle(oracle.problem_from_dict(prob), oracle.Options(max_iter=iters,
+                                                                     check_freq=CHECK_FREQ))
+    t1 = time.perf_counter()
+    r = o.solve()
+    t2 = time.perf_counter()
+    return r["iters"] / (t2 - t1), t1 - t0, r["iters"], t2 - t1
+
+
+def _oracle_child(args, out_path):
+    """Run the oracle sample in a child process (one BLAS thread) so it
+    overlaps the GPU measurement; writes its result as JSON."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "a=bench._args_from(%r); p,_=bench._workload(a, 0); "
+            "v,su,it,dt=bench._oracle_sample(p, a.oracle_iters); "
+            "json.dump(dict(value=v, setup_s=su, iters=it, loop_s=dt), open(%r,'w'))"
+            % (ROOT, sys.argv[1:], out_path))
+    return subprocess.Popen([sys.executable, "-c", code], env=env, cwd=ROOT,
+                            stdout=subprocess.DEVNULL, stderr=subprocess.PIPE)
+
+
+def _args_from(argv):
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py"] + list(argv)
+        return _args()
+    finally:
+        sys.argv = old
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2603_15504_b300 as P
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    oracle_proc, oracle_out = None, None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        fd, oracle_out = tempfile.mkstemp(suffix=".json")
+        os.close(fd)
+        oracle_proc = _oracle_child(args, oracle_out)
+
+    prob, desc = _workload(args, rank)
+    opts = dict(precision=args.precision, check_freq=CHECK_FREQ, profile=1, time_limit=3600.0)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+
+    t0 = time.perf_counter()
+    s = P.Solver(prob, **dict(opts, max_iter=args.warmup * CHECK_FREQ))
+    setup_s = time.perf_counter() - t0
+    r0 = s.solve()  # warm-up periods; the timed steps continue this trajectory
+    it0 = r0["iters"]
+    kb0 = r0["attempts"]
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    r1 = s.resume(max_iter=it0 + args.steps * CHECK_FREQ)
+    ev1.record(stream)
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    ck = clocks.stop()
+    prof = s.profile()
+    iters = r1["iters"] - it0
+    attempts = r1["attempts"] - kb0
+    tmax = elapsed
+    it_all = iters
+    if ws > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+        c = torch.tensor([iters], device=dev, dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        it_all = int(c.item())
+    value = it_all / tmax
+
+    # roofline of the dominant kernel (the two sparse products), measured live
+    peaks, peak_kind = _peaks()
+    sp_time = prof["g_seconds"] + prof["gt_seconds"]
+    sp_bytes = prof["g_bytes"] * prof["g_launches"] + prof["gt_bytes"] * prof["gt_launches"]
+    launches = prof["g_launches"] + prof["gt_launches"]
+    achieved = sp_bytes / sp_time / 1e9 if sp_time > 0 else None
+    traffic = NCU_TRAFFIC.get((args.precision, _spmv_digest()))
+    roofline = {"bound": "hbm", "kernel": "k_spmv (G xhat and G^T yhat)",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"] if achieved else None,
+                "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": sp_bytes / launches if launches else None,
+                "avg_launch_us": 1e6 * sp_time / launches if launches else None,
+                "launches": launches, "spmv_time_share": sp_time / elapsed if elapsed else None}
+    if args.precision == "fp64":
+        # each nonzero costs one FP64 FMA; context for the FP64 ALU bound
+        roofline["fp64_fma_per_s"] = (prof["nnz_flops"] / 2 * launches / sp_time) if sp_time else None
+
+    # end to end through the public API: set-up from pinned host arrays (H2D
+    # inside the timed region), K periods from a cold start, solution back to
+    # pinned host buffers.
+    e2e = None
+    if not args.no_e2e:
+        import torch as _t
+        host = {}
+        h2d = 0
+        for key in ("row_ptr", "col_idx", "val", "h", "c", "lo", "hi"):
+            a = _t.from_numpy(np.ascontiguousarray(prob[key])).pin_memory()
+            host[key] = a
+            h2d += a.numel() * a.element_size()
+        hp = dict(prob, **host)
+        outs = tuple(_t.empty(k, dtype=_t.float64).pin_memory() for k in (prob["n"], prob["m"], prob["m"]))
+        barrier()
+        t1 = time.perf_counter()
+        with P.Solver(hp, **dict(opts, max_iter=args.steps * CHECK_FREQ, profile=0)) as se:
+            re = se.solve(out=outs)
+        barrier()
+        te = time.perf_counter() - t1
+        d2h = sum(o.numel() * o.element_size() for o in outs)
+        e2e = {"value": re["iters"] / te, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "seconds": te, "includes": "pdcs_setup from pinned host CSR + pdcs_solve of "
+               "%d iterations + copy of x, y, s to pinned host" % (args.steps * CHECK_FREQ)}
+
+    # time to 1e-6 relative KKT error
+    tts = None
+    if args.tts_cap > 0 and rank == 0:
+        with P.Solver(prob, **dict(opts, time_limit=args.tts_cap, max_iter=2**62, profile=0)) as st:
+            t2 = time.perf_counter()
+            rt = st.solve()
+            tt = time.perf_counter() - t2
+        tts = {"reached": rt["exit_code"] == 0, "seconds": tt, "setup_s": setup_s,
+               "iters": rt["iters"], "attempts": rt["attempts"], "restarts": rt["restarts"],
+               "rel_kkt": max(rt["err_rel_p"], rt["err_rel_d"], rt["err_rel_gap"]),
+               "status": rt["status"], "time_cap_s": args.tts_cap}
+    s.close()
+
+    cpu = None
+    if oracle_proc is not None:
+        _, err = oracle_proc.communicate(timeout=1800)
+        try:
+            o = json.load(open(oracle_out))
+            cpu = {"value": o["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "FP64 CPU oracle on the same instance: %d accepted PDHG iterations "
+                             "after its set-up (%.0f s, not counted)" % (o["iters"], o["setup_s"])}
+        except (OSError, ValueError, KeyError):
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "oracle run failed: %s" % err.decode()[-200:]}
+        os.unlink(oracle_out)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * tmax / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32",
+                "data": "synthetic (seeded factor-model portfolio generator)",
+                "config": {"workload": desc, "step": "%d accepted PDHG iterations + 1 restart check"
+                           % CHECK_FREQ, "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (two CSR copies of G, %.0f MB)"
+                           % (2 * len(prob["val"]) * (12 if args.precision == "fp64" else 8) / 1e6)},
+                "attempts_per_s": attempts / elapsed, "setup_s": setup_s,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": prof["kernel_launches"], "graph_launches": prof["graph_launches"],
+                "clocks": ck, "time_to_tol": tts}
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    prob, desc = _workload(args, 0)
+    import oracle
+    o = oracle.Oracle(oracle.problem_from_dict(prob),
+                      oracle.Options(max_iter=args.warmup + args.steps, check_freq=CHECK_FREQ))
+    # one step = one accepted PDHG iteration of the oracle; warm-up iterations
+    # are run first, the timed steps continue the same trajectory
+    trace = []
+    t_marks = []
+
+    class Clock(list):
+        def append(self, rec):
+            t_marks.append(time.perf_counter())
+            super().append(rec)
+
+    tr = Clock()
+    t0 = time.perf_counter()
+    o.solve(trace=tr)
+    del trace
+    n = len(t_marks)
+    if n > args.warmup:
+        dt = t_marks[-1] - t_marks[args.warmup - 1] if args.warmup > 0 else t_marks[-1] - t0
+        steps = n - args.warmup
+    else:
+        dt, steps = t_marks[-1] - t0, n
+    value = steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded factor-model portfolio generator)",
+            "config": {"workload": desc, "step": "1 accepted PDHG iteration of the FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d timed oracle iterations after %d warm-up iterations"
+                                       % (steps, args.warmup)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

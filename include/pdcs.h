@@ -101,6 +101,8 @@ typedef struct {
   double bisect_rel_tol;     /* 1e-6: Algorithm 3 stops when t_r - t_l <= tol * t_r */
   int32_t verbose;           /* 0 silent, 1 one line per check period on stderr */
   int32_t trace_capacity;    /* >0: record one trace row per accepted iteration */
+  int32_t profile;           /* 1: time the SpMV launches of every attempt on the
+                                device (see pdcs_get_profile) */
 } pdcs_options;
 
 typedef struct {
@@ -205,6 +207,26 @@ int pdcs_get_iterate(pdcs_handle* handle, int32_t which, double* x, double* y);
  * omega, max_err, check, cand_avg, restart, rho_c. */
 #define PDCS_TRACE_FIELDS 12
 int pdcs_get_trace(pdcs_handle* handle, double* out, int64_t cap, int64_t* count);
+
+/* Device-measured cost of the sparse products of the last pdcs_solve /
+ * pdcs_resume call (requires options.profile = 1; zero otherwise).  Each launch
+ * is timed from the start of its first CTA to the end of its last CTA with the
+ * GPU's global nanosecond timer.  bytes_* are the algorithmic bytes of one
+ * launch: values and column indices once, row pointers once, the gathered
+ * vector and the result vector once each. */
+typedef struct {
+  int64_t g_launches;    /* G xhat products (one per attempt) */
+  double g_seconds;
+  double g_bytes;        /* per launch */
+  int64_t gt_launches;   /* G^T yhat products (one per accepted attempt) */
+  double gt_seconds;
+  double gt_bytes;       /* per launch */
+  double nnz_flops;      /* 2 * nnz: multiply-adds of one launch, as flops */
+  int64_t graph_launches;   /* check-period graphs launched by the call */
+  int64_t kernel_launches;  /* kernels this library launched inside those graphs */
+} pdcs_profile;
+
+int pdcs_get_profile(pdcs_handle* handle, pdcs_profile* prof);
 
 /* Sizes after set-up (m, n of the reformulated problem, nnz of G). */
 int pdcs_get_sizes(pdcs_handle* handle, int64_t* m, int64_t* n, int64_t* nnz);

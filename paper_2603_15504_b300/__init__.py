@@ -34,7 +34,7 @@ class PdcsOptions(ctypes.Structure):
                 ("use_adaptive_restart", ctypes.c_int32), ("check_freq", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("require_abs", ctypes.c_int32),
                 ("bisect_rel_tol", ctypes.c_double), ("verbose", ctypes.c_int32),
-                ("trace_capacity", ctypes.c_int32)]
+                ("trace_capacity", ctypes.c_int32), ("profile", ctypes.c_int32)]
 
 
 class PdcsResult(ctypes.Structure):
@@ -59,9 +59,17 @@ class PdcsState(ctypes.Structure):
                 ("prev_abs_d", ctypes.c_double), ("prev_abs_gap", ctypes.c_double)]
 
 
+class PdcsProfile(ctypes.Structure):
+    _fields_ = [("g_launches", ctypes.c_int64), ("g_seconds", ctypes.c_double),
+                ("g_bytes", ctypes.c_double), ("gt_launches", ctypes.c_int64),
+                ("gt_seconds", ctypes.c_double), ("gt_bytes", ctypes.c_double),
+                ("nnz_flops", ctypes.c_double), ("graph_launches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
 EXPORTS = ("pdcs_default_options", "pdcs_setup", "pdcs_solve", "pdcs_resume", "pdcs_get_state",
-           "pdcs_set_state", "pdcs_get_iterate", "pdcs_get_trace", "pdcs_get_sizes", "pdcs_free",
-           "pdcs_last_error")
+           "pdcs_set_state", "pdcs_get_iterate", "pdcs_get_trace", "pdcs_get_profile",
+           "pdcs_get_sizes", "pdcs_free", "pdcs_last_error")
 
 _LIB = None
 
@@ -98,6 +106,8 @@ def lib():
     L.pdcs_get_iterate.restype = ctypes.c_int
     L.pdcs_get_trace.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     L.pdcs_get_trace.restype = ctypes.c_int
+    L.pdcs_get_profile.argtypes = [vp, ctypes.POINTER(PdcsProfile)]
+    L.pdcs_get_profile.restype = ctypes.c_int
     L.pdcs_get_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.pdcs_get_sizes.restype = ctypes.c_int
     L.pdcs_free.argtypes = [vp]
@@ -252,6 +262,12 @@ class Solver:
         x, y = np.empty(self.n), np.empty(self.m)
         _check(lib().pdcs_get_iterate(self._h, int(which), _ptr(x), _ptr(y)))
         return x, y
+
+    def profile(self):
+        """Device-timed SpMV statistics of the last solve / resume."""
+        pr = PdcsProfile()
+        _check(lib().pdcs_get_profile(self._h, ctypes.byref(pr)))
+        return {k: getattr(pr, k) for k, _ in PdcsProfile._fields_}
 
     def trace(self):
         cap = int(self.options.trace_capacity)

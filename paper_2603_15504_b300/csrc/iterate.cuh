@@ -51,6 +51,7 @@ struct Ctl {
   int method, adaptive_restart, require_abs, trace_cap;
   int guard, guard_cap, probes, probe_cap;
   int g_attempt, g_accept, g_check, g_restart;
+  long long bodies_a, bodies_b;  // executions of the attempt / probe loop bodies
   PointStats st[4];  // 0 zhat (attempt), 1 z, 2 zbar (check), 3 returned point
   Bisect bs[2];
   unsigned int cnt[CNT_NUM];
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(kEwThreads) k_halpern(
 // accepted iterations (bounded by guard_cap bodies per graph launch).
 __global__ void k_loop_ctl(Ctl* ctl, cudaGraphConditionalHandle h) {
   ctl->guard += 1;
+  ctl->bodies_a += 1;
   const int go = (ctl->status == kRunning && !ctl->period_done && ctl->guard < ctl->guard_cap);
   ctl->g_attempt = go;
   cudaGraphSetConditional(h, go ? 1u : 0u);
@@ -628,6 +630,7 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __r
     any |= b.active;
   }
   ctl->probes += 1;
+  ctl->bodies_b += 1;
   if (ctl->probes >= ctl->probe_cap) {
     for (int cc = 0; cc < 2; ++cc) {
       Bisect& b = ctl->bs[cc];
@@ -778,6 +781,206 @@ __global__ void k_unscale(Prob<T> p, const T* xt, const T* yt, const T* gxt, dou
   PDCS_GRID_LOOP(i, p.m) {
     y[i] = p.d1[i] * (double)yt[i];
     s[i] = ((double)gxt[i] - (double)p.h[i]) / p.d1[i];
+  }
+}
+
+}  // namespace pdcs
+
+namespace pdcs {
+
+// ------------------------------------------------- grid-wide SOC projection
+// For second-order-cone blocks too large for one CTA (e.g. the single block of
+// dimension k + n + 2 of a factor-model portfolio), the same root-finding as
+// soc_proj_cta runs over the whole grid: each Newton step is a grid-wide sum
+// (per-CTA partials, a grid barrier, then every CTA adds the partials in the
+// same fixed order, so all CTAs take identical decisions).  The kernel is
+// launched cooperatively, so all CTAs are resident; each barrier wait is still
+// bounded and, if it ever gives up, sets *err and lets the kernel finish.
+struct GridSync {
+  unsigned int* count;  // zeroed before every launch
+  int* err;
+};
+
+PDCS_DEV void grid_sync(const GridSync& gs, unsigned int& target) {
+  __syncthreads();
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(gs.count, 1u);
+    unsigned long long spins = 0;
+    while (true) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gs.count) : "memory");
+      if (v >= target) break;
+      __nanosleep(64);
+      if (++spins > (1ull << 24)) { atomicExch(gs.err, 1); break; }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Grid-wide sum of K <= 2 values (fixed order: per-CTA tree, then lane-strided
+// sequential sums over the CTA partials and a fixed butterfly).  Every thread
+// of every CTA receives the totals.  Successive reductions alternate between
+// two partial buffers (flip), so a CTA that runs ahead never overwrites
+// partials another CTA is still reading.
+template <int K>
+PDCS_DEV void grid_sum(double (&v)[K], double* part_base, const GridSync& gs, unsigned int& target,
+                       double* sh, int& flip) {
+  double* part = part_base + (size_t)flip * 2 * gridDim.x;
+  flip ^= 1;
+  block_sum<K>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) part[blockIdx.x * K + k] = v[k];
+  }
+  grid_sync(gs, target);
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s += __ldcg(part + b * K + k);
+      s = warp_sum(s);
+      if (threadIdx.x == 0) sh[k] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = sh[k];
+  __syncthreads();
+}
+
+PDCS_DEV double grid_max1(double v, double* part_base, const GridSync& gs, unsigned int& target,
+                          double* sh, int& flip) {
+  double* part = part_base + (size_t)flip * 2 * gridDim.x;
+  flip ^= 1;
+  double a[1] = {v};
+  block_max<1>(a, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = a[0];
+  grid_sync(gs, target);
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s = fmax(s, __ldcg(part + b));
+    s = warp_max(s);
+    if (threadIdx.x == 0) sh[0] = s;
+  }
+  __syncthreads();
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Projection of the blocks (starts[b], dims[b]) of one or two vectors onto
+// diag(e) K_soc, e = d or 1/d (inv) or 1 (d == NULL).  part needs
+// 4 * gridDim.x doubles; every grid barrier uses a fresh target, so the
+// counter must be zero at launch.
+template <typename B>
+__global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
+                                                       const int64_t* __restrict__ starts,
+                                                       const int64_t* __restrict__ dims,
+                                                       int nblocks, const double* __restrict__ d,
+                                                       int inv, const int* __restrict__ gate0,
+                                                       const int* __restrict__ gate1,
+                                                       double* __restrict__ part, GridSync gs) {
+  __shared__ double sh[2 * 512 / 32 + 8];
+  unsigned int target = 0;
+  int flip = 0;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  for (int q = 0; q < nvec; ++q) {
+    const int* gate = q == 0 ? gate0 : gate1;
+    if (gate != nullptr && *gate == 0) continue;  // uniform across the grid
+    B* v = q == 0 ? v0 : v1;
+    for (int blk = 0; blk < nblocks; ++blk) {
+      const int64_t s = starts[blk], dim = dims[blk];
+      const double v0h = (double)v[s];
+      const double e0 = cone_scale(d, s, inv);
+      double acc[2] = {0.0, 0.0};
+      double mx = fabs(v0h);
+      for (int64_t i = 1 + tid; i < dim; i += nth) {
+        const double vi = (double)v[s + i], ei = cone_scale(d, s + i, inv);
+        const double a = vi / ei, b = vi * ei;
+        acc[0] += a * a;
+        acc[1] += b * b;
+        mx = fmax(mx, fabs(vi));
+      }
+      grid_sum<2>(acc, part, gs, target, sh, flip);
+      mx = grid_max1(mx, part, gs, target, sh, flip);
+      // every CTA read the head v[s] before the barriers above; it is only
+      // rewritten after them
+      if (sqrt(acc[0]) <= v0h / e0) continue;  // inside (uniform decision)
+      if (sqrt(acc[1]) <= -e0 * v0h) {         // polar: zero
+        for (int64_t i = tid; i < dim; i += nth) v[s + i] = (B)0.0;
+        continue;
+      }
+      const double e02 = e0 * e0;
+      if (v0h == 0.0) {
+        double w[1] = {0.0};
+        for (int64_t i = 1 + tid; i < dim; i += nth) {
+          const double ei = cone_scale(d, s + i, inv), b = ei * ei;
+          const double nv = (double)v[s + i] * b / (b + e02);
+          const double t = nv / ei;
+          w[0] += t * t;
+        }
+        grid_sum<1>(w, part, gs, target, sh, flip);
+        for (int64_t i = 1 + tid; i < dim; i += nth) {
+          const double ei = cone_scale(d, s + i, inv), b = ei * ei;
+          v[s + i] = (B)((double)v[s + i] * b / (b + e02));
+        }
+        if (tid == 0) v[s] = (B)(e0 * sqrt(w[0]));
+        continue;
+      }
+      const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
+      const double c0 = (v0h * sc) * (v0h * sc) * e02;
+      const bool pos = v0h > 0.0;
+      double lo = 0.0, hi = pos ? 0.5 * e02 : 1.0 / e02;
+      double x = 0.0;
+      for (int it = 0; it < 200; ++it) {
+        double f[2] = {0.0, 0.0};
+        for (int64_t i = 1 + tid; i < dim; i += nth) {
+          const double ei = cone_scale(d, s + i, inv);
+          const double vv = (double)v[s + i] * sc, b = ei * ei, a = vv * vv * b;
+          if (pos) {
+            const double r = 1.0 / (b + 2.0 * x);
+            f[0] += a * r * r;
+            f[1] += a * r * r * r;
+          } else {
+            const double r = 1.0 / (1.0 + b * x);
+            f[0] += a * r * r;
+            f[1] += a * b * r * r * r;
+          }
+        }
+        grid_sum<2>(f, part, gs, target, sh, flip);
+        double F, dF;
+        if (pos) {
+          const double r = 1.0 / (e02 - 2.0 * x);
+          F = f[0] - c0 * r * r;
+          dF = -4.0 * f[1] - 4.0 * c0 * r * r * r;
+        } else {
+          const double r = 1.0 / (1.0 - e02 * x);
+          F = f[0] - c0 * r * r;
+          dF = -2.0 * f[1] - 2.0 * c0 * e02 * r * r * r;
+        }
+        if (F > 0.0) lo = x; else hi = x;
+        if (F == 0.0) break;
+        const double step = -F / dF;
+        double xn = x + step;
+        if (fabs(step) <= 1e-15 * x) {
+          if (xn >= lo && xn <= hi) x = xn;
+          break;
+        }
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        x = xn;
+        if (hi - lo <= 1e-15 * hi) break;
+      }
+      const double mu2 = pos ? 2.0 * x : 1.0 / x;
+      for (int64_t i = 1 + tid; i < dim; i += nth) {
+        const double ei = cone_scale(d, s + i, inv), b = ei * ei;
+        v[s + i] = (B)((double)v[s + i] * (b / (b + mu2)));
+      }
+      if (tid == 0) v[s] = (B)(pos ? v0h * e02 / (e02 - mu2) : v0h * e02 * x / (e02 * x - 1.0));
+    }
   }
 }
 

@@ -168,21 +168,31 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
 
 template <typename T>
 static void launch_spmv(const SpmvPlan& p, const int64_t* rp, const int32_t* ci, const T* vv,
-                        const T* x, T* y, const int* gate, cudaStream_t st) {
+                        const T* x, T* y, const int* gate, cudaStream_t st, KTimer* tm = nullptr) {
   if (p.ntasks == 0) return;
-  k_spmv<T><<<p.ntasks, kSpmvThreads, 0, st>>>(p.tasks, rp, ci, vv, x, y, p.partial, p.counters, gate);
+  k_spmv<T><<<p.ntasks, kSpmvThreads, 0, st>>>(p.tasks, rp, ci, vv, x, y, p.partial, p.counters, gate, tm);
 }
 
 // ------------------------------------------------------------- cone tables
 struct ConeTable {
-  // SOC tiers by block dimension: <= 128 (32 threads), <= 4096 (256), <= 8192 (512)
+  // SOC tiers by block dimension: <= 128 (32 threads), <= 4096 (256), <= 8192 (512),
+  // larger blocks grid-wide (k_cone_soc_grid)
   int64_t* soc_s[3] = {nullptr, nullptr, nullptr};
   int32_t* soc_d[3] = {nullptr, nullptr, nullptr};
   int64_t nsoc[3] = {0, 0, 0};
+  int64_t* big_s = nullptr;
+  int64_t* big_d = nullptr;
+  int nbig = 0;
   int64_t* exp_s = nullptr;
   uint8_t* exp_isd = nullptr;
   int64_t nexp = 0;
+  // grid-wide kernel resources (shared by both tables)
+  double* gpart = nullptr;
+  GridSync gsync = {nullptr, nullptr};
+  int big_grid = 0;
 };
+
+__global__ void k_zero_u32(unsigned int* p) { *p = 0u; }
 
 static const int kSocTierMax[3] = {128, 4096, 8192};
 
@@ -203,6 +213,21 @@ static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d,
     k_cone_soc<B, 256, 16><<<dim3((unsigned)t.nsoc[1], nvec), 256, 0, st>>>(v0, v1, t.soc_s[1], t.soc_d[1], d, inv, g0, g1);
   if (t.nsoc[2] > 0)
     k_cone_soc<B, 512, 16><<<dim3((unsigned)t.nsoc[2], nvec), 512, 0, st>>>(v0, v1, t.soc_s[2], t.soc_d[2], d, inv, g0, g1);
+  if (t.nbig > 0) {
+    k_zero_u32<<<1, 1, 0, st>>>(t.gsync.count);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)t.big_grid);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B>, v0, v1, nvec, (const int64_t*)t.big_s,
+                          (const int64_t*)t.big_d, t.nbig, d, inv, g0, g1, t.gpart, t.gsync));
+  }
 }
 
 }  // namespace pdcs
@@ -221,6 +246,7 @@ struct SolverBase {
                          const double* x0, const double* y0, const double* xs,
                          const double* ys) = 0;
   virtual void get_iterate(int which, double* x, double* y) = 0;
+  virtual void get_profile(pdcs_profile* pr) = 0;
   virtual int64_t get_trace(double* out, int64_t cap) = 0;
   int64_t m = 0, n = 0, nnz = 0;
 };
@@ -263,9 +289,17 @@ struct Solver : SolverBase {
   double *obuf_n = nullptr, *obuf_m = nullptr, *obuf_s = nullptr;
   Ctl* ctl = nullptr;
   Ctl* hctl = nullptr;
+  KTimer* timers = nullptr;             // [0] G xhat, [1] G^T yhat (profile option)
+  unsigned int* gsync_count = nullptr;  // grid barrier of k_cone_soc_grid
+  int* gsync_err = nullptr;             // set if a bounded barrier wait gave up
+  double* gpart = nullptr;
+  int big_grid = 0;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   int64_t trace_rows = 0;
+  int64_t nk_a = 0, nk_b = 0, nk_top = 0;  // kernel nodes: attempt body, probe body, top level
+  int64_t graph_launches = 0;
+  long long bodies_a0 = 0, bodies_b0 = 0;  // loop-body counters at the start of the call
 
   Prob<T> prob() const {
     Prob<T> p;
@@ -354,11 +388,12 @@ struct Solver : SolverBase {
     std::vector<int64_t> rpairs, cpairs;
     std::vector<uint8_t> hrk((size_t)m), hck((size_t)n);
     std::vector<std::vector<std::pair<int64_t, int32_t>>> rsoc(3), csoc(3);
+    std::vector<std::pair<int64_t, int64_t>> rbig, cbig;
     std::vector<int64_t> rexp, cexp;
     std::vector<uint8_t> rexpd, cexpd;
-    layout(rc, 0, m, true, hrk, rpairs, rsoc, rexp, rexpd);
+    layout(rc, 0, m, true, hrk, rpairs, rsoc, rbig, rexp, rexpd);
     for (int64_t j = 0; j < nb; ++j) hck[j] = CK_BOX;
-    layout(cc, nb, n, false, hck, cpairs, csoc, cexp, cexpd);
+    layout(cc, nb, n, false, hck, cpairs, csoc, cbig, cexp, cexpd);
     // ---- RSOC reformulation on rows
     if (!rpairs.empty()) {
       merge_row_pairs(hrp, drp, dci, dv, rpairs, m);
@@ -459,8 +494,8 @@ struct Solver : SolverBase {
     ck = ar.alloc<uint8_t>(n);
     copy_in(rk, hrk.data(), m, st);
     copy_in(ck, hck.data(), n, st);
-    fill_table(rows, rsoc, rexp, rexpd);
-    fill_table(cols, csoc, cexp, cexpd);
+    fill_table(rows, rsoc, rbig, rexp, rexpd);
+    fill_table(cols, csoc, cbig, cexp, cexpd);
     planG = build_plan(hrp, ar, st);
     planGT = build_plan(hrpT, ar, st);
     alloc_state();
@@ -470,7 +505,8 @@ struct Solver : SolverBase {
   // Per-element kinds and cone tables from an ordered cone list starting at off.
   void layout(const std::vector<pdcs_cone>& cl, int64_t off, int64_t end, bool is_row,
               std::vector<uint8_t>& kind, std::vector<int64_t>& pairs,
-              std::vector<std::vector<std::pair<int64_t, int32_t>>>& soc, std::vector<int64_t>& ex,
+              std::vector<std::vector<std::pair<int64_t, int32_t>>>& soc,
+              std::vector<std::pair<int64_t, int64_t>>& big, std::vector<int64_t>& ex,
               std::vector<uint8_t>& exd) {
     for (const auto& cn : cl) {
       const int64_t d = cn.dim;
@@ -486,10 +522,12 @@ struct Solver : SolverBase {
         case PDCS_CONE_SOC: {
           if (cn.type == PDCS_CONE_RSOC) pairs.push_back(off);
           for (int64_t i = 0; i < d; ++i) kind[off + i] = is_row ? (uint8_t)RK_SOC : (uint8_t)CK_SOC;
-          if (d > kSocTierMax[2])
-            throw Fail{PDCS_ERR_UNSUPPORTED, "SOC block dimension above 8192 is not supported"};
-          const int tier = d <= kSocTierMax[0] ? 0 : (d <= kSocTierMax[1] ? 1 : 2);
-          soc[tier].push_back({off, (int32_t)d});
+          if (d > kSocTierMax[2]) {
+            big.push_back({off, d});
+          } else {
+            const int tier = d <= kSocTierMax[0] ? 0 : (d <= kSocTierMax[1] ? 1 : 2);
+            soc[tier].push_back({off, (int32_t)d});
+          }
           break;
         }
         case PDCS_CONE_EXP:
@@ -509,7 +547,34 @@ struct Solver : SolverBase {
   }
 
   void fill_table(ConeTable& t, const std::vector<std::vector<std::pair<int64_t, int32_t>>>& soc,
+                  const std::vector<std::pair<int64_t, int64_t>>& big,
                   const std::vector<int64_t>& ex, const std::vector<uint8_t>& exd) {
+    t.nbig = (int)big.size();
+    if (t.nbig > 0) {
+      std::vector<int64_t> bs, bd;
+      for (auto& pr : big) { bs.push_back(pr.first); bd.push_back(pr.second); }
+      t.big_s = ar.alloc<int64_t>(t.nbig);
+      t.big_d = ar.alloc<int64_t>(t.nbig);
+      copy_in(t.big_s, bs.data(), (int64_t)t.nbig, st);
+      copy_in(t.big_d, bd.data(), (int64_t)t.nbig, st);
+      if (!gsync_count) {
+        int dev = 0, sms = 0, occ_t = 0, occ_d = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, k_cone_soc_grid<T>, 512, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, k_cone_soc_grid<double>, 512, 0));
+        const int occ = std::max(1, std::min(std::min(occ_t, occ_d), 2));
+        big_grid = sms * occ;
+        gsync_count = ar.alloc<unsigned int>(1);
+        gsync_err = ar.alloc<int>(1);
+        gpart = ar.alloc<double>(4 * (int64_t)big_grid);
+        CK(cudaMemsetAsync(gsync_count, 0, sizeof(unsigned int), st));
+        CK(cudaMemsetAsync(gsync_err, 0, sizeof(int), st));
+      }
+    }
+    t.gpart = gpart;
+    t.gsync = GridSync{gsync_count, gsync_err};
+    t.big_grid = big_grid;
     for (int k = 0; k < 3; ++k) {
       t.nsoc[k] = (int64_t)soc[k].size();
       if (t.nsoc[k] == 0) continue;
@@ -613,6 +678,36 @@ struct Solver : SolverBase {
     obuf_m = ar.alloc<double>(m);
     obuf_s = ar.alloc<double>(m);
     if (opt.trace_capacity > 0) trace = ar.alloc<double>((int64_t)opt.trace_capacity * PDCS_TRACE_FIELDS);
+    if (opt.profile) {
+      timers = ar.alloc<KTimer>(2);
+      reset_timers();
+    }
+  }
+
+  void reset_timers() {
+    if (!timers) return;
+    KTimer z[2];
+    for (auto& t : z) { t.start = ~0ull; t.total_ns = 0; t.ticket = 0; t.launches = 0; }
+    CK(cudaMemcpyAsync(timers, z, sizeof(z), cudaMemcpyHostToDevice, st));
+  }
+
+  void get_profile(pdcs_profile* pr) override {
+    std::memset(pr, 0, sizeof(*pr));
+    const double vb = (double)sizeof(T);
+    pr->g_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(m + 1) + vb * (double)(n + m);
+    pr->gt_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(n + 1) + vb * (double)(n + m);
+    pr->nnz_flops = 2.0 * (double)nnz;
+    pr->graph_launches = graph_launches;
+    pr->kernel_launches = graph_launches * nk_top + (hctl->bodies_a - bodies_a0) * nk_a +
+                          (hctl->bodies_b - bodies_b0) * nk_b;
+    if (!timers) return;
+    KTimer z[2];
+    CK(cudaMemcpyAsync(z, timers, sizeof(z), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    pr->g_launches = z[0].launches;
+    pr->g_seconds = 1e-9 * (double)z[0].total_ns;
+    pr->gt_launches = z[1].launches;
+    pr->gt_seconds = 1e-9 * (double)z[1].total_ns;
   }
 
   // ------------------------------------------------------- graph capture
@@ -650,11 +745,11 @@ struct Solver : SolverBase {
     const int gn = ew_grid(n), gm = ew_grid(m), gmx = ew_grid(std::max(m, n));
     k_primal<T><<<gn, kEwThreads, 0, s>>>(p, ctl, x, gty, xh);
     project<T>(cols, xh, xh, 1, d2, 1, 0, &ctl->g_attempt, nullptr, s);
-    launch_spmv<T>(planG, rp, ci, vv, xh, gxh, &ctl->g_attempt, s);
+    launch_spmv<T>(planG, rp, ci, vv, xh, gxh, &ctl->g_attempt, s, timers);
     k_dual<T><<<gm, kEwThreads, 0, s>>>(p, ctl, y, gxh, gx, yh);
     project<T>(rows, yh, yh, 1, d1, 1, 1, &ctl->g_attempt, nullptr, s);
     k_step<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, xh, y, yh, gxh, gx, part);
-    launch_spmv<T>(planGT, rpT, ciT, vvT, yh, gtyh, &ctl->g_accept, s);
+    launch_spmv<T>(planGT, rpT, ciT, vvT, yh, gtyh, &ctl->g_accept, s, timers ? timers + 1 : nullptr);
     const PointRef<T> ph{xh, yh, gxh, gtyh};
     const TmpRef t0{tm[0], tn[0], nullptr, nullptr};
     k_res_prep<T><<<dim3(gmx, 1), kEwThreads, 0, s>>>(p, &ctl->g_accept, ph, ph, t0, t0);
@@ -701,6 +796,21 @@ struct Solver : SolverBase {
     k_check_end<<<1, 1, 0, s>>>(ctl);
   }
 
+  // Kernel nodes of a graph (conditional nodes and their bodies not included).
+  static int64_t kernel_nodes(cudaGraph_t g) {
+    size_t num = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &num));
+    std::vector<cudaGraphNode_t> nodes(num);
+    if (num) CK(cudaGraphGetNodes(g, nodes.data(), &num));
+    int64_t k = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      CK(cudaGraphNodeGetType(nd, &t));
+      if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+  }
+
   void capture() {
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     cudaGraphConditionalHandle hA = new_handle(st);
@@ -718,6 +828,9 @@ struct Solver : SolverBase {
     CK(cudaStreamEndCapture(st2, &bodyB));
     rec_check_end(st);
     CK(cudaStreamEndCapture(st, &graph));
+    nk_a = kernel_nodes(bodyA);
+    nk_b = kernel_nodes(bodyB);
+    nk_top = kernel_nodes(graph);
     CK(cudaGraphInstantiate(&exec, graph, 0));
   }
 
@@ -806,8 +919,13 @@ struct Solver : SolverBase {
   void run(double* xo, double* yo, double* so, pdcs_result* res,
            std::chrono::steady_clock::time_point t0) {
     int status = kRunning;
+    reset_timers();
+    graph_launches = 0;
+    bodies_a0 = hctl->bodies_a;
+    bodies_b0 = hctl->bodies_b;
     while (true) {
       CK(cudaGraphLaunch(exec, st));
+      ++graph_launches;
       CK(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       status = hctl->status;
@@ -855,6 +973,14 @@ struct Solver : SolverBase {
     if (so && m) CK(cudaMemcpyAsync(so, obuf_s, sizeof(double) * m, cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
     trace_rows = std::min<int64_t>(hctl->iter, opt.trace_capacity);
+    if (gsync_err) {
+      int herr = 0;
+      CK(cudaMemcpy(&herr, gsync_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (herr) {
+        CK(cudaMemset(gsync_err, 0, sizeof(int)));
+        throw Fail{PDCS_ERR_TIMEOUT, "a grid barrier wait of the SOC projection gave up"};
+      }
+    }
     if (res) {
       const PointStats& s3 = hctl->st[3];
       res->exit_code = status;
@@ -978,6 +1104,7 @@ void pdcs_default_options(pdcs_options* o) {
   o->bisect_rel_tol = 1e-6;
   o->verbose = 0;
   o->trace_capacity = 0;
+  o->profile = 0;
 }
 
 const char* pdcs_last_error(void) { return g_last_error.c_str(); }
@@ -1096,6 +1223,11 @@ int pdcs_get_iterate(pdcs_handle* hd, int32_t which, double* x, double* y) {
 int pdcs_get_trace(pdcs_handle* hd, double* out, int64_t cap, int64_t* count) {
   if (cap > 0 && !out) return fail(PDCS_ERR_INVALID, "out is NULL");
   PDCS_API_BODY(const int64_t k = hd->solver->get_trace(out, cap); if (count) *count = k)
+}
+
+int pdcs_get_profile(pdcs_handle* hd, pdcs_profile* prof) {
+  if (!prof) return fail(PDCS_ERR_INVALID, "prof is NULL");
+  PDCS_API_BODY(hd->solver->get_profile(prof))
 }
 
 int pdcs_get_sizes(pdcs_handle* hd, int64_t* m, int64_t* n, int64_t* nnz) {

@@ -79,17 +79,70 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
   }
 }
 
+// Live kernel timer: span from the first CTA's start to the last CTA's end of
+// each launch, read from %globaltimer (ns) and accumulated on the device.
+struct KTimer {
+  unsigned long long start;  // ~0 between launches
+  unsigned long long total_ns;
+  unsigned int ticket;
+  unsigned int launches;
+};
+
+PDCS_DEV unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+PDCS_DEV void ktimer_begin(KTimer* tm) {
+  if (tm != nullptr && threadIdx.x == 0) atomicMin(&tm->start, global_ns());
+}
+
+PDCS_DEV void ktimer_end(KTimer* tm) {
+  if (tm == nullptr) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int tk = atomicAdd(&tm->ticket, 1u);
+    if (tk == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long t1 = global_ns();
+      const unsigned long long t0 = atomicAdd(&tm->start, 0ull);
+      tm->total_ns += t1 > t0 ? t1 - t0 : 0ull;
+      tm->launches += 1u;
+      tm->start = ~0ull;
+      tm->ticket = 0u;
+    }
+  }
+}
+
+template <typename T>
+PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
+                        const int32_t* __restrict__ ci, const T* __restrict__ vv,
+                        const T* __restrict__ x, T* __restrict__ y, double* __restrict__ partial,
+                        unsigned int* __restrict__ counters);
+
 // y = A x over the task list.  When `gate` is non-NULL and *gate == 0 the kernel
 // does nothing (used to skip products inside a captured graph).  partial /
-// counters are the scratch of kind-2 tasks (counters are left at zero).
+// counters are the scratch of kind-2 tasks (counters are left at zero).  tm,
+// when non-NULL, accumulates the launch's duration.
 template <typename T>
 __global__ void __launch_bounds__(kSpmvThreads)
 k_spmv(const SpmvTask* __restrict__ tasks, const int64_t* __restrict__ rp,
        const int32_t* __restrict__ ci, const T* __restrict__ vv, const T* __restrict__ x,
        T* __restrict__ y, double* __restrict__ partial, unsigned int* __restrict__ counters,
-       const int* __restrict__ gate) {
+       const int* __restrict__ gate, KTimer* tm) {
   if (gate != nullptr && *gate == 0) return;
-  const SpmvTask t = tasks[blockIdx.x];
+  ktimer_begin(tm);
+  spmv_task<T>(tasks[blockIdx.x], rp, ci, vv, x, y, partial, counters);
+  ktimer_end(tm);
+}
+
+template <typename T>
+PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
+                        const int32_t* __restrict__ ci, const T* __restrict__ vv,
+                        const T* __restrict__ x, T* __restrict__ y, double* __restrict__ partial,
+                        unsigned int* __restrict__ counters) {
   if (t.kind == 0) {
     const int64_t row = t.a + threadIdx.x;
     if (row < t.b) {

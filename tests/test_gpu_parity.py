@@ -130,6 +130,14 @@ def test_no_preconditioner_first_200_iterations():
             use_preconditioner=False)
 
 
+def test_large_soc_block_grid_tier():
+    """An SOC block of dimension n + k + 2 > 8192 goes through the cooperative
+    grid-wide projection kernel."""
+    prob = workloads.portfolio(n=9000, k=30, n_limits=5, limit_density=0.002, seed=11)
+    assert max(d for _, d in prob["row_cones"]) > 8192
+    _parity(prob, iters=70, check_freq=32)
+
+
 def _full(prob, **kw):
     P = _gpu()
     g = P.solve(prob, max_iter=100000, time_limit=120.0, **kw)

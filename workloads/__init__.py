@@ -24,8 +24,9 @@ ZERO, NONNEG, SOC, RSOC, EXP, DUAL_EXP = 0, 1, 2, 3, 4, 5
 
 def _pack(G, h, c, nb, lo, hi, row_cones, col_cones, meta):
     G = sp.csr_matrix(G, dtype=np.float64)
-    G.sum_duplicates()
-    G.sort_indices()
+    if not G.has_canonical_format:
+        G.sum_duplicates()
+        G.sort_indices()
     m, n = G.shape
     return dict(m=int(m), n=int(n), row_ptr=G.indptr.astype(np.int64),
                 col_idx=G.indices.astype(np.int32), val=G.data.astype(np.float64),
@@ -146,29 +147,22 @@ def portfolio(n=200_000, k=200, n_limits=1000, limit_density=1e-3, limit_nnz_min
         ub = A @ np.full(n, 1.0 / n) + rng.uniform(0.0, 1.0, size=n_limits) / n
         limits = (A, ub)
     A, ub = limits
+    A = sp.csr_matrix(A)
+    A.sort_indices()
     nv = n + 1                                   # x then t
-    t_col = n
-    blocks = []
-    hs = []
-    # zero row: 1^T x - 1 = 0
-    blocks.append(sp.csr_matrix((np.ones(n), (np.zeros(n, int), np.arange(n))), shape=(1, nv)))
-    hs.append(np.array([1.0]))
-    # limits: -a_j^T x - (-u_j) >= 0
+    k = F.shape[1]
     L = A.shape[0]
-    if L:
-        blocks.append(sp.hstack([-A, sp.csr_matrix((L, 1))], format="csr"))
-        hs.append(-ub)
-    # RSOC block rows: p = t, q = 1/2, F^T x, sqrt(d) x
-    blocks.append(sp.csr_matrix(([1.0], ([0], [t_col])), shape=(1, nv)))
-    hs.append(np.array([0.0]))
-    blocks.append(sp.csr_matrix((1, nv)))
-    hs.append(np.array([-0.5]))
-    blocks.append(sp.hstack([sp.csr_matrix(F.T), sp.csr_matrix((F.shape[1], 1))], format="csr"))
-    hs.append(np.zeros(F.shape[1]))
-    blocks.append(sp.csr_matrix((np.sqrt(d), (np.arange(n), np.arange(n))), shape=(n, nv)))
-    hs.append(np.zeros(n))
-    G = sp.vstack(blocks, format="csr")
-    h = np.concatenate(hs)
+    # Rows, assembled directly in CSR form: the budget row 1^T x = 1 (zero
+    # cone); the limits u_j - a_j^T x >= 0 (G row -a_j, h = -u_j); the RSOC
+    # block (t, 1/2, F^T x, sqrt(d) o x) as rows (e_t; 0 with h = -1/2; F^T; diag(sqrt d)).
+    lens = [np.array([n]), np.diff(A.indptr), np.array([1, 0]), np.full(k, n),
+            np.ones(n, dtype=np.int64)]
+    idx = [np.arange(n), A.indices, np.array([n]), np.tile(np.arange(n), k), np.arange(n)]
+    val = [np.ones(n), -A.data, np.array([1.0]), np.ascontiguousarray(F.T).ravel(), np.sqrt(d)]
+    indptr = np.concatenate([[0], np.cumsum(np.concatenate(lens))]).astype(np.int64)
+    G = sp.csr_matrix((np.concatenate(val), np.concatenate(idx).astype(np.int32), indptr),
+                      shape=(1 + L + 2 + k + n, nv))
+    h = np.concatenate([[1.0], -ub, [0.0, -0.5], np.zeros(k), np.zeros(n)])
     c = np.concatenate([-mu, [gamma]])
     row_cones = [(ZERO, 1)] + ([(NONNEG, L)] if L else []) + [(RSOC, F.shape[1] + n + 2)]
     meta = dict(kind="portfolio", seed=seed, n_assets=n, k=F.shape[1], n_limits=L, gamma=gamma)
