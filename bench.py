@@ -58,6 +58,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-iters", type=int, default=12)
+    ap.add_argument("--eager", action="store_true",
+                    help="launch kernels from the host (for per-kernel profilers)")
     return ap.parse_args()
 
 
@@ -190,7 +192,8 @@ def run_ours(args):
         oracle_proc = _oracle_child(args, oracle_out)
 
     prob, desc = _workload(args, rank)
-    opts = dict(precision=args.precision, check_freq=CHECK_FREQ, profile=1, time_limit=3600.0)
+    opts = dict(precision=args.precision, check_freq=CHECK_FREQ, profile=1, time_limit=3600.0,
+                eager=int(args.eager))
 
     def barrier():
         torch.cuda.synchronize()
@@ -216,6 +219,7 @@ def run_ours(args):
     elapsed = ev0.elapsed_time(ev1) / 1000.0
     ck = clocks.stop()
     prof = s.profile()
+    ktimes = s.kernel_times()
     iters = r1["iters"] - it0
     attempts = r1["attempts"] - kb0
     tmax = elapsed
@@ -312,7 +316,8 @@ def run_ours(args):
                 "attempts_per_s": attempts / elapsed, "setup_s": setup_s,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": prof["kernel_launches"], "graph_launches": prof["graph_launches"],
-                "clocks": ck, "time_to_tol": tts}
+                "clocks": ck, "time_to_tol": tts,
+                "kernel_seconds": {k: [round(v[0], 6), v[1]] for k, v in ktimes.items()}}
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()

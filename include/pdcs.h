@@ -101,8 +101,11 @@ typedef struct {
   double bisect_rel_tol;     /* 1e-6: Algorithm 3 stops when t_r - t_l <= tol * t_r */
   int32_t verbose;           /* 0 silent, 1 one line per check period on stderr */
   int32_t trace_capacity;    /* >0: record one trace row per accepted iteration */
-  int32_t profile;           /* 1: time the SpMV launches of every attempt on the
-                                device (see pdcs_get_profile) */
+  int32_t profile;           /* 1: time every kernel launch on the device (see
+                                pdcs_get_profile and pdcs_get_kernel_times) */
+  int32_t eager;             /* 1: launch the kernels one by one from the host
+                                instead of replaying captured graphs (slower; for
+                                per-kernel profilers) */
 } pdcs_options;
 
 typedef struct {
@@ -227,6 +230,18 @@ typedef struct {
 } pdcs_profile;
 
 int pdcs_get_profile(pdcs_handle* handle, pdcs_profile* prof);
+
+/* Device time of every kernel class during the last pdcs_solve / pdcs_resume
+ * (requires options.profile = 1; *count = 0 otherwise), measured like
+ * pdcs_profile.  Up to cap entries, in this order: spmv_g (G xhat), spmv_gt
+ * (G^T yhat), spmv_check (products at checks and restarts), soc_grid (grid-wide
+ * SOC projection), soc_cta (per-CTA SOC projection), exp (exponential-cone
+ * projection), primal, dual, step (step-size test), res_prep, stats_attempt
+ * (maxErr of zhat), stats_check (KKT statistics of the candidates), halpern,
+ * probe_prep, probe_reduce (Algorithm 3 probes), check_misc. */
+#define PDCS_KERNEL_CLASSES 16
+int pdcs_get_kernel_times(pdcs_handle* handle, double* seconds, int64_t* launches, int32_t cap,
+                          int32_t* count);
 
 /* Sizes after set-up (m, n of the reformulated problem, nnz of G). */
 int pdcs_get_sizes(pdcs_handle* handle, int64_t* m, int64_t* n, int64_t* nnz);

@@ -34,7 +34,8 @@ class PdcsOptions(ctypes.Structure):
                 ("use_adaptive_restart", ctypes.c_int32), ("check_freq", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("require_abs", ctypes.c_int32),
                 ("bisect_rel_tol", ctypes.c_double), ("verbose", ctypes.c_int32),
-                ("trace_capacity", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("trace_capacity", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("eager", ctypes.c_int32)]
 
 
 class PdcsResult(ctypes.Structure):
@@ -67,9 +68,13 @@ class PdcsProfile(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64)]
 
 
+KERNEL_CLASSES = ("spmv_g", "spmv_gt", "spmv_check", "soc_grid", "soc_cta", "exp", "primal", "dual",
+                  "step", "res_prep", "stats_attempt", "stats_check", "halpern", "probe_prep",
+                  "probe_reduce", "check_misc")
+
 EXPORTS = ("pdcs_default_options", "pdcs_setup", "pdcs_solve", "pdcs_resume", "pdcs_get_state",
            "pdcs_set_state", "pdcs_get_iterate", "pdcs_get_trace", "pdcs_get_profile",
-           "pdcs_get_sizes", "pdcs_free", "pdcs_last_error")
+           "pdcs_get_kernel_times", "pdcs_get_sizes", "pdcs_free", "pdcs_last_error")
 
 _LIB = None
 
@@ -108,6 +113,8 @@ def lib():
     L.pdcs_get_trace.restype = ctypes.c_int
     L.pdcs_get_profile.argtypes = [vp, ctypes.POINTER(PdcsProfile)]
     L.pdcs_get_profile.restype = ctypes.c_int
+    L.pdcs_get_kernel_times.argtypes = [vp, vp, vp, i32, ctypes.POINTER(i32)]
+    L.pdcs_get_kernel_times.restype = ctypes.c_int
     L.pdcs_get_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.pdcs_get_sizes.restype = ctypes.c_int
     L.pdcs_free.argtypes = [vp]
@@ -268,6 +275,15 @@ class Solver:
         pr = PdcsProfile()
         _check(lib().pdcs_get_profile(self._h, ctypes.byref(pr)))
         return {k: getattr(pr, k) for k, _ in PdcsProfile._fields_}
+
+    def kernel_times(self):
+        """{kernel class: (seconds, launches)} of the last solve / resume."""
+        k = len(KERNEL_CLASSES)
+        sec = np.zeros(k)
+        la = np.zeros(k, dtype=np.int64)
+        cnt = ctypes.c_int32()
+        _check(lib().pdcs_get_kernel_times(self._h, _ptr(sec), _ptr(la), k, ctypes.byref(cnt)))
+        return {KERNEL_CLASSES[i]: (float(sec[i]), int(la[i])) for i in range(cnt.value)}
 
     def trace(self):
         cap = int(self.options.trace_capacity)

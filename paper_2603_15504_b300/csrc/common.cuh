@@ -73,4 +73,50 @@ PDCS_DEV bool last_block_done(unsigned int* counter) {
   return last;
 }
 
+// Live kernel timer: span from the first CTA's start to the last CTA's end of
+// each launch, read from %globaltimer (ns) and accumulated on the device.  A
+// NULL timer disables the bookkeeping.  ktimer_end must be reached by every
+// thread of the CTA.
+struct KTimer {
+  unsigned long long start;  // ~0 between launches
+  unsigned long long total_ns;
+  unsigned int ticket;
+  unsigned int launches;
+};
+
+PDCS_DEV unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+PDCS_DEV void ktimer_begin(KTimer* tm) {
+  if (tm != nullptr && threadIdx.x == 0) atomicMin(&tm->start, global_ns());
+}
+
+PDCS_DEV void ktimer_end(KTimer* tm) {
+  if (tm == nullptr) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int tk = atomicAdd(&tm->ticket, 1u);
+    if (tk == gridDim.x * gridDim.y - 1) {
+      __threadfence();
+      const unsigned long long t1 = global_ns();
+      const unsigned long long t0 = atomicAdd(&tm->start, 0ull);
+      tm->total_ns += t1 > t0 ? t1 - t0 : 0ull;
+      tm->launches += 1u;
+      tm->start = ~0ull;
+      tm->ticket = 0u;
+    }
+  }
+}
+
+// Timer slots of one solver (pdcs_get_kernel_times lists them in this order).
+enum : int { TM_SPMV_G = 0, TM_SPMV_GT, TM_SPMV_CHECK, TM_SOC_GRID, TM_SOC_CTA, TM_EXP, TM_PRIMAL,
+             TM_DUAL, TM_STEP, TM_RES_PREP, TM_STATS_ATTEMPT, TM_STATS_CHECK, TM_HALPERN,
+             TM_PROBE_PREP, TM_PROBE_REDUCE, TM_CHECK_MISC, TM_NUM };
+
+PDCS_DEV KTimer* tslot(KTimer* base, int id) { return base == nullptr ? nullptr : base + id; }
+
 }  // namespace pdcs

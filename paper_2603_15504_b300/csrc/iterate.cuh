@@ -68,6 +68,7 @@ struct Prob {
   const double* d2;
   const uint8_t* rk;
   const uint8_t* ck;
+  KTimer* tm;  // timer slots (NULL: not profiling)
 };
 
 template <typename T>
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(kEwThreads) k_primal(Prob<T> p, const Ctl* __r
                                                        const T* __restrict__ gty,
                                                        T* __restrict__ xh) {
   if (!ctl->g_attempt) return;
+  ktimer_begin(tslot(p.tm, TM_PRIMAL));
   const double tau = ctl->eta / ctl->omega;
   PDCS_GRID_LOOP(j, p.n) {
     double v = (double)x[j] - tau * ((double)p.c[j] - (double)gty[j]);
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(kEwThreads) k_primal(Prob<T> p, const Ctl* __r
     else if (kd == CK_NONNEG) v = fmax(v, 0.0);
     xh[j] = (T)v;
   }
+  ktimer_end(tslot(p.tm, TM_PRIMAL));
 }
 
 // yhat = Proj_Y(y + sigma (h - G (2 xhat - x))), sigma = eta omega.
@@ -116,12 +119,14 @@ __global__ void __launch_bounds__(kEwThreads) k_dual(Prob<T> p, const Ctl* __res
                                                      const T* __restrict__ gx,
                                                      T* __restrict__ yh) {
   if (!ctl->g_attempt) return;
+  ktimer_begin(tslot(p.tm, TM_DUAL));
   const double sigma = ctl->eta * ctl->omega;
   PDCS_GRID_LOOP(i, p.m) {
     double v = (double)y[i] + sigma * ((double)p.h[i] - 2.0 * (double)gxh[i] + (double)gx[i]);
     if (p.rk[i] == RK_NONNEG) v = fmax(v, 0.0);
     yh[i] = (T)v;
   }
+  ktimer_end(tslot(p.tm, TM_DUAL));
 }
 
 // Step-size test of Function 1 (eq. adaptive_step_size).  kbar counts every
@@ -136,6 +141,7 @@ __global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict_
                                                      const T* __restrict__ gx,
                                                      double* __restrict__ part) {
   if (!ctl->g_attempt) return;
+  ktimer_begin(tslot(p.tm, TM_STEP));
   __shared__ double sh[3 * kEwThreads / 32];
   double s[3] = {0.0, 0.0, 0.0};
   PDCS_GRID_LOOP(j, p.n) {
@@ -151,6 +157,7 @@ __global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict_
   if (threadIdx.x == 0) {
     for (int k = 0; k < 3; ++k) part[blockIdx.x * 3 + k] = s[k];
   }
+  ktimer_end(tslot(p.tm, TM_STEP));
   if (!last_block_done(&ctl->cnt[CNT_STEP])) return;
   if (threadIdx.x != 0) return;
   double dx2 = 0.0, dy2 = 0.0, inter = 0.0;
@@ -192,15 +199,19 @@ PDCS_DEV double cone_scale(const double* d, int64_t i, int inv) {
 // Exponential-cone blocks: one thread per 3-vector.  Target cone diag(e) K' with
 // e = d or 1/d (inv) and K' = K_exp or K_exp^* (is_dual_exp[b] xor dual).
 // blockIdx.y selects one of two vectors (each with its own gate).
+PDCS_DEV bool gate_on(const int* g) { return g == nullptr || *g != 0; }
+
 template <typename B>
 __global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
                            const uint8_t* __restrict__ isd, int64_t count,
                            const double* __restrict__ d, int inv, int dual,
-                           const int* __restrict__ gate0, const int* __restrict__ gate1) {
+                           const int* __restrict__ gate0, const int* __restrict__ gate1,
+                           KTimer* tm) {
   B* v = blockIdx.y == 0 ? v0 : v1;
-  const int* gate = blockIdx.y == 0 ? gate0 : gate1;
-  if (gate != nullptr && *gate == 0) return;
-  PDCS_GRID_LOOP(b, count) {
+  const bool on = gate_on(blockIdx.y == 0 ? gate0 : gate1);
+  if (!gate_on(gate0) && (gridDim.y == 1 || !gate_on(gate1))) return;  // whole launch idle
+  ktimer_begin(tm);
+  if (on) PDCS_GRID_LOOP(b, count) {
     const int64_t s = starts[b];
     const double in[3] = {(double)v[s], (double)v[s + 1], (double)v[s + 2]};
     const double e[3] = {cone_scale(d, s, inv), cone_scale(d, s + 1, inv), cone_scale(d, s + 2, inv)};
@@ -210,6 +221,7 @@ __global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
     v[s + 1] = (B)out[1];
     v[s + 2] = (B)out[2];
   }
+  ktimer_end(tm);
 }
 
 // Second-order-cone blocks: one CTA per block (dims <= NT * EPT); target cone
@@ -219,10 +231,14 @@ __global__ void __launch_bounds__(NT) k_cone_soc(B* v0, B* v1, const int64_t* __
                                                  const int32_t* __restrict__ dims,
                                                  const double* __restrict__ d, int inv,
                                                  const int* __restrict__ gate0,
-                                                 const int* __restrict__ gate1) {
+                                                 const int* __restrict__ gate1, KTimer* tm) {
   B* v = blockIdx.y == 0 ? v0 : v1;
-  const int* gate = blockIdx.y == 0 ? gate0 : gate1;
-  if (gate != nullptr && *gate == 0) return;
+  if (!gate_on(gate0) && (gridDim.y == 1 || !gate_on(gate1))) return;  // whole launch idle
+  ktimer_begin(tm);
+  if (!gate_on(blockIdx.y == 0 ? gate0 : gate1)) {
+    ktimer_end(tm);
+    return;
+  }
   __shared__ double sh[8 + 2 * (NT / 32) + 8];
   const int64_t s = starts[blockIdx.x];
   const int dim = dims[blockIdx.x];
@@ -239,6 +255,7 @@ __global__ void __launch_bounds__(NT) k_cone_soc(B* v0, B* v1, const int64_t* __
     const int i = threadIdx.x + k * NT;
     if (i < dim) v[s + i] = (B)vv[k];
   }
+  ktimer_end(tm);
 }
 
 // --------------------------------------------------------- KKT statistics
@@ -250,6 +267,7 @@ __global__ void __launch_bounds__(kEwThreads) k_res_prep(Prob<T> p, const int* _
                                                          PointRef<T> a, PointRef<T> b,
                                                          TmpRef ta, TmpRef tb) {
   if (gate != nullptr && *gate == 0) return;
+  ktimer_begin(tslot(p.tm, TM_RES_PREP));
   const PointRef<T> pt = blockIdx.y == 0 ? a : b;
   const TmpRef tr = blockIdx.y == 0 ? ta : tb;
   PDCS_GRID_LOOP(i, p.m) {
@@ -266,6 +284,7 @@ __global__ void __launch_bounds__(kEwThreads) k_res_prep(Prob<T> p, const int* _
       if (tr.un) tr.un[j] = l / p.d2[j];
     }
   }
+  ktimer_end(tslot(p.tm, TM_RES_PREP));
 }
 
 // Projection onto Lambda_j (Sec. 1.1): {0}, R^-, R^+ or R by bound finiteness.
@@ -310,6 +329,8 @@ __global__ void __launch_bounds__(kEwThreads) k_point_stats(Prob<T> p, Ctl* __re
                                                             const T* __restrict__ y0, TmpRef tr,
                                                             double* __restrict__ part) {
   if (gate != nullptr && *gate == 0) return;
+  KTimer* tmr = tslot(p.tm, slot == 0 ? TM_STATS_ATTEMPT : TM_STATS_CHECK);
+  ktimer_begin(tmr);
   __shared__ double sh[kStatK * kEwThreads / 32];
   double s[kStatSums];
   double mx[kStatMax];
@@ -382,6 +403,7 @@ __global__ void __launch_bounds__(kEwThreads) k_point_stats(Prob<T> p, Ctl* __re
     for (int k = 0; k < kStatSums; ++k) part[blockIdx.x * kStatK + k] = s[k];
     for (int k = 0; k < kStatMax; ++k) part[blockIdx.x * kStatK + kStatSums + k] = mx[k];
   }
+  ktimer_end(tmr);
   if (!last_block_done(&ctl->cnt[CNT_STATS0 + slot])) return;
   if (threadIdx.x != 0) return;
   double S[kStatSums], M[kStatMax];
@@ -416,6 +438,7 @@ __global__ void __launch_bounds__(kEwThreads) k_halpern(
     const T* __restrict__ y0, const T* __restrict__ gx0, const T* __restrict__ gty0,
     double* __restrict__ xs, double* __restrict__ ys, double* __restrict__ trace) {
   if (!ctl->g_accept) return;
+  ktimer_begin(tslot(p.tm, TM_HALPERN));
   const double kk = (double)ctl->k;
   const double beta = ctl->beta, eta = ctl->eta_acc;
   const double a = (kk + 1.0) / (kk + 2.0), b = 1.0 / (kk + 2.0);
@@ -431,6 +454,7 @@ __global__ void __launch_bounds__(kEwThreads) k_halpern(
     ys[i] += eta * (double)yn;
     gx[i] = (T)(a * ((1.0 + beta) * (double)gxh[i] - beta * (double)gx[i]) + b * (double)gx0[i]);
   }
+  ktimer_end(tslot(p.tm, TM_HALPERN));
   if (!last_block_done(&ctl->cnt[CNT_HALPERN])) return;
   if (threadIdx.x != 0) return;
   ctl->cnt[CNT_HALPERN] = 0u;
@@ -459,20 +483,21 @@ __global__ void __launch_bounds__(kEwThreads) k_halpern(
 
 // Body terminator of the attempt loop: continue while the period needs more
 // accepted iterations (bounded by guard_cap bodies per graph launch).
-__global__ void k_loop_ctl(Ctl* ctl, cudaGraphConditionalHandle h) {
+// (use_cond = 0: launched eagerly from the host, which reads g_attempt itself.)
+__global__ void k_loop_ctl(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
   ctl->guard += 1;
   ctl->bodies_a += 1;
   const int go = (ctl->status == kRunning && !ctl->period_done && ctl->guard < ctl->guard_cap);
   ctl->g_attempt = go;
-  cudaGraphSetConditional(h, go ? 1u : 0u);
+  if (use_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
-__global__ void k_period_begin(Ctl* ctl, cudaGraphConditionalHandle h) {
+__global__ void k_period_begin(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
   ctl->guard = 0;
   const int go = (ctl->status == kRunning && !ctl->period_done);
   ctl->g_attempt = go;
   ctl->g_accept = 0;
-  cudaGraphSetConditional(h, go ? 1u : 0u);
+  if (use_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 // ------------------------------------------------------------------ check
@@ -480,17 +505,20 @@ template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_average(int64_t n, int64_t m, const Ctl* __restrict__ ctl,
                                                         const double* __restrict__ xs,
                                                         const double* __restrict__ ys,
-                                                        T* __restrict__ xb, T* __restrict__ yb) {
+                                                        T* __restrict__ xb, T* __restrict__ yb,
+                                                        KTimer* tm) {
   if (!ctl->g_check) return;
+  ktimer_begin(tm);
   const double w = ctl->wsum;
   PDCS_GRID_LOOP(j, n) xb[j] = (T)(xs[j] / w);
   PDCS_GRID_LOOP(i, m) yb[i] = (T)(ys[i] / w);
+  ktimer_end(tm);
 }
 
 // Algorithm 3 set-up for both candidates: r = ||z_c - z^{t,0}||_N, and the first
 // trial t0 = r / sqrt(tau ||b1||^2 + sigma ||b2||^2) (the unconstrained step that
 // reaches radius r).
-__global__ void k_bisect_init(Ctl* ctl, cudaGraphConditionalHandle h) {
+__global__ void k_bisect_init(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
   int any = 0;
   const double tau = ctl->eta_acc / ctl->omega, sigma = ctl->eta_acc * ctl->omega;
   for (int c = 0; c < 2; ++c) {
@@ -519,7 +547,7 @@ __global__ void k_bisect_init(Ctl* ctl, cudaGraphConditionalHandle h) {
     any = 1;
   }
   ctl->probes = 0;
-  cudaGraphSetConditional(h, any ? 1u : 0u);
+  if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 PDCS_DEV double probe_t(const Bisect& b) { return b.phase == BS_EXP ? b.t : 0.5 * (b.tl + b.tr); }
@@ -535,7 +563,13 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_prep(Prob<T> p, const Ctl*
                                                            double* __restrict__ py1) {
   const int c = blockIdx.y;
   const Bisect& bs = ctl->bs[c];
-  if (!bs.active) return;
+  if (!ctl->bs[0].active && !ctl->bs[1].active) return;  // whole launch idle
+  KTimer* tm = tslot(p.tm, TM_PROBE_PREP);
+  ktimer_begin(tm);
+  if (!bs.active) {
+    ktimer_end(tm);
+    return;
+  }
   const PointRef<T> pt = c == 0 ? a : bpt;
   double* px = c == 0 ? px0 : px1;
   double* py = c == 0 ? py0 : py1;
@@ -556,6 +590,7 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_prep(Prob<T> p, const Ctl*
     if (p.rk[i] == RK_NONNEG) v = fmax(v, 0.0);
     py[i] = v;
   }
+  ktimer_end(tm);
 }
 
 // ||z(t) - z||_N and b^T (z(t) - z) for both candidates; the last CTA advances
@@ -568,9 +603,11 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __r
                                                              const double* __restrict__ px1,
                                                              const double* __restrict__ py1,
                                                              double* __restrict__ part,
-                                                             cudaGraphConditionalHandle h) {
+                                                             cudaGraphConditionalHandle h,
+                                                             int use_cond) {
   const int c = blockIdx.y;
   const Bisect& bs = ctl->bs[c];
+  ktimer_begin(tslot(p.tm, TM_PROBE_REDUCE));
   __shared__ double sh[4 * kEwThreads / 32];
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   if (bs.active) {
@@ -592,6 +629,7 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __r
   if (threadIdx.x == 0) {
     for (int k = 0; k < 4; ++k) part[(blockIdx.y * gridDim.x + blockIdx.x) * 4 + k] = s[k];
   }
+  ktimer_end(tslot(p.tm, TM_PROBE_REDUCE));
   if (!last_block_done(&ctl->cnt[CNT_PROBE])) return;
   if (threadIdx.x != 0) return;
   ctl->cnt[CNT_PROBE] = 0u;
@@ -638,7 +676,7 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __r
     }
     any = 0;
   }
-  cudaGraphSetConditional(h, any ? 1u : 0u);
+  if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 PDCS_DEV double kkt_w(double ep, double ed, double eg, double w) {
@@ -720,8 +758,9 @@ template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_cand_copy(int64_t n, int64_t m, const Ctl* __restrict__ ctl,
                                                           PointRef<T> z, PointRef<T> zb, T* xc, T* yc,
                                                           T* gxc, T* gtyc, T* x0, T* y0, T* x, T* y,
-                                                          double* xs, double* ys) {
+                                                          double* xs, double* ys, KTimer* tm) {
   if (!ctl->g_check) return;
+  ktimer_begin(tm);
   const PointRef<T> s = ctl->cand ? zb : z;
   const bool rs = ctl->g_restart != 0;
   PDCS_GRID_LOOP(j, n) {
@@ -736,14 +775,18 @@ __global__ void __launch_bounds__(kEwThreads) k_cand_copy(int64_t n, int64_t m, 
     yc[i] = v;
     if (rs) { y0[i] = v; y[i] = v; ys[i] = 0.0; }
   }
+  ktimer_end(tm);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_copy_products(int64_t n, int64_t m, const int* __restrict__ gate,
-                                                              const T* gx0, const T* gty0, T* gx, T* gty) {
+                                                              const T* gx0, const T* gty0, T* gx, T* gty,
+                                                              KTimer* tm) {
   if (!*gate) return;
+  ktimer_begin(tm);
   PDCS_GRID_LOOP(j, n) gty[j] = gty0[j];
   PDCS_GRID_LOOP(i, m) gx[i] = gx0[i];
+  ktimer_end(tm);
 }
 
 __global__ void k_check_end(Ctl* ctl) {
@@ -882,8 +925,11 @@ __global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
                                                        int nblocks, const double* __restrict__ d,
                                                        int inv, const int* __restrict__ gate0,
                                                        const int* __restrict__ gate1,
-                                                       double* __restrict__ part, GridSync gs) {
+                                                       double* __restrict__ part, GridSync gs,
+                                                       KTimer* tm) {
   __shared__ double sh[2 * 512 / 32 + 8];
+  if (!gate_on(gate0) && (nvec == 1 || !gate_on(gate1))) return;  // whole launch idle
+  ktimer_begin(tm);
   unsigned int target = 0;
   int flip = 0;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -982,6 +1028,7 @@ __global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
       if (tid == 0) v[s] = (B)(pos ? v0h * e02 / (e02 - mu2) : v0h * e02 * x / (e02 * x - 1.0));
     }
   }
+  ktimer_end(tm);
 }
 
 }  // namespace pdcs

@@ -190,6 +190,7 @@ struct ConeTable {
   double* gpart = nullptr;
   GridSync gsync = {nullptr, nullptr};
   int big_grid = 0;
+  KTimer* timers = nullptr;  // profiling slots (NULL: off)
 };
 
 __global__ void k_zero_u32(unsigned int* p) { *p = 0u; }
@@ -203,16 +204,19 @@ static const int kSocTierMax[3] = {128, 4096, 8192};
 template <typename B>
 static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d, int inv, int dual,
                     const int* g0, const int* g1, cudaStream_t st) {
+  KTimer* tm = t.timers;
   if (t.nexp > 0) {
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((t.nexp + 127) / 128, 148 * 8)), nvec);
-    k_cone_exp<B><<<grid, 128, 0, st>>>(v0, v1, t.exp_s, t.exp_isd, t.nexp, d, inv, dual, g0, g1);
+    k_cone_exp<B><<<grid, 128, 0, st>>>(v0, v1, t.exp_s, t.exp_isd, t.nexp, d, inv, dual, g0, g1,
+                                         tm ? tm + TM_EXP : nullptr);
   }
+  KTimer* tsc = tm ? tm + TM_SOC_CTA : nullptr;
   if (t.nsoc[0] > 0)
-    k_cone_soc<B, 32, 4><<<dim3((unsigned)t.nsoc[0], nvec), 32, 0, st>>>(v0, v1, t.soc_s[0], t.soc_d[0], d, inv, g0, g1);
+    k_cone_soc<B, 32, 4><<<dim3((unsigned)t.nsoc[0], nvec), 32, 0, st>>>(v0, v1, t.soc_s[0], t.soc_d[0], d, inv, g0, g1, tsc);
   if (t.nsoc[1] > 0)
-    k_cone_soc<B, 256, 16><<<dim3((unsigned)t.nsoc[1], nvec), 256, 0, st>>>(v0, v1, t.soc_s[1], t.soc_d[1], d, inv, g0, g1);
+    k_cone_soc<B, 256, 16><<<dim3((unsigned)t.nsoc[1], nvec), 256, 0, st>>>(v0, v1, t.soc_s[1], t.soc_d[1], d, inv, g0, g1, tsc);
   if (t.nsoc[2] > 0)
-    k_cone_soc<B, 512, 16><<<dim3((unsigned)t.nsoc[2], nvec), 512, 0, st>>>(v0, v1, t.soc_s[2], t.soc_d[2], d, inv, g0, g1);
+    k_cone_soc<B, 512, 16><<<dim3((unsigned)t.nsoc[2], nvec), 512, 0, st>>>(v0, v1, t.soc_s[2], t.soc_d[2], d, inv, g0, g1, tsc);
   if (t.nbig > 0) {
     k_zero_u32<<<1, 1, 0, st>>>(t.gsync.count);
     cudaLaunchConfig_t cfg = {};
@@ -226,7 +230,8 @@ static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d,
     cfg.attrs = at;
     cfg.numAttrs = 1;
     CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B>, v0, v1, nvec, (const int64_t*)t.big_s,
-                          (const int64_t*)t.big_d, t.nbig, d, inv, g0, g1, t.gpart, t.gsync));
+                          (const int64_t*)t.big_d, t.nbig, d, inv, g0, g1, t.gpart, t.gsync,
+                          tm ? tm + TM_SOC_GRID : (KTimer*)nullptr));
   }
 }
 
@@ -247,6 +252,7 @@ struct SolverBase {
                          const double* ys) = 0;
   virtual void get_iterate(int which, double* x, double* y) = 0;
   virtual void get_profile(pdcs_profile* pr) = 0;
+  virtual int get_kernel_times(double* sec, int64_t* launches, int cap) = 0;
   virtual int64_t get_trace(double* out, int64_t cap) = 0;
   int64_t m = 0, n = 0, nnz = 0;
 };
@@ -289,7 +295,7 @@ struct Solver : SolverBase {
   double *obuf_n = nullptr, *obuf_m = nullptr, *obuf_s = nullptr;
   Ctl* ctl = nullptr;
   Ctl* hctl = nullptr;
-  KTimer* timers = nullptr;             // [0] G xhat, [1] G^T yhat (profile option)
+  KTimer* timers = nullptr;             // TM_NUM slots (profile option)
   unsigned int* gsync_count = nullptr;  // grid barrier of k_cone_soc_grid
   int* gsync_err = nullptr;             // set if a bounded barrier wait gave up
   double* gpart = nullptr;
@@ -297,6 +303,7 @@ struct Solver : SolverBase {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   int64_t trace_rows = 0;
+  int use_cond = 1;  // 0 in eager mode (kernels launched from the host, no graphs)
   int64_t nk_a = 0, nk_b = 0, nk_top = 0;  // kernel nodes: attempt body, probe body, top level
   int64_t graph_launches = 0;
   long long bodies_a0 = 0, bodies_b0 = 0;  // loop-body counters at the start of the call
@@ -304,7 +311,7 @@ struct Solver : SolverBase {
   Prob<T> prob() const {
     Prob<T> p;
     p.m = m; p.n = n; p.nb = nb; p.h = h; p.c = c; p.lo = lo; p.hi = hi; p.d1 = d1; p.d2 = d2;
-    p.rk = rk; p.ck = ck;
+    p.rk = rk; p.ck = ck; p.tm = timers;
     return p;
   }
 
@@ -499,7 +506,8 @@ struct Solver : SolverBase {
     planG = build_plan(hrp, ar, st);
     planGT = build_plan(hrpT, ar, st);
     alloc_state();
-    capture();
+    if (opt.eager) use_cond = 0;
+    else capture();
   }
 
   // Per-element kinds and cone tables from an ordered cone list starting at off.
@@ -679,16 +687,31 @@ struct Solver : SolverBase {
     obuf_s = ar.alloc<double>(m);
     if (opt.trace_capacity > 0) trace = ar.alloc<double>((int64_t)opt.trace_capacity * PDCS_TRACE_FIELDS);
     if (opt.profile) {
-      timers = ar.alloc<KTimer>(2);
+      timers = ar.alloc<KTimer>(TM_NUM);
       reset_timers();
     }
+    rows.timers = timers;
+    cols.timers = timers;
   }
 
   void reset_timers() {
     if (!timers) return;
-    KTimer z[2];
+    KTimer z[TM_NUM];
     for (auto& t : z) { t.start = ~0ull; t.total_ns = 0; t.ticket = 0; t.launches = 0; }
     CK(cudaMemcpyAsync(timers, z, sizeof(z), cudaMemcpyHostToDevice, st));
+  }
+
+  int get_kernel_times(double* sec, int64_t* launches, int cap) override {
+    if (!timers) return 0;
+    KTimer z[TM_NUM];
+    CK(cudaMemcpyAsync(z, timers, sizeof(z), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int k = std::min(cap, (int)TM_NUM);
+    for (int i = 0; i < k; ++i) {
+      if (sec) sec[i] = 1e-9 * (double)z[i].total_ns;
+      if (launches) launches[i] = z[i].launches;
+    }
+    return k;
   }
 
   void get_profile(pdcs_profile* pr) override {
@@ -701,7 +724,7 @@ struct Solver : SolverBase {
     pr->kernel_launches = graph_launches * nk_top + (hctl->bodies_a - bodies_a0) * nk_a +
                           (hctl->bodies_b - bodies_b0) * nk_b;
     if (!timers) return;
-    KTimer z[2];
+    KTimer z[TM_NUM];
     CK(cudaMemcpyAsync(z, timers, sizeof(z), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     pr->g_launches = z[0].launches;
@@ -745,11 +768,11 @@ struct Solver : SolverBase {
     const int gn = ew_grid(n), gm = ew_grid(m), gmx = ew_grid(std::max(m, n));
     k_primal<T><<<gn, kEwThreads, 0, s>>>(p, ctl, x, gty, xh);
     project<T>(cols, xh, xh, 1, d2, 1, 0, &ctl->g_attempt, nullptr, s);
-    launch_spmv<T>(planG, rp, ci, vv, xh, gxh, &ctl->g_attempt, s, timers);
+    launch_spmv<T>(planG, rp, ci, vv, xh, gxh, &ctl->g_attempt, s, timers ? timers + TM_SPMV_G : nullptr);
     k_dual<T><<<gm, kEwThreads, 0, s>>>(p, ctl, y, gxh, gx, yh);
     project<T>(rows, yh, yh, 1, d1, 1, 1, &ctl->g_attempt, nullptr, s);
     k_step<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, xh, y, yh, gxh, gx, part);
-    launch_spmv<T>(planGT, rpT, ciT, vvT, yh, gtyh, &ctl->g_accept, s, timers ? timers + 1 : nullptr);
+    launch_spmv<T>(planGT, rpT, ciT, vvT, yh, gtyh, &ctl->g_accept, s, timers ? timers + TM_SPMV_GT : nullptr);
     const PointRef<T> ph{xh, yh, gxh, gtyh};
     const TmpRef t0{tm[0], tn[0], nullptr, nullptr};
     k_res_prep<T><<<dim3(gmx, 1), kEwThreads, 0, s>>>(p, &ctl->g_accept, ph, ph, t0, t0);
@@ -757,16 +780,18 @@ struct Solver : SolverBase {
     project<double>(cols, tn[0], tn[0], 1, d2, 0, 1, &ctl->g_accept, nullptr, s);
     k_point_stats<T, false><<<gmx, kEwThreads, 0, s>>>(p, ctl, &ctl->g_accept, 0, ph, nullptr, nullptr, t0, part);
     k_halpern<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, y, gx, gty, xh, yh, gxh, gtyh, x0, y0, gx0, gty0, xs, ys, trace);
-    k_loop_ctl<<<1, 1, 0, s>>>(ctl, hA);
+    k_loop_ctl<<<1, 1, 0, s>>>(ctl, hA, use_cond);
   }
 
   void rec_check_stats(cudaStream_t s) {
     const Prob<T> p = prob();
     const int gmx = ew_grid(std::max(m, n));
     int* g = &ctl->g_check;
-    k_average<T><<<gmx, kEwThreads, 0, s>>>(n, m, ctl, xs, ys, xb, yb);
-    launch_spmv<T>(planG, rp, ci, vv, xb, gxb, g, s);
-    launch_spmv<T>(planGT, rpT, ciT, vvT, yb, gtyb, g, s);
+    KTimer* tmisc = timers ? timers + TM_CHECK_MISC : nullptr;
+    KTimer* tchk = timers ? timers + TM_SPMV_CHECK : nullptr;
+    k_average<T><<<gmx, kEwThreads, 0, s>>>(n, m, ctl, xs, ys, xb, yb, tmisc);
+    launch_spmv<T>(planG, rp, ci, vv, xb, gxb, g, s, tchk);
+    launch_spmv<T>(planGT, rpT, ciT, vvT, yb, gtyb, g, s, tchk);
     const TmpRef ta{tm[0], tn[0], um[0], un[0]}, tb{tm[1], tn[1], um[1], un[1]};
     k_res_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, g, pz(), pzb(), ta, tb);
     project<double>(rows, tm[0], tm[1], 2, d1, 0, 0, g, g, s);
@@ -783,16 +808,18 @@ struct Solver : SolverBase {
     k_probe_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pz(), pzb(), px[0], py[0], px[1], py[1]);
     project<double>(cols, px[0], px[1], 2, d2, 1, 0, &ctl->bs[0].active, &ctl->bs[1].active, s);
     project<double>(rows, py[0], py[1], 2, d1, 1, 1, &ctl->bs[0].active, &ctl->bs[1].active, s);
-    k_probe_reduce<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pz(), pzb(), px[0], py[0], px[1], py[1], part, hB);
+    k_probe_reduce<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pz(), pzb(), px[0], py[0], px[1], py[1], part, hB, use_cond);
   }
 
   void rec_check_end(cudaStream_t s) {
     const int gmx = ew_grid(std::max(m, n));
     k_check_decide<<<1, 1, 0, s>>>(ctl, trace);
-    k_cand_copy<T><<<gmx, kEwThreads, 0, s>>>(n, m, ctl, pz(), pzb(), xc, yc, gxc, gtyc, x0, y0, x, y, xs, ys);
-    launch_spmv<T>(planG, rp, ci, vv, x0, gx0, &ctl->g_restart, s);
-    launch_spmv<T>(planGT, rpT, ciT, vvT, y0, gty0, &ctl->g_restart, s);
-    k_copy_products<T><<<gmx, kEwThreads, 0, s>>>(n, m, &ctl->g_restart, gx0, gty0, gx, gty);
+    KTimer* tmisc = timers ? timers + TM_CHECK_MISC : nullptr;
+    KTimer* tchk = timers ? timers + TM_SPMV_CHECK : nullptr;
+    k_cand_copy<T><<<gmx, kEwThreads, 0, s>>>(n, m, ctl, pz(), pzb(), xc, yc, gxc, gtyc, x0, y0, x, y, xs, ys, tmisc);
+    launch_spmv<T>(planG, rp, ci, vv, x0, gx0, &ctl->g_restart, s, tchk);
+    launch_spmv<T>(planGT, rpT, ciT, vvT, y0, gty0, &ctl->g_restart, s, tchk);
+    k_copy_products<T><<<gmx, kEwThreads, 0, s>>>(n, m, &ctl->g_restart, gx0, gty0, gx, gty, tmisc);
     k_check_end<<<1, 1, 0, s>>>(ctl);
   }
 
@@ -815,13 +842,13 @@ struct Solver : SolverBase {
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     cudaGraphConditionalHandle hA = new_handle(st);
     cudaGraphConditionalHandle hB = new_handle(st);
-    k_period_begin<<<1, 1, 0, st>>>(ctl, hA);
+    k_period_begin<<<1, 1, 0, st>>>(ctl, hA, 1);
     cudaGraph_t bodyA = add_while(st, hA);
     CK(cudaStreamBeginCaptureToGraph(st2, bodyA, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     rec_attempt(st2, hA);
     CK(cudaStreamEndCapture(st2, &bodyA));
     rec_check_stats(st);
-    k_bisect_init<<<1, 1, 0, st>>>(ctl, hB);
+    k_bisect_init<<<1, 1, 0, st>>>(ctl, hB, 1);
     cudaGraph_t bodyB = add_while(st, hB);
     CK(cudaStreamBeginCaptureToGraph(st2, bodyB, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     rec_probe(st2, hB);
@@ -916,6 +943,28 @@ struct Solver : SolverBase {
     run(xo, yo, so, res, t0);
   }
 
+  // One check period launched kernel by kernel from the host (the same kernels
+  // and gates as the captured graph; the host reads the loop conditions).  Slow;
+  // meant for per-kernel profilers, which cannot see inside conditional graphs.
+  int read_flag(const int* dflag) {
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return v;
+  }
+
+  void run_period_eager() {
+    k_period_begin<<<1, 1, 0, st>>>(ctl, 0, 0);
+    for (int guard = 0; guard < 1 << 20 && read_flag(&ctl->g_attempt); ++guard) rec_attempt(st, 0);
+    rec_check_stats(st);
+    k_bisect_init<<<1, 1, 0, st>>>(ctl, 0, 0);
+    for (int guard = 0; guard < 1024 && (read_flag(&ctl->bs[0].active) || read_flag(&ctl->bs[1].active));
+         ++guard)
+      rec_probe(st, 0);
+    rec_check_end(st);
+    CK(cudaGetLastError());
+  }
+
   void run(double* xo, double* yo, double* so, pdcs_result* res,
            std::chrono::steady_clock::time_point t0) {
     int status = kRunning;
@@ -924,7 +973,8 @@ struct Solver : SolverBase {
     bodies_a0 = hctl->bodies_a;
     bodies_b0 = hctl->bodies_b;
     while (true) {
-      CK(cudaGraphLaunch(exec, st));
+      if (use_cond) CK(cudaGraphLaunch(exec, st));
+      else run_period_eager();
       ++graph_launches;
       CK(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -1105,6 +1155,7 @@ void pdcs_default_options(pdcs_options* o) {
   o->verbose = 0;
   o->trace_capacity = 0;
   o->profile = 0;
+  o->eager = 0;
 }
 
 const char* pdcs_last_error(void) { return g_last_error.c_str(); }
@@ -1228,6 +1279,12 @@ int pdcs_get_trace(pdcs_handle* hd, double* out, int64_t cap, int64_t* count) {
 int pdcs_get_profile(pdcs_handle* hd, pdcs_profile* prof) {
   if (!prof) return fail(PDCS_ERR_INVALID, "prof is NULL");
   PDCS_API_BODY(hd->solver->get_profile(prof))
+}
+
+int pdcs_get_kernel_times(pdcs_handle* hd, double* seconds, int64_t* launches, int32_t cap,
+                          int32_t* count) {
+  int k = 0;
+  PDCS_API_BODY(k = hd->solver->get_kernel_times(seconds, launches, cap); if (count) *count = k)
 }
 
 int pdcs_get_sizes(pdcs_handle* hd, int64_t* m, int64_t* n, int64_t* nnz) {

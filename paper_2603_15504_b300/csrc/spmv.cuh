@@ -79,43 +79,6 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
   }
 }
 
-// Live kernel timer: span from the first CTA's start to the last CTA's end of
-// each launch, read from %globaltimer (ns) and accumulated on the device.
-struct KTimer {
-  unsigned long long start;  // ~0 between launches
-  unsigned long long total_ns;
-  unsigned int ticket;
-  unsigned int launches;
-};
-
-PDCS_DEV unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-PDCS_DEV void ktimer_begin(KTimer* tm) {
-  if (tm != nullptr && threadIdx.x == 0) atomicMin(&tm->start, global_ns());
-}
-
-PDCS_DEV void ktimer_end(KTimer* tm) {
-  if (tm == nullptr) return;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int tk = atomicAdd(&tm->ticket, 1u);
-    if (tk == gridDim.x - 1) {
-      __threadfence();
-      const unsigned long long t1 = global_ns();
-      const unsigned long long t0 = atomicAdd(&tm->start, 0ull);
-      tm->total_ns += t1 > t0 ? t1 - t0 : 0ull;
-      tm->launches += 1u;
-      tm->start = ~0ull;
-      tm->ticket = 0u;
-    }
-  }
-}
-
 template <typename T>
 PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
                         const int32_t* __restrict__ ci, const T* __restrict__ vv,

@@ -138,6 +138,20 @@ def test_large_soc_block_grid_tier():
     _parity(prob, iters=70, check_freq=32)
 
 
+def test_eager_mode_matches_graph_mode():
+    """Host-launched kernels (for profilers) give exactly the graph results."""
+    P = _gpu()
+    prob = workloads.tiny_conic(seed=4)
+    out = []
+    for eager in (0, 1):
+        with P.Solver(prob, max_iter=150, check_freq=32, eager=eager, time_limit=60.0) as s:
+            s.solve()
+            out.append(s.get_state())
+    for key in ("x", "y", "x0", "y0", "xs", "ys"):
+        assert np.array_equal(out[0][key], out[1][key]), key
+    assert out[0]["kbar"] == out[1]["kbar"] and out[0]["restarts"] == out[1]["restarts"]
+
+
 def _full(prob, **kw):
     P = _gpu()
     g = P.solve(prob, max_iter=100000, time_limit=120.0, **kw)
