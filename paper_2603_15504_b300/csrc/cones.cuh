@@ -24,8 +24,9 @@
 // a_i = vbar_i^2 b_i, on (0, e0^2/2) when v0 > 0; when v0 < 0 the variable
 // nu = 1/(2 mu) in (0, 1/e0^2) is used with
 //   H(nu) = sum a_i/(1 + b_i nu)^2 - v0^2 e0^2/(1 - e0^2 nu)^2;
-// both are decreasing from a positive value to -inf, and are solved by a
-// safeguarded Newton iteration.  v0 = 0 gives mu = e0^2/2, w0 = e0 ||wbar/ebar||.
+// both are decreasing from a positive value to -inf, and are solved by
+// safeguarded Halley steps from the closed-form root of the uniformly scaled
+// case.  v0 = 0 gives mu = e0^2/2, w0 = e0 ||wbar/ebar||.
 #pragma once
 #include <math.h>
 
@@ -194,9 +195,98 @@ PDCS_HD void proj_exp_family(const double v[3], const double e[3], bool dual, do
 }
 
 // ------------------------------------------------------------------ K_soc
+// 1/d by Newton-Raphson refinement (r <- r + r (1 - d r), twice) of a
+// correctly rounded FP32 seed: relative error below 2^-48 after the first step
+// and at rounding level after the second.  Used where the SOC root-finding
+// needs many reciprocals and FP64 division throughput is scarce.  Falls back
+// to division outside the FP32 range.
+PDCS_HD double rcp_nr(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+#ifdef __CUDA_ARCH__
+  double r = (double)__frcp_rn((float)d);
+#else
+  double r = (double)(1.0f / (float)d);
+#endif
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Per-element terms of the secular function and its first two derivatives:
+// f += (a r^2, a r^3, a r^4) with r = 1/(b + 2x) (branch v0 > 0, x = mu) or
+// (a r^2, a b r^3, a b^2 r^4) with r = 1/(1 + b x) (branch v0 < 0, x = nu).
+PDCS_HD void soc_secular_terms(bool pos, double a, double b, double x, double (&f)[3]) {
+  const double r = pos ? rcp_nr(b + 2.0 * x) : rcp_nr(1.0 + b * x);
+  const double ar2 = a * r * r;
+  if (pos) {
+    f[0] += ar2;
+    f[1] += ar2 * r;
+    f[2] += ar2 * r * r;
+  } else {
+    f[0] += ar2;
+    f[1] += ar2 * b * r;
+    f[2] += ar2 * b * b * r * r;
+  }
+}
+
+// One safeguarded Halley step on F (v0 > 0: F(mu) = sum a/(b+2mu)^2 -
+// c0/(e0^2-2mu)^2) or H (v0 < 0: H(nu) = sum a/(1+b nu)^2 - c0/(1-e0^2 nu)^2),
+// both decreasing on their interval.  Updates the bracket [lo, hi] (F > 0 at
+// lo); returns the step, 0 when converged (the caller then stops).
+PDCS_HD double soc_halley_step(bool pos, const double (&f)[3], double c0, double e02, double& x,
+                               double& lo, double& hi) {
+  double F, dF, d2F;
+  if (pos) {
+    const double r = 1.0 / (e02 - 2.0 * x);
+    F = f[0] - c0 * r * r;
+    dF = -4.0 * f[1] - 4.0 * c0 * r * r * r;
+    d2F = 24.0 * f[2] - 24.0 * c0 * r * r * r * r;
+  } else {
+    const double r = 1.0 / (1.0 - e02 * x);
+    F = f[0] - c0 * r * r;
+    dF = -2.0 * f[1] - 2.0 * c0 * e02 * r * r * r;
+    d2F = 6.0 * f[2] - 6.0 * c0 * e02 * e02 * r * r * r * r;
+  }
+  if (F > 0.0) lo = x; else hi = x;
+  if (F == 0.0) return 0.0;
+  double step = -2.0 * F * dF / (2.0 * dF * dF - F * d2F);
+  if (!(fabs(step) < INFINITY)) step = -F / dF;
+  const double xn = x + step;
+  if (fabs(step) <= 1e-15 * x) {  // converged; the step may not even move x
+    if (xn >= lo && xn <= hi) x = xn;
+    return 0.0;
+  }
+  return step;
+}
+
+// Starting point of the SOC root-finding from the closed-form root obtained
+// when every ebar_i^2 equals b_eff = sqrt(sum a_i / sum a_i b_i^-2) (the value
+// that matches the secular function at 0 and at infinity).  s0 = sum (v/e)^2,
+// s1 = sum (e v)^2 over the tail, v0 / e0 the head; returns x in the variable
+// of the branch (mu for v0 > 0, nu = 1/(2 mu) for v0 < 0), strictly inside
+// its interval.
+PDCS_HD double soc_initial_guess(double s0, double s1, double v0, double e0) {
+  const double e02 = e0 * e0;
+  const double sa = sqrt(s1);                 // sqrt(sum a_i) without the common scale
+  const double beff = sqrt(s1 / s0);
+  const double av = fabs(v0) * e0;
+  double x, hi;
+  if (v0 > 0.0) {
+    x = 0.5 * (sa * e02 - av * beff) / (sa + av);  // mu
+    hi = 0.5 * e02;
+  } else {
+    x = (sa - av) / (sa * e02 + av * beff);        // nu
+    hi = 1.0 / e02;
+  }
+  if (!(x > 0.0 && x < hi)) x = 0.5 * hi;
+  return x;
+}
+
 // CTA-wide projection of one block held in registers: each thread owns EPT
 // elements (index = threadIdx.x + k * NT); element 0 is the head.  `sh` is
-// scratch for block reductions (>= 8 + 2 * NT/32 doubles).
+// scratch for block reductions (>= 8 + 3 * NT/32 doubles).
 template <int NT, int EPT>
 __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)[EPT], int dim,
                                              double* sh) {
@@ -252,44 +342,21 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
   const double c0 = (v0 * sc) * (v0 * sc) * e02;
   const bool pos = v0 > 0.0;
   double lo = 0.0, hi = pos ? 0.5 * e02 : 1.0 / e02;
-  double x = 0.0;
+  double x = soc_initial_guess(s[0], s[1], v0, e0);
   for (int it = 0; it < 200; ++it) {
-    double f[2] = {0.0, 0.0};
+    double f[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int i = tid + k * NT;
       if (i >= 1 && i < dim) {
         const double vv = v[k] * sc, b = e[k] * e[k], a = vv * vv * b;
-        if (pos) {
-          const double r = 1.0 / (b + 2.0 * x);
-          f[0] += a * r * r;
-          f[1] += a * r * r * r;
-        } else {
-          const double r = 1.0 / (1.0 + b * x);
-          f[0] += a * r * r;
-          f[1] += a * b * r * r * r;
-        }
+        soc_secular_terms(pos, a, b, x, f);
       }
     }
-    block_sum<2>(f, red);
-    double F, dF;
-    if (pos) {
-      const double r = 1.0 / (e02 - 2.0 * x);
-      F = f[0] - c0 * r * r;
-      dF = -4.0 * f[1] - 4.0 * c0 * r * r * r;
-    } else {
-      const double r = 1.0 / (1.0 - e02 * x);
-      F = f[0] - c0 * r * r;
-      dF = -2.0 * f[1] - 2.0 * c0 * e02 * r * r * r;
-    }
-    if (F > 0.0) lo = x; else hi = x;
-    if (F == 0.0) break;
-    const double step = -F / dF;
+    block_sum<3>(f, red);
+    const double step = soc_halley_step(pos, f, c0, e02, x, lo, hi);
+    if (step == 0.0) break;
     double xn = x + step;
-    if (fabs(step) <= 1e-15 * x) {  // converged (the step may not even move x)
-      if (xn >= lo && xn <= hi) x = xn;
-      break;
-    }
     if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
     x = xn;
     if (hi - lo <= 1e-15 * hi) break;

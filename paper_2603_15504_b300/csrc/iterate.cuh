@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(NT) k_cone_soc(B* v0, B* v1, const int64_t* __
     ktimer_end(tm);
     return;
   }
-  __shared__ double sh[8 + 2 * (NT / 32) + 8];
+  __shared__ double sh[8 + 3 * (NT / 32) + 8];
   const int64_t s = starts[blockIdx.x];
   const int dim = dims[blockIdx.x];
   double vv[EPT], ee[EPT];
@@ -863,7 +863,7 @@ PDCS_DEV void grid_sync(const GridSync& gs, unsigned int& target) {
   __syncthreads();
 }
 
-// Grid-wide sum of K <= 2 values (fixed order: per-CTA tree, then lane-strided
+// Grid-wide sum of K <= 4 values (fixed order: per-CTA tree, then lane-strided
 // sequential sums over the CTA partials and a fixed butterfly).  Every thread
 // of every CTA receives the totals.  Successive reductions alternate between
 // two partial buffers (flip), so a CTA that runs ahead never overwrites
@@ -871,7 +871,7 @@ PDCS_DEV void grid_sync(const GridSync& gs, unsigned int& target) {
 template <int K>
 PDCS_DEV void grid_sum(double (&v)[K], double* part_base, const GridSync& gs, unsigned int& target,
                        double* sh, int& flip) {
-  double* part = part_base + (size_t)flip * 2 * gridDim.x;
+  double* part = part_base + (size_t)flip * 4 * gridDim.x;
   flip ^= 1;
   block_sum<K>(v, sh);
   if (threadIdx.x == 0) {
@@ -896,7 +896,7 @@ PDCS_DEV void grid_sum(double (&v)[K], double* part_base, const GridSync& gs, un
 
 PDCS_DEV double grid_max1(double v, double* part_base, const GridSync& gs, unsigned int& target,
                           double* sh, int& flip) {
-  double* part = part_base + (size_t)flip * 2 * gridDim.x;
+  double* part = part_base + (size_t)flip * 4 * gridDim.x;
   flip ^= 1;
   double a[1] = {v};
   block_max<1>(a, sh);
@@ -916,7 +916,7 @@ PDCS_DEV double grid_max1(double v, double* part_base, const GridSync& gs, unsig
 
 // Projection of the blocks (starts[b], dims[b]) of one or two vectors onto
 // diag(e) K_soc, e = d or 1/d (inv) or 1 (d == NULL).  part needs
-// 4 * gridDim.x doubles; every grid barrier uses a fresh target, so the
+// 8 * gridDim.x doubles; every grid barrier uses a fresh target, so the
 // counter must be zero at launch.
 template <typename B>
 __global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
@@ -927,7 +927,7 @@ __global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
                                                        const int* __restrict__ gate1,
                                                        double* __restrict__ part, GridSync gs,
                                                        KTimer* tm) {
-  __shared__ double sh[2 * 512 / 32 + 8];
+  __shared__ double sh[3 * 512 / 32 + 8];
   if (!gate_on(gate0) && (nvec == 1 || !gate_on(gate1))) return;  // whole launch idle
   ktimer_begin(tm);
   unsigned int target = 0;
@@ -981,41 +981,18 @@ __global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
       const double c0 = (v0h * sc) * (v0h * sc) * e02;
       const bool pos = v0h > 0.0;
       double lo = 0.0, hi = pos ? 0.5 * e02 : 1.0 / e02;
-      double x = 0.0;
+      double x = soc_initial_guess(acc[0], acc[1], v0h, e0);
       for (int it = 0; it < 200; ++it) {
-        double f[2] = {0.0, 0.0};
+        double f[3] = {0.0, 0.0, 0.0};
         for (int64_t i = 1 + tid; i < dim; i += nth) {
           const double ei = cone_scale(d, s + i, inv);
           const double vv = (double)v[s + i] * sc, b = ei * ei, a = vv * vv * b;
-          if (pos) {
-            const double r = 1.0 / (b + 2.0 * x);
-            f[0] += a * r * r;
-            f[1] += a * r * r * r;
-          } else {
-            const double r = 1.0 / (1.0 + b * x);
-            f[0] += a * r * r;
-            f[1] += a * b * r * r * r;
-          }
+          soc_secular_terms(pos, a, b, x, f);
         }
-        grid_sum<2>(f, part, gs, target, sh, flip);
-        double F, dF;
-        if (pos) {
-          const double r = 1.0 / (e02 - 2.0 * x);
-          F = f[0] - c0 * r * r;
-          dF = -4.0 * f[1] - 4.0 * c0 * r * r * r;
-        } else {
-          const double r = 1.0 / (1.0 - e02 * x);
-          F = f[0] - c0 * r * r;
-          dF = -2.0 * f[1] - 2.0 * c0 * e02 * r * r * r;
-        }
-        if (F > 0.0) lo = x; else hi = x;
-        if (F == 0.0) break;
-        const double step = -F / dF;
+        grid_sum<3>(f, part, gs, target, sh, flip);
+        const double step = soc_halley_step(pos, f, c0, e02, x, lo, hi);
+        if (step == 0.0) break;
         double xn = x + step;
-        if (fabs(step) <= 1e-15 * x) {
-          if (xn >= lo && xn <= hi) x = xn;
-          break;
-        }
         if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
         x = xn;
         if (hi - lo <= 1e-15 * hi) break;
@@ -1023,7 +1000,7 @@ __global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
       const double mu2 = pos ? 2.0 * x : 1.0 / x;
       for (int64_t i = 1 + tid; i < dim; i += nth) {
         const double ei = cone_scale(d, s + i, inv), b = ei * ei;
-        v[s + i] = (B)((double)v[s + i] * (b / (b + mu2)));
+        v[s + i] = (B)((double)v[s + i] * (b * rcp_nr(b + mu2)));
       }
       if (tid == 0) v[s] = (B)(pos ? v0h * e02 / (e02 - mu2) : v0h * e02 * x / (e02 * x - 1.0));
     }

@@ -575,7 +575,7 @@ struct Solver : SolverBase {
         big_grid = sms * occ;
         gsync_count = ar.alloc<unsigned int>(1);
         gsync_err = ar.alloc<int>(1);
-        gpart = ar.alloc<double>(4 * (int64_t)big_grid);
+        gpart = ar.alloc<double>(8 * (int64_t)big_grid);
         CK(cudaMemsetAsync(gsync_count, 0, sizeof(unsigned int), st));
         CK(cudaMemsetAsync(gsync_err, 0, sizeof(int), st));
       }
