@@ -59,6 +59,38 @@ PDCS_DEV void block_max(double (&v)[K], double* sh) {
   __syncthreads();
 }
 
+// Reduction of per-CTA partials by one whole CTA, in a fixed order (thread t
+// adds parts t, t + blockDim, ... sequentially, then a fixed tree): partial
+// b's value k sits at part[b * stride + off + k].  KS sums then KM maxima.
+template <int KS, int KM>
+PDCS_DEV void cta_reduce_parts(const double* part, unsigned nparts, int stride, double (&S)[KS],
+                               double (&M)[KM], double* sh) {
+#pragma unroll
+  for (int k = 0; k < KS; ++k) S[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < KM; ++k) M[k] = 0.0;
+  for (unsigned b = threadIdx.x; b < nparts; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k) S[k] += __ldcg(part + (size_t)b * stride + k);
+#pragma unroll
+    for (int k = 0; k < KM; ++k) M[k] = fmax(M[k], __ldcg(part + (size_t)b * stride + KS + k));
+  }
+  block_sum<KS>(S, sh);
+  block_max<KM>(M, sh);
+}
+
+template <int KS>
+PDCS_DEV void cta_reduce_sums(const double* part, unsigned nparts, int stride, double (&S)[KS],
+                              double* sh) {
+#pragma unroll
+  for (int k = 0; k < KS; ++k) S[k] = 0.0;
+  for (unsigned b = threadIdx.x; b < nparts; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < KS; ++k) S[k] += __ldcg(part + (size_t)b * stride + k);
+  }
+  block_sum<KS>(S, sh);
+}
+
 // "Last CTA done" protocol: each CTA publishes its partials, then the CTA that
 // observes the final ticket performs the grid-level epilogue.  No CTA waits on
 // another, so this cannot hang.  Returns true in exactly one CTA.

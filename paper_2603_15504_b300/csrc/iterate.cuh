@@ -159,14 +159,10 @@ __global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict_
   }
   ktimer_end(tslot(p.tm, TM_STEP));
   if (!last_block_done(&ctl->cnt[CNT_STEP])) return;
+  double S3[3];
+  cta_reduce_sums<3>(part, gridDim.x, 3, S3, sh);
   if (threadIdx.x != 0) return;
-  double dx2 = 0.0, dy2 = 0.0, inter = 0.0;
-  const volatile double* vp = part;
-  for (unsigned b = 0; b < gridDim.x; ++b) {
-    dx2 += vp[b * 3 + 0];
-    dy2 += vp[b * 3 + 1];
-    inter += vp[b * 3 + 2];
-  }
+  double dx2 = S3[0], dy2 = S3[1], inter = S3[2];
   ctl->cnt[CNT_STEP] = 0u;
   inter = fabs(inter);
   const double omega = ctl->omega, eta = ctl->eta;
@@ -405,15 +401,9 @@ __global__ void __launch_bounds__(kEwThreads) k_point_stats(Prob<T> p, Ctl* __re
   }
   ktimer_end(tmr);
   if (!last_block_done(&ctl->cnt[CNT_STATS0 + slot])) return;
-  if (threadIdx.x != 0) return;
   double S[kStatSums], M[kStatMax];
-  for (int k = 0; k < kStatSums; ++k) S[k] = 0.0;
-  for (int k = 0; k < kStatMax; ++k) M[k] = 0.0;
-  const volatile double* vp = part;
-  for (unsigned b = 0; b < gridDim.x; ++b) {
-    for (int k = 0; k < kStatSums; ++k) S[k] += vp[b * kStatK + k];
-    for (int k = 0; k < kStatMax; ++k) M[k] = fmax(M[k], vp[b * kStatK + kStatSums + k]);
-  }
+  cta_reduce_parts<kStatSums, kStatMax>(part, gridDim.x, kStatK, S, M, sh);
+  if (threadIdx.x != 0) return;
   ctl->cnt[CNT_STATS0 + slot] = 0u;
   PointStats& st = ctl->st[slot];
   finish_stats(ctl, st, S, M);
@@ -631,16 +621,19 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __r
   }
   ktimer_end(tslot(p.tm, TM_PROBE_REDUCE));
   if (!last_block_done(&ctl->cnt[CNT_PROBE])) return;
+  double SS[2][4];
+  for (int cc = 0; cc < 2; ++cc) {
+    double S4[4];
+    cta_reduce_sums<4>(part + (size_t)cc * gridDim.x * 4, gridDim.x, 4, S4, sh);
+    for (int k = 0; k < 4; ++k) SS[cc][k] = S4[k];
+  }
   if (threadIdx.x != 0) return;
   ctl->cnt[CNT_PROBE] = 0u;
-  const volatile double* vp = part;
   int any = 0;
   for (int cc = 0; cc < 2; ++cc) {
     Bisect& b = ctl->bs[cc];
     if (!b.active) continue;
-    double S[4] = {0.0, 0.0, 0.0, 0.0};
-    for (unsigned blk = 0; blk < gridDim.x; ++blk)
-      for (int k = 0; k < 4; ++k) S[k] += vp[(cc * gridDim.x + blk) * 4 + k];
+    const double* S = SS[cc];
     const double dist = sqrt(S[0] / b.tau + S[1] / b.sigma);
     b.last_dot = S[2] + S[3];
     if (b.phase == BS_EXP) {
