@@ -19,43 +19,65 @@ PDCS_DEV double warp_max(double v) {
   return v;
 }
 
-// Sum of K values over the CTA; every thread receives the totals.  `sh` must
-// hold K * (blockDim.x / 32) doubles.  Deterministic (fixed tree order).
+// Block reductions.  FP64 instructions are scarce on this GPU (one FP64 pipe
+// slot serves a handful of lanes per cycle), so the trees avoid redundant FP64
+// work: every thread stages its K values in shared memory, warp 0 alone adds
+// them (lane l takes threads l, l+32, ... in order, then a fixed butterfly), and
+// the totals are broadcast back.  Deterministic.  `sh` must hold
+// K * blockDim.x + K doubles.
 template <int K>
 PDCS_DEV void block_sum(double (&v)[K], double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x;
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
-  if (lane == 0) {
+  for (int k = 0; k < K; ++k) sh[k * nt + tid] = v[k];
+  __syncthreads();
+  if (tid < 32) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) sh[k * nw + wid] = v[k];
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int t = tid; t < nt; t += 32) s += sh[k * nt + t];
+      s = warp_sum(s);
+      if (tid == 0) sh[K * nt + k] = s;
+    }
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += sh[k * nw + w];
-    v[k] = s;
-  }
+  for (int k = 0; k < K; ++k) v[k] = sh[K * nt + k];
   __syncthreads();
+}
+
+// Maxima of non-negative values (NaN propagates): for non-negative IEEE
+// doubles the order of the values equals the order of their bit patterns, so
+// the comparisons run on the integer pipes.
+PDCS_DEV long long warp_max_bits(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, (long long)__shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+PDCS_DEV double warp_max_nonneg(double v) {
+  return __longlong_as_double(warp_max_bits(__double_as_longlong(v)));
 }
 
 template <int K>
 PDCS_DEV void block_max(double (&v)[K], double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  long long* shl = reinterpret_cast<long long*>(sh);
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = warp_max(v[k]);
-  if (lane == 0) {
+  for (int k = 0; k < K; ++k) shl[k * nt + tid] = __double_as_longlong(v[k]);
+  __syncthreads();
+  if (tid < 32) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) sh[k * nw + wid] = v[k];
+    for (int k = 0; k < K; ++k) {
+      long long s = 0;
+      for (int t = tid; t < nt; t += 32) s = max(s, shl[k * nt + t]);
+      s = warp_max_bits(s);
+      if (tid == 0) shl[K * nt + k] = s;
+    }
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double s = sh[k * nw];
-    for (int w = 1; w < nw; ++w) s = fmax(s, sh[k * nw + w]);
-    v[k] = s;
-  }
+  for (int k = 0; k < K; ++k) v[k] = __longlong_as_double(shl[K * nt + k]);
   __syncthreads();
 }
 
@@ -73,7 +95,9 @@ PDCS_DEV void cta_reduce_parts(const double* part, unsigned nparts, int stride, 
 #pragma unroll
     for (int k = 0; k < KS; ++k) S[k] += __ldcg(part + (size_t)b * stride + k);
 #pragma unroll
-    for (int k = 0; k < KM; ++k) M[k] = fmax(M[k], __ldcg(part + (size_t)b * stride + KS + k));
+    for (int k = 0; k < KM; ++k)
+      M[k] = __longlong_as_double(max(__double_as_longlong(M[k]),
+                                      __double_as_longlong(__ldcg(part + (size_t)b * stride + KS + k))));
   }
   block_sum<KS>(S, sh);
   block_max<KM>(M, sh);

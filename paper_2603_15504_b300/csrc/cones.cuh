@@ -286,7 +286,8 @@ PDCS_HD double soc_initial_guess(double s0, double s1, double v0, double e0) {
 
 // CTA-wide projection of one block held in registers: each thread owns EPT
 // elements (index = threadIdx.x + k * NT); element 0 is the head.  `sh` is
-// scratch for block reductions (>= 8 + 3 * NT/32 doubles).
+// scratch: 8 doubles of broadcast slots, then a block-reduction area of
+// 3 * NT + 3 doubles.
 template <int NT, int EPT>
 __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)[EPT], int dim,
                                              double* sh) {
@@ -354,12 +355,24 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
       }
     }
     block_sum<3>(f, red);
-    const double step = soc_halley_step(pos, f, c0, e02, x, lo, hi);
-    if (step == 0.0) break;
-    double xn = x + step;
-    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-    x = xn;
-    if (hi - lo <= 1e-15 * hi) break;
+    if (tid == 0) {  // scalar step once per CTA, broadcast
+      int stop = 0;
+      const double step = soc_halley_step(pos, f, c0, e02, x, lo, hi);
+      if (step == 0.0) {
+        stop = 1;
+      } else {
+        double xn = x + step;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        x = xn;
+        if (hi - lo <= 1e-15 * hi) stop = 1;
+      }
+      sh[2] = x; sh[3] = lo; sh[4] = hi; sh[5] = (double)stop;
+    }
+    __syncthreads();
+    x = sh[2]; lo = sh[3]; hi = sh[4];
+    const bool stop = sh[5] != 0.0;
+    __syncthreads();
+    if (stop) break;
   }
   const double mu2 = pos ? 2.0 * x : 1.0 / x;  // 2 mu
 #pragma unroll

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict_
                                                      double* __restrict__ part) {
   if (!ctl->g_attempt) return;
   ktimer_begin(tslot(p.tm, TM_STEP));
-  __shared__ double sh[3 * kEwThreads / 32];
+  __shared__ double sh[3 * kEwThreads + 3];
   double s[3] = {0.0, 0.0, 0.0};
   PDCS_GRID_LOOP(j, p.n) {
     const double d = (double)xh[j] - (double)x[j];
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(NT) k_cone_soc(B* v0, B* v1, const int64_t* __
     ktimer_end(tm);
     return;
   }
-  __shared__ double sh[8 + 3 * (NT / 32) + 8];
+  __shared__ double sh[8 + 3 * NT + 3];
   const int64_t s = starts[blockIdx.x];
   const int dim = dims[blockIdx.x];
   double vv[EPT], ee[EPT];
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kEwThreads) k_point_stats(Prob<T> p, Ctl* __re
   if (gate != nullptr && *gate == 0) return;
   KTimer* tmr = tslot(p.tm, slot == 0 ? TM_STATS_ATTEMPT : TM_STATS_CHECK);
   ktimer_begin(tmr);
-  __shared__ double sh[kStatK * kEwThreads / 32];
+  __shared__ double sh[kStatSums * kEwThreads + kStatSums];
   double s[kStatSums];
   double mx[kStatMax];
 #pragma unroll
@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __r
   const int c = blockIdx.y;
   const Bisect& bs = ctl->bs[c];
   ktimer_begin(tslot(p.tm, TM_PROBE_REDUCE));
-  __shared__ double sh[4 * kEwThreads / 32];
+  __shared__ double sh[4 * kEwThreads + 4];
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   if (bs.active) {
     const PointRef<T> pt = c == 0 ? a : bpt;
@@ -896,10 +896,11 @@ PDCS_DEV double grid_max1(double v, double* part_base, const GridSync& gs, unsig
   if (threadIdx.x == 0) part[blockIdx.x] = a[0];
   grid_sync(gs, target);
   if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s = fmax(s, __ldcg(part + b));
-    s = warp_max(s);
-    if (threadIdx.x == 0) sh[0] = s;
+    long long s = 0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
+      s = max(s, __double_as_longlong(__ldcg(part + b)));
+    s = warp_max_bits(s);
+    if (threadIdx.x == 0) sh[0] = __longlong_as_double(s);
   }
   __syncthreads();
   const double r = sh[0];
@@ -920,7 +921,7 @@ __global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
                                                        const int* __restrict__ gate1,
                                                        double* __restrict__ part, GridSync gs,
                                                        KTimer* tm) {
-  __shared__ double sh[3 * 512 / 32 + 8];
+  __shared__ double sh[3 * 512 + 3 + 8];
   if (!gate_on(gate0) && (nvec == 1 || !gate_on(gate1))) return;  // whole launch idle
   ktimer_begin(tm);
   unsigned int target = 0;
@@ -983,12 +984,26 @@ __global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
           soc_secular_terms(pos, a, b, x, f);
         }
         grid_sum<3>(f, part, gs, target, sh, flip);
-        const double step = soc_halley_step(pos, f, c0, e02, x, lo, hi);
-        if (step == 0.0) break;
-        double xn = x + step;
-        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-        x = xn;
-        if (hi - lo <= 1e-15 * hi) break;
+        // the scalar step is computed once per CTA and broadcast (redundant
+        // FP64 work in every thread would cost more than the pass itself)
+        if (threadIdx.x == 0) {
+          int stop = 0;
+          const double step = soc_halley_step(pos, f, c0, e02, x, lo, hi);
+          if (step == 0.0) {
+            stop = 1;
+          } else {
+            double xn = x + step;
+            if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+            x = xn;
+            if (hi - lo <= 1e-15 * hi) stop = 1;
+          }
+          sh[0] = x; sh[1] = lo; sh[2] = hi; sh[3] = (double)stop;
+        }
+        __syncthreads();
+        x = sh[0]; lo = sh[1]; hi = sh[2];
+        const bool stop = sh[3] != 0.0;
+        __syncthreads();
+        if (stop) break;
       }
       const double mu2 = pos ? 2.0 * x : 1.0 / x;
       for (int64_t i = 1 + tid; i < dim; i += nth) {

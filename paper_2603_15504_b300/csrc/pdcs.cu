@@ -103,7 +103,7 @@ struct SpmvPlan {
 
 // Bin rows into SpMV tasks (see spmv.cuh): short rows one per thread, medium
 // rows one lane group per row, long rows split into kChunk-nonzero chunks.
-static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream_t st) {
+static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream_t st, int small_g) {
   const int64_t m = (int64_t)rp.size() - 1;
   std::vector<SpmvTask> tasks;
   int64_t npart = 0;
@@ -111,7 +111,7 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
   auto cls = [&](int64_t r) {
     const int64_t len = rp[r + 1] - rp[r];
     if (len <= 4) return 0;
-    if (len <= 64) return 1;
+    if (len <= 512) return 1;
     if (len <= 4096) return 2;
     return 3;
   };
@@ -138,7 +138,7 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
       ++r;
       continue;
     }
-    const int64_t max_rows = c == 0 ? 256 : (c == 1 ? 128 : 32);
+    const int64_t max_rows = c == 0 ? 256 : (c == 1 ? 4 * (256 / small_g) : 32);
     const int64_t max_nnz = c == 2 ? 16384 : 8192;
     int64_t e = r, nnz = 0;
     while (e < m && cls(e) == c && e - r < max_rows && (nnz == 0 || nnz + rp[e + 1] - rp[e] <= max_nnz)) {
@@ -147,7 +147,7 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
     }
     SpmvTask t{};
     t.kind = c == 0 ? 0 : 1;
-    t.g = c == 1 ? 8 : 32;
+    t.g = c == 1 ? small_g : 32;
     t.a = r;
     t.b = e;
     tasks.push_back(t);
@@ -503,8 +503,9 @@ struct Solver : SolverBase {
     copy_in(ck, hck.data(), n, st);
     fill_table(rows, rsoc, rbig, rexp, rexpd);
     fill_table(cols, csoc, cbig, cexp, cexpd);
-    planG = build_plan(hrp, ar, st);
-    planGT = build_plan(hrpT, ar, st);
+    const int small_g = sizeof(T) == 8 ? 4 : 8;
+    planG = build_plan(hrp, ar, st, small_g);
+    planGT = build_plan(hrpT, ar, st, small_g);
     alloc_state();
     if (opt.eager) use_cond = 0;
     else capture();

@@ -230,7 +230,7 @@ __global__ void k_scale_vec(const double* in, const double* d, int64_t n, int mo
 
 // One-CTA set-up reduction: out = {sum |v|, sum v^2, max |v / div|}.
 __global__ void k_vec_norms(const double* v, int64_t n, const double* div, double* out) {
-  __shared__ double sh[4 * 32];
+  __shared__ double sh[2 * 1024 + 2];
   double s[2] = {0.0, 0.0};
   double mx[1] = {0.0};
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {

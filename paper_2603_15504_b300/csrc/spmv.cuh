@@ -3,8 +3,11 @@
 //
 // Rows are binned on the host into tasks, one CTA per task:
 //   kind 0  up to 256 short rows (<= 4 nonzeros), one thread per row;
-//   kind 1  medium rows, one group of G lanes per row (G = 8 or 32), lanes
-//           striding over the row so loads are coalesced;
+//   kind 1  medium rows, one group of G lanes per row, lanes striding over the
+//           row so loads are coalesced: G = 32 for rows of 513..4096 nonzeros,
+//           else the smallest group whose loads still fill 32-byte sectors
+//           (G = 4 for FP64, 8 for FP32), which keeps the FP64 shuffle-add tree
+//           per row short (FP64 instructions are the scarce resource here);
 //   kind 2  one chunk of <= kChunk nonzeros of a long row; the chunk sums are
 //           written to a partial buffer and the last chunk CTA of the row (an
 //           atomic ticket, no waiting) adds them in chunk order, so the result
@@ -117,12 +120,13 @@ PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
     return;
   }
   if (t.kind == 1) {
-    if (t.g == 8) spmv_group_rows<T, 8>(t, rp, ci, vv, x, y);
+    if (t.g == 4) spmv_group_rows<T, 4>(t, rp, ci, vv, x, y);
+    else if (t.g == 8) spmv_group_rows<T, 8>(t, rp, ci, vv, x, y);
     else spmv_group_rows<T, 32>(t, rp, ci, vv, x, y);
     return;
   }
   // kind 2: chunk of a long row
-  __shared__ double sh[kSpmvThreads / 32 + 1];
+  __shared__ double sh[kSpmvThreads + 1];
   Acc<T> acc;
   int64_t k = t.c + threadIdx.x;
   for (; k + 3 * kSpmvThreads < t.d; k += 4 * kSpmvThreads) {
