@@ -13,6 +13,34 @@ PDCS_DEV double warp_sum(double v) {
   return v;
 }
 
+// FP64 <-> FP32 conversions on the integer pipes, from the IEEE-754 binary64
+// and binary32 layouts (the FP64 pipe, which would execute cvt, is scarce).
+// f32_trunc: v * 2^-shift with the mantissa truncated to 24 bits; zero,
+// subnormal and underflowing values give a signed zero, overflowing ones (and
+// inf / NaN inputs) a signed infinity.
+PDCS_DEV float f32_trunc(double v, int shift = 0) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const int ef = e - 1023 + 127 - shift;
+  unsigned r;
+  if (e == 0 || ef <= 0) r = sign;
+  else if (ef >= 255) r = sign | 0x7f800000u;
+  else r = sign | ((unsigned)ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(r);
+}
+
+// Exact widening of a normal FP32 value (zero and subnormals give zero,
+// inf / NaN an infinity).
+PDCS_DEV double f64_of_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  if (e == 255u) return __hiloint2double((int)(sign | 0x7ff00000u), 0);
+  const unsigned hi = sign | ((e - 127u + 1023u) << 20) | ((u >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 PDCS_DEV double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));

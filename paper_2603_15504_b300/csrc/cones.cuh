@@ -195,23 +195,29 @@ PDCS_HD void proj_exp_family(const double v[3], const double e[3], bool dual, do
 }
 
 // ------------------------------------------------------------------ K_soc
-// 1/d by Newton-Raphson refinement (r <- r + r (1 - d r), twice) of a
-// correctly rounded FP32 seed: relative error below 2^-48 after the first step
-// and at rounding level after the second.  Used where the SOC root-finding
-// needs many reciprocals and FP64 division throughput is scarce.  Falls back
-// to division outside the FP32 range.
+// 1/d by Newton-Raphson refinement (r <- r + r (1 - d r), twice) of an FP32
+// seed: the seed (FP32 approximate reciprocal of d truncated to FP32) has a
+// relative error below 2^-21, so the first step leaves below 2^-42 and the
+// second rounding level.  On the device the seed and the range test run on
+// the integer and FP32 pipes; only the four FMAs use the FP64 pipe, whose
+// throughput is scarce.  Falls back to division outside |d| in
+// [2^-100, 2^100].
 PDCS_HD double rcp_nr(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
 #ifdef __CUDA_ARCH__
-  double r = (double)__frcp_rn((float)d);
+  const int e = (__double2hiint(d) >> 20) & 0x7ff;
+  if (e < 1023 - 100 || e > 1023 + 100) return 1.0 / d;
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f32_trunc(d)));
+  double r = f64_of_f32(rf);
 #else
+  const double ad = fabs(d);
+  if (!(ad > 0x1p-100 && ad < 0x1p100)) return 1.0 / d;
   double r = (double)(1.0f / (float)d);
 #endif
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
+  double e1 = fma(-d, r, 1.0);
+  r = fma(r, e1, r);
+  e1 = fma(-d, r, 1.0);
+  return fma(r, e1, r);
 }
 
 // Per-element terms of the secular function and its first two derivatives:

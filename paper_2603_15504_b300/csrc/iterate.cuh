@@ -824,6 +824,9 @@ __global__ void k_unscale(Prob<T> p, const T* xt, const T* yt, const T* gxt, dou
 
 namespace pdcs {
 
+// Largest grid of the cooperative kernels (partials are read in one sweep).
+constexpr int kMaxGridParts = 512;
+
 // ------------------------------------------------- grid-wide SOC projection
 // For second-order-cone blocks too large for one CTA (e.g. the single block of
 // dimension k + n + 2 of a factor-model portfolio), the same root-finding as
@@ -856,161 +859,463 @@ PDCS_DEV void grid_sync(const GridSync& gs, unsigned int& target) {
   __syncthreads();
 }
 
-// Grid-wide sum of K <= 4 values (fixed order: per-CTA tree, then lane-strided
-// sequential sums over the CTA partials and a fixed butterfly).  Every thread
-// of every CTA receives the totals.  Successive reductions alternate between
-// two partial buffers (flip), so a CTA that runs ahead never overwrites
-// partials another CTA is still reading.
+// Grid-wide reductions of the cooperative SOC kernel.  Each pass stages K <= 8
+// values per CTA in a partial buffer, crosses one grid barrier, and then warp
+// k reduces value k over the CTAs in a fixed order (lane l takes CTAs l,
+// l + 32, ... with all loads issued together, then a fixed butterfly), leaving
+// the total in out[k].  Every CTA adds the same partials in the same order, so
+// all CTAs obtain bit-identical totals and take identical decisions.
+//
+// Buffer layout (G = gridDim.x): two alternating halves of 12 G doubles (a CTA
+// that runs ahead never overwrites partials another CTA is still reading);
+// each half holds 8 slots x G FP64 values, slot-major (so the reads after the
+// barrier coalesce), followed by 8 slots x G FP32 values.  Slots < KS are
+// sums, the others maxima of non-negative values (integer bit-pattern maxima);
+// slots in f32mask are FP32 sums.
+struct GridPart {
+  double* d;
+  float* f;
+};
+
+PDCS_DEV GridPart grid_part(double* base, int flip) {
+  double* h = base + (size_t)flip * 12 * gridDim.x;
+  return GridPart{h, reinterpret_cast<float*>(h + 8 * (size_t)gridDim.x)};
+}
+
+// CTA partials of K FP64 values: staged in shared memory, warp k adds value k.
 template <int K>
-PDCS_DEV void grid_sum(double (&v)[K], double* part_base, const GridSync& gs, unsigned int& target,
-                       double* sh, int& flip) {
-  double* part = part_base + (size_t)flip * 4 * gridDim.x;
-  flip ^= 1;
-  block_sum<K>(v, sh);
-  if (threadIdx.x == 0) {
+PDCS_DEV void cta_rows_f64(const double (&v)[K], int KS, unsigned mask, double* red, GridPart p) {
+  const int nt = blockDim.x;
 #pragma unroll
-    for (int k = 0; k < K; ++k) part[blockIdx.x * K + k] = v[k];
-  }
-  grid_sync(gs, target);
-  if (threadIdx.x < 32) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < K; ++k) red[k * nt + threadIdx.x] = v[k];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < K && ((mask >> w) & 1u)) {
+    const double* r = red + w * nt;
+    if (w < KS) {
       double s = 0.0;
-      for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s += __ldcg(part + b * K + k);
+      for (int t = lane; t < nt; t += 32) s += r[t];
       s = warp_sum(s);
-      if (threadIdx.x == 0) sh[k] = s;
+      if (lane == 0) p.d[(size_t)w * gridDim.x + blockIdx.x] = s;
+    } else {
+      long long s = 0;
+      for (int t = lane; t < nt; t += 32) s = max(s, __double_as_longlong(r[t]));
+      s = warp_max_bits(s);
+      if (lane == 0) p.d[(size_t)w * gridDim.x + blockIdx.x] = __longlong_as_double(s);
+    }
+  }
+}
+
+PDCS_DEV float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// CTA partials of K FP32 sums (warp butterflies, then warp k adds the warps'
+// value k); redf holds 32 * K floats.
+template <int K>
+PDCS_DEV void cta_rows_f32(const float (&v)[K], unsigned mask, float* redf, GridPart p) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!((mask >> k) & 1u)) continue;
+    const float s = warp_sum_f(v[k]);
+    if (lane == 0) redf[w * K + k] = s;
+  }
+  __syncthreads();
+  if (w < K && ((mask >> w) & 1u)) {
+    float s = lane < nw ? redf[lane * K + w] : 0.0f;
+    s = warp_sum_f(s);
+    if (lane == 0) p.f[(size_t)w * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// After the barrier: out[k] = grid total of slot k (k < K); FP32 totals are
+// left in outf (not widened: the FP64 pipe is scarce).
+PDCS_DEV void grid_totals(GridPart p, int K, int KS, unsigned f32mask, double* out, float* outf) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned G = gridDim.x;
+  if (w < K) {
+    if ((f32mask >> w) & 1u) {
+      const float* src = p.f + (size_t)w * G;
+      float buf[kMaxGridParts / 32];
+#pragma unroll
+      for (int j = 0; j < kMaxGridParts / 32; ++j) {
+        const unsigned b = lane + 32u * j;
+        buf[j] = b < G ? __ldcg(src + b) : 0.0f;
+      }
+      float s = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kMaxGridParts / 32; ++j) s += buf[j];
+      s = warp_sum_f(s);
+      if (lane == 0) outf[w] = s;
+    } else {
+      const double* src = p.d + (size_t)w * G;
+      if (w >= KS) {
+        long long buf[kMaxGridParts / 32];
+#pragma unroll
+        for (int j = 0; j < kMaxGridParts / 32; ++j) {
+          const unsigned b = lane + 32u * j;
+          buf[j] = b < G ? __double_as_longlong(__ldcg(src + b)) : 0ll;
+        }
+        long long s = 0;
+#pragma unroll
+        for (int j = 0; j < kMaxGridParts / 32; ++j) s = max(s, buf[j]);
+        s = warp_max_bits(s);
+        if (lane == 0) out[w] = __longlong_as_double(s);
+      } else {
+        double buf[kMaxGridParts / 32];
+#pragma unroll
+        for (int j = 0; j < kMaxGridParts / 32; ++j) {
+          const unsigned b = lane + 32u * j;
+          buf[j] = b < G ? __ldcg(src + b) : 0.0;
+        }
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < kMaxGridParts / 32; ++j) s += buf[j];
+        s = warp_sum(s);
+        if (lane == 0) out[w] = s;
+      }
     }
   }
   __syncthreads();
+}
+
+// Per-vector scalar state of the grid-wide SOC root-finding.  Thread 0 of
+// every CTA updates it from the same grid totals, so all copies agree; the
+// other threads only read it (xf, pos and esh spare them FP64 instructions).
+struct SocGridVec {
+  double x, lo, hi, top, sc, c0, e0, e02, v0h, w, mu2;
+  float xf;
+  int pos, esh, mode, it;
+};
+enum : int {
+  SG_DONE = 0,      // nothing (left) to do for this vector
+  SG_ZERO_HEAD,     // v0 == 0: one pass for the norm of the new tail
+  SG_F32,           // root-finding, per-element terms in FP32
+  SG_F64,           // root-finding, per-element terms in FP64 (polish)
+  SG_WRITE_ZERO,    // write: polar case
+  SG_WRITE_ZH,      // write: v0 == 0 case
+  SG_WRITE          // write: general case
+};
+
+// Thresholds of the two phases: the FP32 phase hands over once a Halley step
+// is below kSgF32Tol times the distance of x to the ends of its interval (or
+// after kSgF32Max passes); the FP64 phase stops after a step below kSgF64Tol
+// of that distance (Halley's cubic convergence leaves an error far below
+// rounding after such a step).
+constexpr double kSgF32Tol = 1e-5;
+constexpr int kSgF32Max = 40;
+constexpr double kSgF64Tol = 1e-5;
+constexpr int kSgF64Max = 200;
+// Elements per thread held in registers across passes (the rest re-read).
+constexpr int kSgSlots = 2;
+
+// Projection of the blocks (starts[b], dims[b]) of NV vectors onto
+// diag(e) K_soc, e = d or 1/d (inv) or 1 (d == NULL), with the squared scales
+// of the tail b_i = e_i^2 and their reciprocals precomputed (bq, bqi at
+// offs[b]; NULL: e = 1).  part needs 24 * gridDim.x doubles; every grid
+// barrier uses a fresh target, so the counter must be zero at launch.
+//
+// Root-finding (same secular equation and Halley steps as soc_proj_cta): an
+// FP32 phase from the closed-form start, whose per-element terms, CTA sums and
+// grid sums are all FP32, locates the root; an FP64 phase (bracket reset to
+// the whole interval) polishes it.  The tail is normalised by 2^-E, E the
+// binary exponent of max |v| (exact, and free in the integer conversions).
+// The NV vectors advance through the same passes, so they share the barriers.
+template <typename B, int NV>
+__global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
+    B* v0, B* v1, const int64_t* __restrict__ starts, const int64_t* __restrict__ dims,
+    const int64_t* __restrict__ offs, int nblocks, const double* __restrict__ d, int inv,
+    const double* __restrict__ bq, const double* __restrict__ bqi, const int* __restrict__ gate0,
+    const int* __restrict__ gate1, double* __restrict__ part, GridSync gs, KTimer* tm) {
+  constexpr int K = 3 * NV;
+  constexpr int RC = kSgSlots;
+  __shared__ double red[K * 512];
+  __shared__ float redf[32 * K];
+  __shared__ double tot[8];
+  __shared__ float totf[8];
+  __shared__ SocGridVec sv[NV];
+  bool act[NV];
+  act[0] = gate_on(gate0);
+  if (NV > 1) act[NV - 1] = gate_on(gate1);
+  bool any_act = false;
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = sh[k];
-  __syncthreads();
-}
-
-PDCS_DEV double grid_max1(double v, double* part_base, const GridSync& gs, unsigned int& target,
-                          double* sh, int& flip) {
-  double* part = part_base + (size_t)flip * 4 * gridDim.x;
-  flip ^= 1;
-  double a[1] = {v};
-  block_max<1>(a, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = a[0];
-  grid_sync(gs, target);
-  if (threadIdx.x < 32) {
-    long long s = 0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32)
-      s = max(s, __double_as_longlong(__ldcg(part + b)));
-    s = warp_max_bits(s);
-    if (threadIdx.x == 0) sh[0] = __longlong_as_double(s);
-  }
-  __syncthreads();
-  const double r = sh[0];
-  __syncthreads();
-  return r;
-}
-
-// Projection of the blocks (starts[b], dims[b]) of one or two vectors onto
-// diag(e) K_soc, e = d or 1/d (inv) or 1 (d == NULL).  part needs
-// 8 * gridDim.x doubles; every grid barrier uses a fresh target, so the
-// counter must be zero at launch.
-template <typename B>
-__global__ void __launch_bounds__(512) k_cone_soc_grid(B* v0, B* v1, int nvec,
-                                                       const int64_t* __restrict__ starts,
-                                                       const int64_t* __restrict__ dims,
-                                                       int nblocks, const double* __restrict__ d,
-                                                       int inv, const int* __restrict__ gate0,
-                                                       const int* __restrict__ gate1,
-                                                       double* __restrict__ part, GridSync gs,
-                                                       KTimer* tm) {
-  __shared__ double sh[3 * 512 + 3 + 8];
-  if (!gate_on(gate0) && (nvec == 1 || !gate_on(gate1))) return;  // whole launch idle
+  for (int q = 0; q < NV; ++q) any_act |= act[q];
+  if (!any_act) return;  // whole launch idle (gates are uniform)
   ktimer_begin(tm);
+  B* vp[NV];
+  vp[0] = v0;
+  if (NV > 1) vp[NV - 1] = v1;
   unsigned int target = 0;
   int flip = 0;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-  for (int q = 0; q < nvec; ++q) {
-    const int* gate = q == 0 ? gate0 : gate1;
-    if (gate != nullptr && *gate == 0) continue;  // uniform across the grid
-    B* v = q == 0 ? v0 : v1;
-    for (int blk = 0; blk < nblocks; ++blk) {
-      const int64_t s = starts[blk], dim = dims[blk];
-      const double v0h = (double)v[s];
-      const double e0 = cone_scale(d, s, inv);
-      double acc[2] = {0.0, 0.0};
-      double mx = fabs(v0h);
-      for (int64_t i = 1 + tid; i < dim; i += nth) {
-        const double vi = (double)v[s + i], ei = cone_scale(d, s + i, inv);
-        const double a = vi / ei, b = vi * ei;
-        acc[0] += a * a;
-        acc[1] += b * b;
-        mx = fmax(mx, fabs(vi));
+  for (int blk = 0; blk < nblocks; ++blk) {
+    const int64_t s = starts[blk], dim = dims[blk], o = offs[blk];
+    const double* bb = bq ? bq + o : nullptr;
+    const double* bbi = bqi ? bqi + o : nullptr;
+    // ---- pass 0: sum (v/e)^2, sum (e v)^2 and max |v| of each tail; the
+    // slots' v and b stay in registers
+    double bc[RC];
+    float bfc[RC];
+    double vc[NV][RC];
+    float afc[NV][RC];
+    double v0h[NV];
+    double acc[2 * NV];
+    long long amx[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      acc[2 * q] = 0.0;
+      acc[2 * q + 1] = 0.0;
+      v0h[q] = act[q] ? (double)vp[q][s] : 0.0;
+      amx[q] = __double_as_longlong(v0h[q]) & 0x7fffffffffffffffll;
+    }
+#pragma unroll
+    for (int k = 0; k < RC; ++k) {
+      const int64_t i = 1 + tid + k * nth;
+      const bool in = i < dim;
+      const double b = in && bb ? bb[i] : 1.0, bi = in && bbi ? bbi[i] : 1.0;
+      bc[k] = b;
+      bfc[k] = f32_trunc(b);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const double vi = in && act[q] ? (double)vp[q][s + i] : 0.0;
+        vc[q][k] = vi;
+        const double v2 = vi * vi;
+        acc[2 * q] = fma(v2, bi, acc[2 * q]);
+        acc[2 * q + 1] = fma(v2, b, acc[2 * q + 1]);
+        amx[q] = max(amx[q], __double_as_longlong(vi) & 0x7fffffffffffffffll);
       }
-      grid_sum<2>(acc, part, gs, target, sh, flip);
-      mx = grid_max1(mx, part, gs, target, sh, flip);
-      // every CTA read the head v[s] before the barriers above; it is only
-      // rewritten after them
-      if (sqrt(acc[0]) <= v0h / e0) continue;  // inside (uniform decision)
-      if (sqrt(acc[1]) <= -e0 * v0h) {         // polar: zero
-        for (int64_t i = tid; i < dim; i += nth) v[s + i] = (B)0.0;
-        continue;
+    }
+    for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
+      const double b = bb ? bb[i] : 1.0, bi = bbi ? bbi[i] : 1.0;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        if (!act[q]) continue;
+        const double vi = (double)vp[q][s + i], v2 = vi * vi;
+        acc[2 * q] = fma(v2, bi, acc[2 * q]);
+        acc[2 * q + 1] = fma(v2, b, acc[2 * q + 1]);
+        amx[q] = max(amx[q], __double_as_longlong(vi) & 0x7fffffffffffffffll);
       }
-      const double e02 = e0 * e0;
-      if (v0h == 0.0) {
-        double w[1] = {0.0};
-        for (int64_t i = 1 + tid; i < dim; i += nth) {
-          const double ei = cone_scale(d, s + i, inv), b = ei * ei;
-          const double nv = (double)v[s + i] * b / (b + e02);
-          const double t = nv / ei;
-          w[0] += t * t;
-        }
-        grid_sum<1>(w, part, gs, target, sh, flip);
-        for (int64_t i = 1 + tid; i < dim; i += nth) {
-          const double ei = cone_scale(d, s + i, inv), b = ei * ei;
-          v[s + i] = (B)((double)v[s + i] * b / (b + e02));
-        }
-        if (tid == 0) v[s] = (B)(e0 * sqrt(w[0]));
-        continue;
+    }
+    {
+      double r0[K];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        r0[2 * q] = acc[2 * q];
+        r0[2 * q + 1] = acc[2 * q + 1];
+        r0[2 * NV + q] = __longlong_as_double(amx[q]);
       }
-      const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
-      const double c0 = (v0h * sc) * (v0h * sc) * e02;
-      const bool pos = v0h > 0.0;
-      double lo = 0.0, hi = pos ? 0.5 * e02 : 1.0 / e02;
-      double x = soc_initial_guess(acc[0], acc[1], v0h, e0);
-      for (int it = 0; it < 200; ++it) {
-        double f[3] = {0.0, 0.0, 0.0};
-        for (int64_t i = 1 + tid; i < dim; i += nth) {
-          const double ei = cone_scale(d, s + i, inv);
-          const double vv = (double)v[s + i] * sc, b = ei * ei, a = vv * vv * b;
-          soc_secular_terms(pos, a, b, x, f);
+      const GridPart gp = grid_part(part, flip);
+      cta_rows_f64<K>(r0, 2 * NV, (1u << K) - 1u, red, gp);
+      grid_sync(gs, target);
+      grid_totals(gp, K, 2 * NV, 0u, tot, totf);
+      flip ^= 1;
+    }
+    if (threadIdx.x == 0) {
+      const double e0 = cone_scale(d, s, inv), e02 = e0 * e0;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        SocGridVec& g = sv[q];
+        g.mode = SG_DONE;
+        g.it = 0;
+        g.esh = 0;
+        g.xf = 0.0f;
+        g.w = 0.0;
+        g.mu2 = 0.0;
+        g.e0 = e0;
+        g.e02 = e02;
+        g.v0h = v0h[q];
+        g.pos = v0h[q] > 0.0;
+        if (!act[q]) continue;
+        const double s0 = tot[2 * q], s1 = tot[2 * q + 1], mx = tot[2 * NV + q];
+        if (sqrt(s0) <= v0h[q] / e0) continue;  // inside
+        if (sqrt(s1) <= -e0 * v0h[q]) {         // polar: zero
+          g.mode = SG_WRITE_ZERO;
+          continue;
         }
-        grid_sum<3>(f, part, gs, target, sh, flip);
-        // the scalar step is computed once per CTA and broadcast (redundant
-        // FP64 work in every thread would cost more than the pass itself)
-        if (threadIdx.x == 0) {
-          int stop = 0;
-          const double step = soc_halley_step(pos, f, c0, e02, x, lo, hi);
-          if (step == 0.0) {
-            stop = 1;
-          } else {
-            double xn = x + step;
-            if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-            x = xn;
-            if (hi - lo <= 1e-15 * hi) stop = 1;
+        if (v0h[q] == 0.0) {
+          g.mode = SG_ZERO_HEAD;
+          continue;
+        }
+        // 2^-E with E the binary exponent of max |v| (mx > 0 here)
+        const int E = ((__double2hiint(mx) >> 20) & 0x7ff) - 1023;
+        g.esh = E;
+        g.sc = ldexp(1.0, -E);
+        g.c0 = (v0h[q] * g.sc) * (v0h[q] * g.sc) * e02;
+        g.top = g.pos ? 0.5 * e02 : 1.0 / e02;
+        g.lo = 0.0;
+        g.hi = g.top;
+        g.x = soc_initial_guess(s0, s1, v0h[q], e0);
+        g.xf = (float)g.x;
+        g.mode = SG_F32;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int esh = sv[q].esh;
+      const bool f32 = sv[q].mode == SG_F32;
+#pragma unroll
+      for (int k = 0; k < RC; ++k) {
+        const float vf = f32 ? f32_trunc(vc[q][k], esh) : 0.0f;
+        afc[q][k] = vf * vf * bfc[k];
+      }
+    }
+    // ---- passes until every vector is written
+    for (;;) {
+      int mode[NV];
+      bool work = false;
+      unsigned m32 = 0u, m64 = 0u;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        mode[q] = sv[q].mode;
+        const SocGridVec& g = sv[q];
+        if (mode[q] >= SG_WRITE_ZERO) {
+          // write pass (each vector once: thread 0 retires the mode below,
+          // after a barrier every thread crosses first)
+          const double e02 = g.e02, mu2 = g.mu2;
+#pragma unroll
+          for (int k = 0; k < RC; ++k) {
+            const int64_t i = 1 + tid + k * nth;
+            if (i >= dim) continue;
+            const double b = bc[k];
+            double out = 0.0;
+            if (mode[q] == SG_WRITE_ZH) out = vc[q][k] * b / (b + e02);
+            else if (mode[q] == SG_WRITE) out = vc[q][k] * (b * rcp_nr(b + mu2));
+            vp[q][s + i] = (B)out;
           }
-          sh[0] = x; sh[1] = lo; sh[2] = hi; sh[3] = (double)stop;
+          for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
+            const double b = bb ? bb[i] : 1.0, vi = (double)vp[q][s + i];
+            double out = 0.0;
+            if (mode[q] == SG_WRITE_ZH) out = vi * b / (b + e02);
+            else if (mode[q] == SG_WRITE) out = vi * (b * rcp_nr(b + mu2));
+            vp[q][s + i] = (B)out;
+          }
+          if (tid == 0) {
+            double h = 0.0;
+            if (mode[q] == SG_WRITE_ZH) h = g.e0 * sqrt(g.w);
+            else if (mode[q] == SG_WRITE)
+              h = g.pos ? g.v0h * e02 / (e02 - mu2) : g.v0h * e02 * g.x / (e02 * g.x - 1.0);
+            vp[q][s] = (B)h;
+          }
+        } else if (mode[q] == SG_F32) {
+          work = true;
+          m32 |= 7u << (3 * q);
+        } else if (mode[q] != SG_DONE) {
+          work = true;
+          m64 |= 7u << (3 * q);
         }
-        __syncthreads();
-        x = sh[0]; lo = sh[1]; hi = sh[2];
-        const bool stop = sh[3] != 0.0;
-        __syncthreads();
-        if (stop) break;
       }
-      const double mu2 = pos ? 2.0 * x : 1.0 / x;
-      for (int64_t i = 1 + tid; i < dim; i += nth) {
-        const double ei = cone_scale(d, s + i, inv), b = ei * ei;
-        v[s + i] = (B)((double)v[s + i] * (b * rcp_nr(b + mu2)));
+      if (!work) break;
+      float fv[K];
+      double dv[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) { fv[k] = 0.0f; dv[k] = 0.0; }
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const SocGridVec& g = sv[q];
+        const bool pos = g.pos != 0;
+        if (mode[q] == SG_F32) {
+          const float xf = g.xf;
+#pragma unroll
+          for (int k = 0; k < RC; ++k) {
+            const float b = bfc[k], a = afc[q][k];  // a = 0 beyond the tail
+            const float r = pos ? __frcp_rn(fmaf(2.0f, xf, b)) : __frcp_rn(fmaf(b, xf, 1.0f));
+            const float ar2 = a * r * r;
+            fv[3 * q] += ar2;
+            fv[3 * q + 1] += pos ? ar2 * r : ar2 * b * r;
+            fv[3 * q + 2] += pos ? ar2 * r * r : ar2 * b * b * r * r;
+          }
+          for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
+            const float bf = f32_trunc(bb ? bb[i] : 1.0), vf = f32_trunc((double)vp[q][s + i], g.esh);
+            const float a = vf * vf * bf;
+            const float r = pos ? __frcp_rn(fmaf(2.0f, xf, bf)) : __frcp_rn(fmaf(bf, xf, 1.0f));
+            const float ar2 = a * r * r;
+            fv[3 * q] += ar2;
+            fv[3 * q + 1] += pos ? ar2 * r : ar2 * bf * r;
+            fv[3 * q + 2] += pos ? ar2 * r * r : ar2 * bf * bf * r * r;
+          }
+        } else if (mode[q] == SG_F64) {
+          double f[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+          for (int k = 0; k < RC; ++k) {
+            if (1 + tid + k * nth >= dim) continue;
+            const double vv = vc[q][k] * g.sc, b = bc[k];
+            soc_secular_terms(pos, vv * vv * b, b, g.x, f);
+          }
+          for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
+            const double b = bb ? bb[i] : 1.0, vv = (double)vp[q][s + i] * g.sc;
+            soc_secular_terms(pos, vv * vv * b, b, g.x, f);
+          }
+          dv[3 * q] = f[0];
+          dv[3 * q + 1] = f[1];
+          dv[3 * q + 2] = f[2];
+        } else if (mode[q] == SG_ZERO_HEAD) {
+          // |new tail / e|^2 with new v_i = v_i b_i / (b_i + e0^2)
+          double w = 0.0;
+#pragma unroll
+          for (int k = 0; k < RC; ++k) {
+            if (1 + tid + k * nth >= dim) continue;
+            const double b = bc[k], t = vc[q][k] / (b + g.e02);
+            w += t * t * b;
+          }
+          for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
+            const double b = bb ? bb[i] : 1.0, t = (double)vp[q][s + i] / (b + g.e02);
+            w += t * t * b;
+          }
+          dv[3 * q] = w;
+        }
       }
-      if (tid == 0) v[s] = (B)(pos ? v0h * e02 / (e02 - mu2) : v0h * e02 * x / (e02 * x - 1.0));
+      const GridPart gp = grid_part(part, flip);
+      if (m32) cta_rows_f32<K>(fv, m32, redf, gp);
+      if (m64) cta_rows_f64<K>(dv, K, m64, red, gp);
+      grid_sync(gs, target);
+      grid_totals(gp, K, K, m32, tot, totf);
+      flip ^= 1;
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          SocGridVec& g = sv[q];
+          if (g.mode >= SG_WRITE_ZERO) { g.mode = SG_DONE; continue; }
+          if (g.mode == SG_ZERO_HEAD) {
+            g.w = tot[3 * q];
+            g.mode = SG_WRITE_ZH;
+            continue;
+          }
+          if (g.mode != SG_F32 && g.mode != SG_F64) continue;
+          const bool pos = g.pos != 0;
+          const bool f32 = g.mode == SG_F32;
+          double f[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) f[j] = f32 ? (double)totf[3 * q + j] : tot[3 * q + j];
+          const double dist = fmin(g.x, g.top - g.x);
+          const double step = soc_halley_step(pos, f, g.c0, g.e02, g.x, g.lo, g.hi);
+          bool small = step == 0.0;
+          if (!small) {
+            double xn = g.x + step;
+            if (!(xn > g.lo && xn < g.hi)) xn = 0.5 * (g.lo + g.hi);
+            g.x = xn;
+            small = fabs(step) <= (f32 ? kSgF32Tol : kSgF64Tol) * dist;
+          }
+          ++g.it;
+          if (f32) {
+            if (small || g.it >= kSgF32Max) {  // hand over; the FP32 bracket is not trusted
+              g.mode = SG_F64;
+              g.it = 0;
+              g.lo = 0.0;
+              g.hi = g.top;
+            }
+          } else if (small || g.hi - g.lo <= 1e-15 * g.hi || g.it >= kSgF64Max) {
+            g.mode = SG_WRITE;
+            g.mu2 = pos ? 2.0 * g.x : 1.0 / g.x;
+          }
+          g.xf = (float)g.x;
+        }
+      }
+      __syncthreads();
     }
   }
   ktimer_end(tm);

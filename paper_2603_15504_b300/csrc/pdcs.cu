@@ -182,6 +182,9 @@ struct ConeTable {
   int64_t nsoc[3] = {0, 0, 0};
   int64_t* big_s = nullptr;
   int64_t* big_d = nullptr;
+  int64_t* big_o = nullptr;   // offset of each big block in big_b / big_bi
+  double* big_b = nullptr;    // d_i^2 over the big blocks (in block order)
+  double* big_bi = nullptr;   // 1 / d_i^2
   int nbig = 0;
   int64_t* exp_s = nullptr;
   uint8_t* exp_isd = nullptr;
@@ -194,6 +197,17 @@ struct ConeTable {
 };
 
 __global__ void k_zero_u32(unsigned int* p) { *p = 0u; }
+
+// b[i] = d[i]^2, bi[i] = 1 / d[i]^2 for i < n.
+__global__ void k_square_scales(const double* __restrict__ d, int64_t n, double* __restrict__ b,
+                                double* __restrict__ bi) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double di = d[i], r = 1.0 / di;
+    b[i] = di * di;
+    bi[i] = r * r;
+  }
+}
 
 static const int kSocTierMax[3] = {128, 4096, 8192};
 
@@ -229,9 +243,20 @@ static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d,
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B>, v0, v1, nvec, (const int64_t*)t.big_s,
-                          (const int64_t*)t.big_d, t.nbig, d, inv, g0, g1, t.gpart, t.gsync,
-                          tm ? tm + TM_SOC_GRID : (KTimer*)nullptr));
+    // squared scales of the target diag(e) K: e = d (b = d^2), 1/d (b = 1/d^2)
+    // or 1 (no arrays)
+    const double* bq = d == nullptr ? nullptr : (inv ? t.big_bi : t.big_b);
+    const double* bqi = d == nullptr ? nullptr : (inv ? t.big_b : t.big_bi);
+    KTimer* tg = tm ? tm + TM_SOC_GRID : (KTimer*)nullptr;
+    const int64_t* bs = t.big_s;
+    const int64_t* bd = t.big_d;
+    const int64_t* bo = t.big_o;
+    if (nvec == 2)
+      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 2>, v0, v1, bs, bd, bo, t.nbig, d, inv, bq,
+                            bqi, g0, g1, t.gpart, t.gsync, tg));
+    else
+      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 1>, v0, v1, bs, bd, bo, t.nbig, d, inv, bq,
+                            bqi, g0, g1, t.gpart, t.gsync, tg));
   }
 }
 
@@ -501,8 +526,8 @@ struct Solver : SolverBase {
     ck = ar.alloc<uint8_t>(n);
     copy_in(rk, hrk.data(), m, st);
     copy_in(ck, hck.data(), n, st);
-    fill_table(rows, rsoc, rbig, rexp, rexpd);
-    fill_table(cols, csoc, cbig, cexp, cexpd);
+    fill_table(rows, rsoc, rbig, rexp, rexpd, d1);
+    fill_table(cols, csoc, cbig, cexp, cexpd, d2);
     const int small_g = sizeof(T) == 8 ? 4 : 8;
     planG = build_plan(hrp, ar, st, small_g);
     planGT = build_plan(hrpT, ar, st, small_g);
@@ -557,26 +582,48 @@ struct Solver : SolverBase {
 
   void fill_table(ConeTable& t, const std::vector<std::vector<std::pair<int64_t, int32_t>>>& soc,
                   const std::vector<std::pair<int64_t, int64_t>>& big,
-                  const std::vector<int64_t>& ex, const std::vector<uint8_t>& exd) {
+                  const std::vector<int64_t>& ex, const std::vector<uint8_t>& exd,
+                  const double* dscale) {
     t.nbig = (int)big.size();
     if (t.nbig > 0) {
-      std::vector<int64_t> bs, bd;
-      for (auto& pr : big) { bs.push_back(pr.first); bd.push_back(pr.second); }
+      std::vector<int64_t> bs, bd, bo;
+      int64_t tot = 0;
+      for (auto& pr : big) {
+        bs.push_back(pr.first);
+        bd.push_back(pr.second);
+        bo.push_back(tot);
+        tot += pr.second;
+      }
       t.big_s = ar.alloc<int64_t>(t.nbig);
       t.big_d = ar.alloc<int64_t>(t.nbig);
+      t.big_o = ar.alloc<int64_t>(t.nbig);
       copy_in(t.big_s, bs.data(), (int64_t)t.nbig, st);
       copy_in(t.big_d, bd.data(), (int64_t)t.nbig, st);
+      copy_in(t.big_o, bo.data(), (int64_t)t.nbig, st);
+      t.big_b = ar.alloc<double>(tot);
+      t.big_bi = ar.alloc<double>(tot);
+      for (int b = 0; b < t.nbig; ++b)
+        k_square_scales<<<ew_grid(bd[b]), 256, 0, st>>>(dscale + bs[b], bd[b], t.big_b + bo[b],
+                                                       t.big_bi + bo[b]);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(st));
       if (!gsync_count) {
-        int dev = 0, sms = 0, occ_t = 0, occ_d = 0;
+        int dev = 0, sms = 0, occ = 2, o = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, k_cone_soc_grid<T>, 512, 0));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, k_cone_soc_grid<double>, 512, 0));
-        const int occ = std::max(1, std::min(std::min(occ_t, occ_d), 2));
-        big_grid = sms * occ;
+        // one grid size for every variant (cooperative launches need all CTAs resident)
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<T, 1>, 512, 0));
+        occ = std::min(occ, o);
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<T, 2>, 512, 0));
+        occ = std::min(occ, o);
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<double, 1>, 512, 0));
+        occ = std::min(occ, o);
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<double, 2>, 512, 0));
+        occ = std::max(1, std::min(occ, o));
+        big_grid = std::min(sms * occ, kMaxGridParts);
         gsync_count = ar.alloc<unsigned int>(1);
         gsync_err = ar.alloc<int>(1);
-        gpart = ar.alloc<double>(8 * (int64_t)big_grid);
+        gpart = ar.alloc<double>(24 * (int64_t)big_grid);
         CK(cudaMemsetAsync(gsync_count, 0, sizeof(unsigned int), st));
         CK(cudaMemsetAsync(gsync_err, 0, sizeof(int), st));
       }

@@ -154,12 +154,16 @@ PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
   __syncthreads();
   if (s_ticket == (unsigned)(t.nchunks - 1)) {
     __threadfence();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // lanes take chunks lane, lane + 32, ... (loads issued together), add
+      // them in order, then a fixed butterfly: deterministic
       double s = 0.0;
-      const volatile double* p = partial + t.pbase;
-      for (int j = 0; j < t.nchunks; ++j) s += p[j];
-      y[t.a] = (T)s;
-      counters[t.counter] = 0u;
+      for (int j = threadIdx.x; j < t.nchunks; j += 32) s += __ldcg(partial + t.pbase + j);
+      s = warp_sum(s);
+      if (threadIdx.x == 0) {
+        y[t.a] = (T)s;
+        counters[t.counter] = 0u;
+      }
     }
   }
 }
