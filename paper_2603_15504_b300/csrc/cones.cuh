@@ -237,28 +237,42 @@ PDCS_HD void soc_secular_terms(bool pos, double a, double b, double x, double (&
   }
 }
 
-// One safeguarded Halley step on F (v0 > 0: F(mu) = sum a/(b+2mu)^2 -
-// c0/(e0^2-2mu)^2) or H (v0 < 0: H(nu) = sum a/(1+b nu)^2 - c0/(1-e0^2 nu)^2),
-// both decreasing on their interval.  Updates the bracket [lo, hi] (F > 0 at
+// F (v0 > 0: F(mu) = sum a/(b+2mu)^2 - c0/(e0^2-2mu)^2; v0 < 0: H(nu) =
+// sum a/(1+b nu)^2 - c0/(1-e0^2 nu)^2) and its first two derivatives at x from
+// the element sums f of soc_secular_terms; both functions decrease on their
+// interval.  T = double, or float for the FP32 search phase.
+template <typename T>
+PDCS_HD void soc_fderiv(bool pos, const T (&f)[3], T c0, T e02, T x, T& F, T& dF, T& d2F) {
+  if (pos) {
+    const T r = T(1) / (e02 - T(2) * x);
+    F = f[0] - c0 * r * r;
+    dF = T(-4) * f[1] - T(4) * c0 * r * r * r;
+    d2F = T(24) * f[2] - T(24) * c0 * r * r * r * r;
+  } else {
+    const T r = T(1) / (T(1) - e02 * x);
+    F = f[0] - c0 * r * r;
+    dF = T(-2) * f[1] - T(2) * c0 * e02 * r * r * r;
+    d2F = T(6) * f[2] - T(6) * c0 * e02 * e02 * r * r * r * r;
+  }
+}
+
+// Halley step -2 F F' / (2 F'^2 - F F''), Newton's where that is not finite.
+template <typename T>
+PDCS_HD T soc_halley(T F, T dF, T d2F) {
+  T step = T(-2) * F * dF / (T(2) * dF * dF - F * d2F);
+  if (!(fabs(step) < T(INFINITY))) step = -F / dF;
+  return step;
+}
+
+// One safeguarded Halley step on F.  Updates the bracket [lo, hi] (F > 0 at
 // lo); returns the step, 0 when converged (the caller then stops).
 PDCS_HD double soc_halley_step(bool pos, const double (&f)[3], double c0, double e02, double& x,
                                double& lo, double& hi) {
   double F, dF, d2F;
-  if (pos) {
-    const double r = 1.0 / (e02 - 2.0 * x);
-    F = f[0] - c0 * r * r;
-    dF = -4.0 * f[1] - 4.0 * c0 * r * r * r;
-    d2F = 24.0 * f[2] - 24.0 * c0 * r * r * r * r;
-  } else {
-    const double r = 1.0 / (1.0 - e02 * x);
-    F = f[0] - c0 * r * r;
-    dF = -2.0 * f[1] - 2.0 * c0 * e02 * r * r * r;
-    d2F = 6.0 * f[2] - 6.0 * c0 * e02 * e02 * r * r * r * r;
-  }
+  soc_fderiv(pos, f, c0, e02, x, F, dF, d2F);
   if (F > 0.0) lo = x; else hi = x;
   if (F == 0.0) return 0.0;
-  double step = -2.0 * F * dF / (2.0 * dF * dF - F * d2F);
-  if (!(fabs(step) < INFINITY)) step = -F / dF;
+  const double step = soc_halley(F, dF, d2F);
   const double xn = x + step;
   if (fabs(step) <= 1e-15 * x) {  // converged; the step may not even move x
     if (xn >= lo && xn <= hi) x = xn;

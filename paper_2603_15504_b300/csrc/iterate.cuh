@@ -859,26 +859,28 @@ PDCS_DEV void grid_sync(const GridSync& gs, unsigned int& target) {
   __syncthreads();
 }
 
-// Grid-wide reductions of the cooperative SOC kernel.  Each pass stages K <= 8
-// values per CTA in a partial buffer, crosses one grid barrier, and then warp
-// k reduces value k over the CTAs in a fixed order (lane l takes CTAs l,
-// l + 32, ... with all loads issued together, then a fixed butterfly), leaving
-// the total in out[k].  Every CTA adds the same partials in the same order, so
-// all CTAs obtain bit-identical totals and take identical decisions.
+// Grid-wide reductions of the cooperative SOC kernel.  Each pass stages its
+// values per CTA in a partial buffer, crosses one grid barrier, and then the
+// CTA adds the partials of all CTAs in a fixed order (so every CTA obtains
+// bit-identical totals and takes identical decisions).
 //
-// Buffer layout (G = gridDim.x): two alternating halves of 12 G doubles (a CTA
-// that runs ahead never overwrites partials another CTA is still reading);
-// each half holds 8 slots x G FP64 values, slot-major (so the reads after the
-// barrier coalesce), followed by 8 slots x G FP32 values.  Slots < KS are
-// sums, the others maxima of non-negative values (integer bit-pattern maxima);
-// slots in f32mask are FP32 sums.
+// Buffer layout (G = gridDim.x): two alternating halves of kSgHalf * G
+// doubles (a CTA that runs ahead never overwrites partials another CTA is
+// still reading); each half holds 8 FP64 slots x G, slot-major (so the reads
+// after the barrier coalesce), followed by kSgF32Slots FP32 slots x G.  FP64
+// slots < KS are sums, the others maxima of non-negative values (integer
+// bit-pattern maxima).
+constexpr int kSgProbes = 8;                     // probe points of pass 0 per vector
+constexpr int kSgF32Slots = 3 * kSgProbes * 2;   // FP32 slots (up to two vectors)
+constexpr int kSgHalf = 8 + kSgF32Slots / 2;     // doubles per CTA per half
+
 struct GridPart {
   double* d;
   float* f;
 };
 
 PDCS_DEV GridPart grid_part(double* base, int flip) {
-  double* h = base + (size_t)flip * 12 * gridDim.x;
+  double* h = base + (size_t)flip * kSgHalf * gridDim.x;
   return GridPart{h, reinterpret_cast<float*>(h + 8 * (size_t)gridDim.x)};
 }
 
@@ -931,8 +933,10 @@ PDCS_DEV void cta_rows_f32(const float (&v)[K], unsigned mask, float* redf, Grid
   }
 }
 
-// After the barrier: out[k] = grid total of slot k (k < K); FP32 totals are
-// left in outf (not widened: the FP64 pipe is scarce).
+// After the barrier: warp k < K totals slot k (lane l takes CTAs l, l + 32,
+// ... with all loads issued together, then a fixed butterfly).  FP64 totals go
+// to out, FP32 ones (slots in f32mask) to outf, not widened (the FP64 pipe is
+// scarce).
 PDCS_DEV void grid_totals(GridPart p, int K, int KS, unsigned f32mask, double* out, float* outf) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned G = gridDim.x;
@@ -982,12 +986,40 @@ PDCS_DEV void grid_totals(GridPart p, int K, int KS, unsigned f32mask, double* o
   __syncthreads();
 }
 
-// Per-vector scalar state of the grid-wide SOC root-finding.  Thread 0 of
-// every CTA updates it from the same grid totals, so all copies agree; the
-// other threads only read it (xf, pos and esh spare them FP64 instructions).
+// After the pass-0 barrier: the FP64 totals (warps < K64, as grid_totals)
+// and, at the same time, the FP32 totals of the S probe slots (the remaining
+// threads, (blockDim.x - 32 K64) / S per slot, each a strided run of CTAs,
+// then a fixed-order sum), so that all loads are in flight together.
+// scratch holds blockDim.x floats.
+PDCS_DEV void grid_totals_pass0(GridPart p, int K64, int KS, int S, float* scratch, double* out,
+                                float* outp) {
+  const int G = gridDim.x, t = threadIdx.x;
+  const int t0 = 32 * K64, tps = S > 0 ? (blockDim.x - t0) / S : 0;
+  if (t >= t0 && S > 0) {
+    const int u = t - t0, sl = u / tps, sub = u - sl * tps;
+    float acc = 0.0f;
+    if (sl < S) {
+      const float* src = p.f + (size_t)sl * G;
+#pragma unroll 16
+      for (int b = sub; b < G; b += tps) acc += __ldcg(src + b);
+    }
+    scratch[u] = acc;
+  }
+  grid_totals(p, K64, KS, 0u, out, nullptr);  // ends with __syncthreads
+  if (t < S) {
+    float a = 0.0f;
+    for (int k = 0; k < tps; ++k) a += scratch[t * tps + k];
+    outp[t] = a;
+  }
+  __syncthreads();
+}
+
+// Per-vector scalar state of the grid-wide SOC root-finding.  Warp 0 of every
+// CTA updates it from the same grid totals, so all copies agree; the other
+// threads only read it (xf, pos and esh spare them FP64 instructions).
 struct SocGridVec {
-  double x, lo, hi, top, sc, c0, e0, e02, v0h, w, mu2;
-  float xf;
+  double x, lo, hi, top, sc, c0, e02, v0h, w, mu2;  // FP64 phase and writes
+  float xf, lof, hif, topf, c0f, e02f;              // probes and FP32 phase
   int pos, esh, mode, it;
 };
 enum : int {
@@ -1003,40 +1035,62 @@ enum : int {
 // Thresholds of the two phases: the FP32 phase hands over once a Halley step
 // is below kSgF32Tol times the distance of x to the ends of its interval (or
 // after kSgF32Max passes); the FP64 phase stops after a step below kSgF64Tol
-// of that distance (Halley's cubic convergence leaves an error far below
-// rounding after such a step).
+// of that distance: Halley's cubic convergence leaves an error of order
+// (1e-4)^3 of the distance after such a step, far below what the FP64 sums
+// resolve.
 constexpr double kSgF32Tol = 1e-5;
 constexpr int kSgF32Max = 40;
-constexpr double kSgF64Tol = 1e-5;
+constexpr double kSgF64Tol = 1e-4;
 constexpr int kSgF64Max = 200;
-// Elements per thread held in registers across passes (the rest re-read).
+// Elements per thread held in registers across passes (the rest re-read; the
+// pass-0 probes need every element of the CTA in a slot).
 constexpr int kSgSlots = 2;
+// Probe abscissae: x_j = top / (1 + exp(-u_j)), u_j evenly spaced in
+// [-kSgProbeU, kSgProbeU] (logit scale, so both ends of (0, top) are covered).
+constexpr float kSgProbeU = 12.0f;
+
+// Probe j of an interval (0, topf), in FP32 (every thread computes it the same way).
+PDCS_DEV float sg_probe_x(float topf, int j) {
+  const float u = -kSgProbeU + 2.0f * kSgProbeU * ((float)j + 0.5f) / (float)kSgProbes;
+  return topf / (1.0f + expf(-u));
+}
 
 // Projection of the blocks (starts[b], dims[b]) of NV vectors onto
-// diag(e) K_soc, e = d or 1/d (inv) or 1 (d == NULL), with the squared scales
-// of the tail b_i = e_i^2 and their reciprocals precomputed (bq, bqi at
-// offs[b]; NULL: e = 1).  part needs 24 * gridDim.x doubles; every grid
-// barrier uses a fresh target, so the counter must be zero at launch.
+// diag(e) K_soc, given the squared scales b_i = e_i^2 of each block (head
+// included) and their reciprocals (bq, bqi at offs[b]; NULL: e = 1).  part needs 2 * kSgHalf * gridDim.x
+// doubles; every grid barrier uses a fresh target, so the counter must be zero
+// at launch.  CTA c owns the tail elements 1 + c * chunk ... of each block.
 //
-// Root-finding (same secular equation and Halley steps as soc_proj_cta): an
-// FP32 phase from the closed-form start, whose per-element terms, CTA sums and
-// grid sums are all FP32, locates the root; an FP64 phase (bracket reset to
-// the whole interval) polishes it.  The tail is normalised by 2^-E, E the
-// binary exponent of max |v| (exact, and free in the integer conversions).
-// The NV vectors advance through the same passes, so they share the barriers.
+// Root-finding (the secular equation and Halley steps of soc_proj_cta):
+//  * pass 0 adds, besides the norms that decide inside / polar, the FP32
+//    element sums at kSgProbes fixed abscissae of (0, top); their signs
+//    bracket the root and the best of their Halley steps starts
+//  * an FP32 phase whose per-element terms, CTA sums and grid sums are all
+//    FP32 narrows it down
+//  * an FP64 phase (bracket reset to the whole interval) polishes it.
+// The tail is normalised by 2^-E, E the binary exponent of max |v| (exact, and
+// free in the integer conversions).  The NV vectors advance through the same
+// passes, so they share the barriers.
 template <typename B, int NV>
 __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
     B* v0, B* v1, const int64_t* __restrict__ starts, const int64_t* __restrict__ dims,
-    const int64_t* __restrict__ offs, int nblocks, const double* __restrict__ d, int inv,
-    const double* __restrict__ bq, const double* __restrict__ bqi, const int* __restrict__ gate0,
+    const int64_t* __restrict__ offs, int nblocks, const double* __restrict__ bq,
+    const double* __restrict__ bqi, const int* __restrict__ gate0,
     const int* __restrict__ gate1, double* __restrict__ part, GridSync gs, KTimer* tm) {
   constexpr int K = 3 * NV;
   constexpr int RC = kSgSlots;
+  constexpr int PS = 3 * kSgProbes;  // probe sums per vector
   __shared__ double red[K * 512];
   __shared__ float redf[32 * K];
+  __shared__ float pa[RC * 512], pb[RC * 512];
+  __shared__ float pred[16 * PS];
+  __shared__ float scratch[512];
+  __shared__ float ptot[NV * PS];
   __shared__ double tot[8];
   __shared__ float totf[8];
   __shared__ SocGridVec sv[NV];
+  // the first block's table entries load together with the gates
+  int64_t s = starts[0], dim = dims[0], o = offs[0];
   bool act[NV];
   act[0] = gate_on(gate0);
   if (NV > 1) act[NV - 1] = gate_on(gate1);
@@ -1050,14 +1104,21 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
   if (NV > 1) vp[NV - 1] = v1;
   unsigned int target = 0;
   int flip = 0;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int t = threadIdx.x, nt = blockDim.x, w = t >> 5, lane = t & 31;
   for (int blk = 0; blk < nblocks; ++blk) {
-    const int64_t s = starts[blk], dim = dims[blk], o = offs[blk];
+    if (blk > 0) {
+      s = starts[blk];
+      dim = dims[blk];
+      o = offs[blk];
+    }
     const double* bb = bq ? bq + o : nullptr;
     const double* bbi = bqi ? bqi + o : nullptr;
-    // ---- pass 0: sum (v/e)^2, sum (e v)^2 and max |v| of each tail; the
-    // slots' v and b stay in registers
+    const int64_t chunk = (dim - 1 + gridDim.x - 1) / gridDim.x;
+    const int64_t cbeg = 1 + (int64_t)blockIdx.x * chunk;
+    const int64_t cend = min(dim, cbeg + chunk);
+    const bool probes_ok = chunk <= (int64_t)RC * nt;  // every element in a slot
+    // ---- pass 0: sum (v/e)^2, sum (e v)^2 and max |v| of each tail (FP64),
+    // and the FP32 probe sums; the slots' v and b stay in registers
     double bc[RC];
     float bfc[RC];
     double vc[NV][RC];
@@ -1065,6 +1126,7 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
     double v0h[NV];
     double acc[2 * NV];
     long long amx[NV];
+    const double b0 = bb ? bb[0] : 1.0;  // the head's squared scale
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       acc[2 * q] = 0.0;
@@ -1074,8 +1136,8 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
     }
 #pragma unroll
     for (int k = 0; k < RC; ++k) {
-      const int64_t i = 1 + tid + k * nth;
-      const bool in = i < dim;
+      const int64_t i = cbeg + t + k * nt;
+      const bool in = i < cend;
       const double b = in && bb ? bb[i] : 1.0, bi = in && bbi ? bbi[i] : 1.0;
       bc[k] = b;
       bfc[k] = f32_trunc(b);
@@ -1089,7 +1151,7 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
         amx[q] = max(amx[q], __double_as_longlong(vi) & 0x7fffffffffffffffll);
       }
     }
-    for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
+    for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
       const double b = bb ? bb[i] : 1.0, bi = bbi ? bbi[i] : 1.0;
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
@@ -1100,6 +1162,54 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
         amx[q] = max(amx[q], __double_as_longlong(vi) & 0x7fffffffffffffffll);
       }
     }
+    const GridPart gp0 = grid_part(part, flip);
+    // probes: thread t evaluates probe t % kSgProbes over elements
+    // t / kSgProbes, + nt / kSgProbes, ... of the CTA (unnormalised FP32
+    // terms; the root does not depend on the scale)
+    const float b0f = f32_trunc(b0);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      if (!act[q] || !probes_ok) continue;  // uniform
+      const bool posq = __double_as_longlong(v0h[q]) > 0ll;
+      const float topf = posq ? 0.5f * b0f : __frcp_rn(b0f);
+#pragma unroll
+      for (int k = 0; k < RC; ++k) {
+        const float vf = f32_trunc(vc[q][k]);
+        pa[t + k * nt] = vf * vf * bfc[k];
+        pb[t + k * nt] = bfc[k];
+      }
+      __syncthreads();
+      const int j = t % kSgProbes;
+      const float xj = sg_probe_x(topf, j);
+      float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
+      const int nel = (int)(cend - cbeg);
+      for (int e = t / kSgProbes; e < nel; e += nt / kSgProbes) {
+        const float b = pb[e], a = pa[e];
+        const float r = posq ? __frcp_rn(fmaf(2.0f, xj, b)) : __frcp_rn(fmaf(b, xj, 1.0f));
+        const float ar2 = a * r * r;
+        p0 += ar2;
+        p1 += posq ? ar2 * r : ar2 * b * r;
+        p2 += posq ? ar2 * r * r : ar2 * b * b * r * r;
+      }
+      // lanes with equal t % kSgProbes: butterflies over the other lane bits
+#pragma unroll
+      for (int off = kSgProbes; off < 32; off <<= 1) {
+        p0 += __shfl_xor_sync(0xffffffffu, p0, off);
+        p1 += __shfl_xor_sync(0xffffffffu, p1, off);
+        p2 += __shfl_xor_sync(0xffffffffu, p2, off);
+      }
+      if (lane < kSgProbes) {
+        pred[w * PS + 3 * lane] = p0;
+        pred[w * PS + 3 * lane + 1] = p1;
+        pred[w * PS + 3 * lane + 2] = p2;
+      }
+      __syncthreads();
+      if (t < PS) {
+        float a = 0.0f;
+        for (int ww = 0; ww < (nt >> 5); ++ww) a += pred[ww * PS + t];
+        gp0.f[(size_t)(q * PS + t) * gridDim.x + blockIdx.x] = a;
+      }
+    }
     {
       double r0[K];
 #pragma unroll
@@ -1108,49 +1218,113 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
         r0[2 * q + 1] = acc[2 * q + 1];
         r0[2 * NV + q] = __longlong_as_double(amx[q]);
       }
-      const GridPart gp = grid_part(part, flip);
-      cta_rows_f64<K>(r0, 2 * NV, (1u << K) - 1u, red, gp);
+      cta_rows_f64<K>(r0, 2 * NV, (1u << K) - 1u, red, gp0);
       grid_sync(gs, target);
-      grid_totals(gp, K, 2 * NV, 0u, tot, totf);
+      grid_totals_pass0(gp0, K, 2 * NV, probes_ok ? NV * PS : 0, scratch, tot, ptot);
       flip ^= 1;
     }
-    if (threadIdx.x == 0) {
-      const double e0 = cone_scale(d, s, inv), e02 = e0 * e0;
+    if (w == 0) {
+      // e0^2 is the head's precomputed squared scale (exactly e0 * e0)
+      const double e02 = b0;
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         SocGridVec& g = sv[q];
-        g.mode = SG_DONE;
-        g.it = 0;
-        g.esh = 0;
-        g.xf = 0.0f;
-        g.w = 0.0;
-        g.mu2 = 0.0;
-        g.e0 = e0;
-        g.e02 = e02;
-        g.v0h = v0h[q];
-        g.pos = v0h[q] > 0.0;
-        if (!act[q]) continue;
-        const double s0 = tot[2 * q], s1 = tot[2 * q + 1], mx = tot[2 * NV + q];
-        if (sqrt(s0) <= v0h[q] / e0) continue;  // inside
-        if (sqrt(s1) <= -e0 * v0h[q]) {         // polar: zero
-          g.mode = SG_WRITE_ZERO;
-          continue;
+        if (lane == 0) {
+          g.mode = SG_DONE;
+          g.it = 0;
+          g.esh = 0;
+          g.xf = 0.0f;
+          g.w = 0.0;
+          g.mu2 = 0.0;
+          g.e02 = e02;
+          g.v0h = v0h[q];
+          g.pos = v0h[q] > 0.0;
+          if (act[q]) {
+            // the tests of soc_proj_cta without roots or divisions:
+            // inside ||tail/e|| <= v0/e0, polar ||e tail|| <= -e0 v0
+            const double s0 = tot[2 * q], s1 = tot[2 * q + 1], mx = tot[2 * NV + q];
+            const double v2 = v0h[q] * v0h[q];
+            if (v0h[q] >= 0.0 && s0 * e02 <= v2) {
+              // inside
+            } else if (v0h[q] <= 0.0 && s1 <= e02 * v2) {
+              g.mode = SG_WRITE_ZERO;  // polar: zero
+            } else if (v0h[q] == 0.0) {
+              g.mode = SG_ZERO_HEAD;
+            } else {
+              // 2^-E with E the binary exponent of max |v| (mx > 0 here)
+              const int E = ((__double2hiint(mx) >> 20) & 0x7ff) - 1023;
+              g.esh = E;
+              g.sc = __hiloint2double((1023 - E) << 20, 0);
+              g.c0 = (v0h[q] * g.sc) * (v0h[q] * g.sc) * e02;
+              g.top = g.pos ? 0.5 * e02 : rcp_nr(e02);
+              g.lo = 0.0;
+              g.hi = g.top;
+              g.c0f = (float)g.c0;
+              g.e02f = (float)e02;
+              g.topf = (float)g.top;
+              g.lof = 0.0f;
+              g.hif = g.topf;
+              g.xf = -1.0f;  // no start yet
+              g.mode = SG_F32;
+            }
+          }
         }
-        if (v0h[q] == 0.0) {
-          g.mode = SG_ZERO_HEAD;
-          continue;
+        __syncwarp();
+        // probe selection in FP32 (lanes < kSgProbes, one probe each; the
+        // unnormalised probe sums are rescaled by 2^-2E, so |v| must lie
+        // within 2^+-40 for them to neither overflow nor underflow)
+        if (g.mode == SG_F32 && probes_ok && g.esh >= -40 && g.esh <= 40) {
+          const bool pos = g.pos != 0;
+          const float topf = pos ? 0.5f * b0f : __frcp_rn(b0f);  // as the probe abscissae
+          const float s2 = __uint_as_float((unsigned)(127 - 2 * g.esh) << 23);  // 2^-2E
+          const float c0 = g.c0f, e02f = g.e02f, top = g.topf;
+          int lo_b = 0, hi_b = __float_as_int(top);
+          int key = 0x7f800000;  // +inf: no candidate
+          float cand = 0.0f;
+          bool finite = true;
+          if (lane < kSgProbes) {
+            const float xj = sg_probe_x(topf, lane);
+            const float f[3] = {ptot[q * PS + 3 * lane] * s2, ptot[q * PS + 3 * lane + 1] * s2,
+                                ptot[q * PS + 3 * lane + 2] * s2};
+            float F, dF, d2F;
+            soc_fderiv(pos, f, c0, e02f, xj, F, dF, d2F);
+            finite = fabsf(F) < INFINITY && fabsf(dF) < INFINITY && fabsf(d2F) < INFINITY &&
+                     f[0] > 0.0f;
+            if (F > 0.0f) lo_b = __float_as_int(xj); else hi_b = __float_as_int(xj);
+            const float step = soc_halley(F, dF, d2F);
+            cand = xj + step;
+            const float rel = fabsf(step) / fminf(xj, top - xj);
+            if (rel < INFINITY) key = __float_as_int(rel);
+          }
+          // bracket: largest probe with F > 0, smallest with F <= 0
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            lo_b = max(lo_b, __shfl_xor_sync(0xffffffffu, lo_b, off));
+            hi_b = min(hi_b, __shfl_xor_sync(0xffffffffu, hi_b, off));
+          }
+          const float plo = __int_as_float(lo_b), phi = __int_as_float(hi_b);
+          if (!(cand > plo && cand < phi)) key = 0x7f800000;
+          // best candidate: smallest relative step, ties to the lowest lane
+          int kb = key;
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) kb = min(kb, __shfl_xor_sync(0xffffffffu, kb, off));
+          const unsigned hit = __ballot_sync(0xffffffffu, key == kb);
+          const float best = __shfl_sync(0xffffffffu, cand, __ffs(hit) - 1);
+          const bool all_finite = __all_sync(0xffffffffu, finite);
+          if (lane == 0 && all_finite && plo < phi) {
+            g.lof = plo;
+            g.hif = phi;
+            g.xf = kb < 0x7f800000 ? best : 0.5f * (plo + phi);
+          }
         }
-        // 2^-E with E the binary exponent of max |v| (mx > 0 here)
-        const int E = ((__double2hiint(mx) >> 20) & 0x7ff) - 1023;
-        g.esh = E;
-        g.sc = ldexp(1.0, -E);
-        g.c0 = (v0h[q] * g.sc) * (v0h[q] * g.sc) * e02;
-        g.top = g.pos ? 0.5 * e02 : 1.0 / e02;
-        g.lo = 0.0;
-        g.hi = g.top;
-        g.x = soc_initial_guess(s0, s1, v0h[q], e0);
-        g.xf = (float)g.x;
-        g.mode = SG_F32;
+        __syncwarp();
+        if (lane == 0 && g.mode == SG_F32 && !(g.xf > g.lof && g.xf < g.hif)) {
+          // no probe start: the closed-form one (e0 = sqrt(e0^2))
+          const double x0 = soc_initial_guess(tot[2 * q], tot[2 * q + 1], v0h[q], sqrt(e02));
+          g.xf = (float)x0;
+          if (!(g.xf > g.lof && g.xf < g.hif)) g.xf = 0.5f * (g.lof + g.hif);
+        }
+        __syncwarp();
       }
     }
     __syncthreads();
@@ -1174,29 +1348,29 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
         mode[q] = sv[q].mode;
         const SocGridVec& g = sv[q];
         if (mode[q] >= SG_WRITE_ZERO) {
-          // write pass (each vector once: thread 0 retires the mode below,
+          // write pass (each vector once: warp 0 retires the mode below,
           // after a barrier every thread crosses first)
           const double e02 = g.e02, mu2 = g.mu2;
 #pragma unroll
           for (int k = 0; k < RC; ++k) {
-            const int64_t i = 1 + tid + k * nth;
-            if (i >= dim) continue;
+            const int64_t i = cbeg + t + k * nt;
+            if (i >= cend) continue;
             const double b = bc[k];
             double out = 0.0;
             if (mode[q] == SG_WRITE_ZH) out = vc[q][k] * b / (b + e02);
             else if (mode[q] == SG_WRITE) out = vc[q][k] * (b * rcp_nr(b + mu2));
             vp[q][s + i] = (B)out;
           }
-          for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
+          for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
             const double b = bb ? bb[i] : 1.0, vi = (double)vp[q][s + i];
             double out = 0.0;
             if (mode[q] == SG_WRITE_ZH) out = vi * b / (b + e02);
             else if (mode[q] == SG_WRITE) out = vi * (b * rcp_nr(b + mu2));
             vp[q][s + i] = (B)out;
           }
-          if (tid == 0) {
+          if (blockIdx.x == 0 && t == 0) {
             double h = 0.0;
-            if (mode[q] == SG_WRITE_ZH) h = g.e0 * sqrt(g.w);
+            if (mode[q] == SG_WRITE_ZH) h = sqrt(e02) * sqrt(g.w);
             else if (mode[q] == SG_WRITE)
               h = g.pos ? g.v0h * e02 / (e02 - mu2) : g.v0h * e02 * g.x / (e02 * g.x - 1.0);
             vp[q][s] = (B)h;
@@ -1229,7 +1403,7 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
             fv[3 * q + 1] += pos ? ar2 * r : ar2 * b * r;
             fv[3 * q + 2] += pos ? ar2 * r * r : ar2 * b * b * r * r;
           }
-          for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
+          for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
             const float bf = f32_trunc(bb ? bb[i] : 1.0), vf = f32_trunc((double)vp[q][s + i], g.esh);
             const float a = vf * vf * bf;
             const float r = pos ? __frcp_rn(fmaf(2.0f, xf, bf)) : __frcp_rn(fmaf(bf, xf, 1.0f));
@@ -1242,11 +1416,11 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
           double f[3] = {0.0, 0.0, 0.0};
 #pragma unroll
           for (int k = 0; k < RC; ++k) {
-            if (1 + tid + k * nth >= dim) continue;
+            if (cbeg + t + k * nt >= cend) continue;
             const double vv = vc[q][k] * g.sc, b = bc[k];
             soc_secular_terms(pos, vv * vv * b, b, g.x, f);
           }
-          for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
+          for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
             const double b = bb ? bb[i] : 1.0, vv = (double)vp[q][s + i] * g.sc;
             soc_secular_terms(pos, vv * vv * b, b, g.x, f);
           }
@@ -1255,18 +1429,18 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
           dv[3 * q + 2] = f[2];
         } else if (mode[q] == SG_ZERO_HEAD) {
           // |new tail / e|^2 with new v_i = v_i b_i / (b_i + e0^2)
-          double w = 0.0;
+          double wv = 0.0;
 #pragma unroll
           for (int k = 0; k < RC; ++k) {
-            if (1 + tid + k * nth >= dim) continue;
-            const double b = bc[k], t = vc[q][k] / (b + g.e02);
-            w += t * t * b;
+            if (cbeg + t + k * nt >= cend) continue;
+            const double b = bc[k], tt = vc[q][k] / (b + g.e02);
+            wv += tt * tt * b;
           }
-          for (int64_t i = 1 + tid + RC * nth; i < dim; i += nth) {
-            const double b = bb ? bb[i] : 1.0, t = (double)vp[q][s + i] / (b + g.e02);
-            w += t * t * b;
+          for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
+            const double b = bb ? bb[i] : 1.0, tt = (double)vp[q][s + i] / (b + g.e02);
+            wv += tt * tt * b;
           }
-          dv[3 * q] = w;
+          dv[3 * q] = wv;
         }
       }
       const GridPart gp = grid_part(part, flip);
@@ -1275,7 +1449,7 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
       grid_sync(gs, target);
       grid_totals(gp, K, K, m32, tot, totf);
       flip ^= 1;
-      if (threadIdx.x == 0) {
+      if (t == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
           SocGridVec& g = sv[q];
@@ -1285,12 +1459,37 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
             g.mode = SG_WRITE_ZH;
             continue;
           }
-          if (g.mode != SG_F32 && g.mode != SG_F64) continue;
           const bool pos = g.pos != 0;
-          const bool f32 = g.mode == SG_F32;
-          double f[3];
-#pragma unroll
-          for (int j = 0; j < 3; ++j) f[j] = f32 ? (double)totf[3 * q + j] : tot[3 * q + j];
+          if (g.mode == SG_F32) {
+            // FP32 Halley step with bracket (FP32 state: the sums are FP32 too)
+            const float f[3] = {totf[3 * q], totf[3 * q + 1], totf[3 * q + 2]};
+            float F, dF, d2F;
+            const float x = g.xf;
+            soc_fderiv(pos, f, g.c0f, g.e02f, x, F, dF, d2F);
+            bool handover = !(fabsf(F) < INFINITY && fabsf(dF) < INFINITY && fabsf(d2F) < INFINITY);
+            if (!handover) {
+              if (F > 0.0f) g.lof = x; else g.hif = x;
+              const float step = F == 0.0f ? 0.0f : soc_halley(F, dF, d2F);
+              float xn = x + step;
+              if (!(xn > g.lof && xn < g.hif)) xn = 0.5f * (g.lof + g.hif);
+              const float dist = fminf(x, g.topf - x);
+              g.xf = xn;
+              ++g.it;
+              handover = fabsf(step) <= (float)kSgF32Tol * dist || g.it >= kSgF32Max ||
+                         !(xn > g.lof && xn < g.hif);
+            }
+            if (handover) {  // the FP32 bracket is not trusted
+              g.mode = SG_F64;
+              g.it = 0;
+              g.x = (double)g.xf;
+              if (!(g.x > 0.0 && g.x < g.top)) g.x = 0.5 * g.top;
+              g.lo = 0.0;
+              g.hi = g.top;
+            }
+            continue;
+          }
+          if (g.mode != SG_F64) continue;
+          const double f[3] = {tot[3 * q], tot[3 * q + 1], tot[3 * q + 2]};
           const double dist = fmin(g.x, g.top - g.x);
           const double step = soc_halley_step(pos, f, g.c0, g.e02, g.x, g.lo, g.hi);
           bool small = step == 0.0;
@@ -1298,21 +1497,13 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
             double xn = g.x + step;
             if (!(xn > g.lo && xn < g.hi)) xn = 0.5 * (g.lo + g.hi);
             g.x = xn;
-            small = fabs(step) <= (f32 ? kSgF32Tol : kSgF64Tol) * dist;
+            small = fabs(step) <= kSgF64Tol * dist;
           }
           ++g.it;
-          if (f32) {
-            if (small || g.it >= kSgF32Max) {  // hand over; the FP32 bracket is not trusted
-              g.mode = SG_F64;
-              g.it = 0;
-              g.lo = 0.0;
-              g.hi = g.top;
-            }
-          } else if (small || g.hi - g.lo <= 1e-15 * g.hi || g.it >= kSgF64Max) {
+          if (small || g.hi - g.lo <= 1e-15 * g.hi || g.it >= kSgF64Max) {
             g.mode = SG_WRITE;
             g.mu2 = pos ? 2.0 * g.x : 1.0 / g.x;
           }
-          g.xf = (float)g.x;
         }
       }
       __syncthreads();

@@ -252,11 +252,11 @@ static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d,
     const int64_t* bd = t.big_d;
     const int64_t* bo = t.big_o;
     if (nvec == 2)
-      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 2>, v0, v1, bs, bd, bo, t.nbig, d, inv, bq,
-                            bqi, g0, g1, t.gpart, t.gsync, tg));
+      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 2>, v0, v1, bs, bd, bo, t.nbig, bq, bqi, g0,
+                            g1, t.gpart, t.gsync, tg));
     else
-      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 1>, v0, v1, bs, bd, bo, t.nbig, d, inv, bq,
-                            bqi, g0, g1, t.gpart, t.gsync, tg));
+      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 1>, v0, v1, bs, bd, bo, t.nbig, bq, bqi, g0,
+                            g1, t.gpart, t.gsync, tg));
   }
 }
 
@@ -623,7 +623,7 @@ struct Solver : SolverBase {
         big_grid = std::min(sms * occ, kMaxGridParts);
         gsync_count = ar.alloc<unsigned int>(1);
         gsync_err = ar.alloc<int>(1);
-        gpart = ar.alloc<double>(24 * (int64_t)big_grid);
+        gpart = ar.alloc<double>(2 * kSgHalf * (int64_t)big_grid);
         CK(cudaMemsetAsync(gsync_count, 0, sizeof(unsigned int), st));
         CK(cudaMemsetAsync(gsync_err, 0, sizeof(int), st));
       }
