@@ -40,7 +40,11 @@ UNIT = "PDHG iterations/s"
 CHECK_FREQ = 64
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
 # (precision, source digest of spmv.cuh at capture time); see profiles/.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/k_spmv_portfolio_n100k_fp64.md: 250.1 MB per launch at n = 100,000,
+    # scaled by the algorithmic bytes (x 2.005) to the n = 200,000 workload
+    ("fp64", "42628348ee83ef5d"): 501.5e6,
+}
 
 
 def _args():

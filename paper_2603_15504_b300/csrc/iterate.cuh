@@ -836,20 +836,23 @@ constexpr int kMaxGridParts = 512;
 // launched cooperatively, so all CTAs are resident; each barrier wait is still
 // bounded and, if it ever gives up, sets *err and lets the kernel finish.
 struct GridSync {
-  unsigned int* count;  // zeroed before every launch
+  // arrival counter, zeroed once at set-up and never reset: a barrier is the
+  // next multiple of gridDim.x arrivals (every launch using the counter has
+  // the same grid size, so arrivals fall into whole generations)
+  unsigned long long* count;
   int* err;
 };
 
-PDCS_DEV void grid_sync(const GridSync& gs, unsigned int& target) {
+PDCS_DEV void grid_sync(const GridSync& gs) {
   __syncthreads();
-  target += gridDim.x;
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(gs.count, 1u);
+    const unsigned long long g = gridDim.x;
+    const unsigned long long target = (atomicAdd(gs.count, 1ull) / g + 1) * g;
     unsigned long long spins = 0;
     while (true) {
-      unsigned int v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gs.count) : "memory");
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(gs.count) : "memory");
       if (v >= target) break;
       __nanosleep(64);
       if (++spins > (1ull << 24)) { atomicExch(gs.err, 1); break; }
@@ -1057,9 +1060,8 @@ PDCS_DEV float sg_probe_x(float topf, int j) {
 
 // Projection of the blocks (starts[b], dims[b]) of NV vectors onto
 // diag(e) K_soc, given the squared scales b_i = e_i^2 of each block (head
-// included) and their reciprocals (bq, bqi at offs[b]; NULL: e = 1).  part needs 2 * kSgHalf * gridDim.x
-// doubles; every grid barrier uses a fresh target, so the counter must be zero
-// at launch.  CTA c owns the tail elements 1 + c * chunk ... of each block.
+// included) and their reciprocals (bq, bqi at offs[b]; NULL: e = 1).  part
+// needs 2 * kSgHalf * gridDim.x doubles.  CTA c owns the tail elements 1 + c * chunk ... of each block.
 //
 // Root-finding (the secular equation and Halley steps of soc_proj_cta):
 //  * pass 0 adds, besides the norms that decide inside / polar, the FP32
@@ -1102,7 +1104,6 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
   B* vp[NV];
   vp[0] = v0;
   if (NV > 1) vp[NV - 1] = v1;
-  unsigned int target = 0;
   int flip = 0;
   const int t = threadIdx.x, nt = blockDim.x, w = t >> 5, lane = t & 31;
   for (int blk = 0; blk < nblocks; ++blk) {
@@ -1219,7 +1220,7 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
         r0[2 * NV + q] = __longlong_as_double(amx[q]);
       }
       cta_rows_f64<K>(r0, 2 * NV, (1u << K) - 1u, red, gp0);
-      grid_sync(gs, target);
+      grid_sync(gs);
       grid_totals_pass0(gp0, K, 2 * NV, probes_ok ? NV * PS : 0, scratch, tot, ptot);
       flip ^= 1;
     }
@@ -1446,7 +1447,7 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
       const GridPart gp = grid_part(part, flip);
       if (m32) cta_rows_f32<K>(fv, m32, redf, gp);
       if (m64) cta_rows_f64<K>(dv, K, m64, red, gp);
-      grid_sync(gs, target);
+      grid_sync(gs);
       grid_totals(gp, K, K, m32, tot, totf);
       flip ^= 1;
       if (t == 0) {

@@ -196,8 +196,6 @@ struct ConeTable {
   KTimer* timers = nullptr;  // profiling slots (NULL: off)
 };
 
-__global__ void k_zero_u32(unsigned int* p) { *p = 0u; }
-
 // b[i] = d[i]^2, bi[i] = 1 / d[i]^2 for i < n.
 __global__ void k_square_scales(const double* __restrict__ d, int64_t n, double* __restrict__ b,
                                 double* __restrict__ bi) {
@@ -232,7 +230,6 @@ static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d,
   if (t.nsoc[2] > 0)
     k_cone_soc<B, 512, 16><<<dim3((unsigned)t.nsoc[2], nvec), 512, 0, st>>>(v0, v1, t.soc_s[2], t.soc_d[2], d, inv, g0, g1, tsc);
   if (t.nbig > 0) {
-    k_zero_u32<<<1, 1, 0, st>>>(t.gsync.count);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)t.big_grid);
     cfg.blockDim = dim3(512);
@@ -321,7 +318,7 @@ struct Solver : SolverBase {
   Ctl* ctl = nullptr;
   Ctl* hctl = nullptr;
   KTimer* timers = nullptr;             // TM_NUM slots (profile option)
-  unsigned int* gsync_count = nullptr;  // grid barrier of k_cone_soc_grid
+  unsigned long long* gsync_count = nullptr;  // grid barrier of k_cone_soc_grid
   int* gsync_err = nullptr;             // set if a bounded barrier wait gave up
   double* gpart = nullptr;
   int big_grid = 0;
@@ -330,6 +327,7 @@ struct Solver : SolverBase {
   int64_t trace_rows = 0;
   int use_cond = 1;  // 0 in eager mode (kernels launched from the host, no graphs)
   int64_t nk_a = 0, nk_b = 0, nk_top = 0;  // kernel nodes: attempt body, probe body, top level
+  int64_t eager_a = 0, eager_b = 0;        // attempt / probe bodies run by the eager loop
   int64_t graph_launches = 0;
   long long bodies_a0 = 0, bodies_b0 = 0;  // loop-body counters at the start of the call
 
@@ -532,8 +530,12 @@ struct Solver : SolverBase {
     planG = build_plan(hrp, ar, st, small_g);
     planGT = build_plan(hrpT, ar, st, small_g);
     alloc_state();
-    if (opt.eager) use_cond = 0;
-    else capture();
+    if (opt.eager) {
+      use_cond = 0;
+      count_eager();
+    } else {
+      capture();
+    }
   }
 
   // Per-element kinds and cone tables from an ordered cone list starting at off.
@@ -621,10 +623,10 @@ struct Solver : SolverBase {
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<double, 2>, 512, 0));
         occ = std::max(1, std::min(occ, o));
         big_grid = std::min(sms * occ, kMaxGridParts);
-        gsync_count = ar.alloc<unsigned int>(1);
+        gsync_count = ar.alloc<unsigned long long>(1);
         gsync_err = ar.alloc<int>(1);
         gpart = ar.alloc<double>(2 * kSgHalf * (int64_t)big_grid);
-        CK(cudaMemsetAsync(gsync_count, 0, sizeof(unsigned int), st));
+        CK(cudaMemsetAsync(gsync_count, 0, sizeof(unsigned long long), st));
         CK(cudaMemsetAsync(gsync_err, 0, sizeof(int), st));
       }
     }
@@ -769,8 +771,11 @@ struct Solver : SolverBase {
     pr->gt_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(n + 1) + vb * (double)(n + m);
     pr->nnz_flops = 2.0 * (double)nnz;
     pr->graph_launches = graph_launches;
-    pr->kernel_launches = graph_launches * nk_top + (hctl->bodies_a - bodies_a0) * nk_a +
-                          (hctl->bodies_b - bodies_b0) * nk_b;
+    if (use_cond)
+      pr->kernel_launches = graph_launches * nk_top + (hctl->bodies_a - bodies_a0) * nk_a +
+                            (hctl->bodies_b - bodies_b0) * nk_b;
+    else
+      pr->kernel_launches = graph_launches * nk_top + eager_a * nk_a + eager_b * nk_b;
     if (!timers) return;
     KTimer z[TM_NUM];
     CK(cudaMemcpyAsync(z, timers, sizeof(z), cudaMemcpyDeviceToHost, st));
@@ -884,6 +889,29 @@ struct Solver : SolverBase {
       if (t == cudaGraphNodeTypeKernel) ++k;
     }
     return k;
+  }
+
+  // Kernel counts of the eager mode's launch sequences (captured, never run).
+  void count_eager() {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(st2, cudaStreamCaptureModeRelaxed));
+    rec_attempt(st2, 0);
+    CK(cudaStreamEndCapture(st2, &g));
+    nk_a = kernel_nodes(g);
+    CK(cudaGraphDestroy(g));
+    CK(cudaStreamBeginCapture(st2, cudaStreamCaptureModeRelaxed));
+    rec_probe(st2, 0);
+    CK(cudaStreamEndCapture(st2, &g));
+    nk_b = kernel_nodes(g);
+    CK(cudaGraphDestroy(g));
+    CK(cudaStreamBeginCapture(st2, cudaStreamCaptureModeRelaxed));
+    k_period_begin<<<1, 1, 0, st2>>>(ctl, 0, 0);
+    rec_check_stats(st2);
+    k_bisect_init<<<1, 1, 0, st2>>>(ctl, 0, 0);
+    rec_check_end(st2);
+    CK(cudaStreamEndCapture(st2, &g));
+    nk_top = kernel_nodes(g);
+    CK(cudaGraphDestroy(g));
   }
 
   void capture() {
@@ -1003,12 +1031,17 @@ struct Solver : SolverBase {
 
   void run_period_eager() {
     k_period_begin<<<1, 1, 0, st>>>(ctl, 0, 0);
-    for (int guard = 0; guard < 1 << 20 && read_flag(&ctl->g_attempt); ++guard) rec_attempt(st, 0);
+    for (int guard = 0; guard < 1 << 20 && read_flag(&ctl->g_attempt); ++guard) {
+      rec_attempt(st, 0);
+      ++eager_a;
+    }
     rec_check_stats(st);
     k_bisect_init<<<1, 1, 0, st>>>(ctl, 0, 0);
     for (int guard = 0; guard < 1024 && (read_flag(&ctl->bs[0].active) || read_flag(&ctl->bs[1].active));
-         ++guard)
+         ++guard) {
       rec_probe(st, 0);
+      ++eager_b;
+    }
     rec_check_end(st);
     CK(cudaGetLastError());
   }
@@ -1018,6 +1051,7 @@ struct Solver : SolverBase {
     int status = kRunning;
     reset_timers();
     graph_launches = 0;
+    eager_a = eager_b = 0;
     bodies_a0 = hctl->bodies_a;
     bodies_b0 = hctl->bodies_b;
     while (true) {
