@@ -252,6 +252,38 @@ void pdcs_free(pdcs_handle* handle);
 /* Message for the calling thread's most recent failure. */
 const char* pdcs_last_error(void);
 
+/* y = G x for a CSR matrix held in device memory, without allocating.  The
+ * paper has no counterpart: this is a service for callers that must not
+ * allocate device memory when they call (for example while a caching
+ * allocator owns the device's whole memory budget, or on a path that cannot
+ * afford cudaMalloc's implicit device synchronisation).
+ *   m, n: rows and columns of G (m = 0: nothing to do).
+ *   row_ptr int64 [m+1], col_idx int32 [nnz] (entries in [0, n)),
+ *   val float64 [nnz], x float64 [n], y float64 [m] (written): all device
+ *   memory of the current device; host pointers are rejected.
+ *   cuda_stream: the stream the work is ordered on (NULL: legacy default).
+ * Scratch: one fixed device array of about 0.8 MB inside the library, sized
+ * for at most 4096 rows with more than 4096 nonzeros and at most 65536
+ * chunks of 4096 nonzeros among them; a matrix beyond either limit is
+ * rejected with PDCS_ERR_INVALID before anything is computed.  Rows of up to
+ * 4096 nonzeros have no limit.
+ * The call synchronises cuda_stream once (to read the size check) and then
+ * enqueues the product; y is ready when the stream reaches it.  It allocates
+ * no device memory and, when it succeeds, no host memory either; a rejected
+ * call stores its message for pdcs_last_error.
+ * The first call on a device looks up the scratch's device address with that
+ * device current and caches it: make that first call before any stream
+ * capture.  The scratch's tickets must be zero when a call starts: they are
+ * zero when the library is loaded and every completed call leaves them zero
+ * (a call cut short by a device error does not).  All calls on one device
+ * share the scratch, so calls that overlap in time race: serialise them.
+ * Results are deterministic (fixed summation order) but round differently
+ * from the solver's own product.
+ * Returns PDCS_OK, PDCS_ERR_INVALID (sizes, NULL or host pointers, scratch
+ * limits) or PDCS_ERR_CUDA. */
+int pdcs_spmv_noalloc(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                      const double* val, const double* x, double* y, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,7 +74,8 @@ KERNEL_CLASSES = ("spmv_g", "spmv_gt", "spmv_check", "soc_grid", "soc_cta", "exp
 
 EXPORTS = ("pdcs_default_options", "pdcs_setup", "pdcs_solve", "pdcs_resume", "pdcs_get_state",
            "pdcs_set_state", "pdcs_get_iterate", "pdcs_get_trace", "pdcs_get_profile",
-           "pdcs_get_kernel_times", "pdcs_get_sizes", "pdcs_free", "pdcs_last_error")
+           "pdcs_get_kernel_times", "pdcs_get_sizes", "pdcs_free", "pdcs_last_error",
+           "pdcs_spmv_noalloc")
 
 _LIB = None
 
@@ -121,6 +122,8 @@ def lib():
     L.pdcs_free.restype = None
     L.pdcs_last_error.argtypes = []
     L.pdcs_last_error.restype = ctypes.c_char_p
+    L.pdcs_spmv_noalloc.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp]
+    L.pdcs_spmv_noalloc.restype = ctypes.c_int
     _LIB = L
     return L
 
@@ -308,6 +311,19 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def spmv_noalloc(row_ptr, col_idx, val, x, y, n=None, stream=None):
+    """y = G x through pdcs_spmv_noalloc (no allocation in the call).  All
+    arrays are CUDA tensors on the current device (int64, int32, float64,
+    float64, float64); stream: a torch.cuda.Stream (default: the current one)."""
+    import torch
+    m = row_ptr.numel() - 1
+    n = x.numel() if n is None else int(n)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().pdcs_spmv_noalloc(int(m), n, _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x),
+                                   _ptr(y), ctypes.c_void_p(st.cuda_stream)))
+    return y
 
 
 def solve(problem, x0=None, y0=None, **options):

@@ -1,0 +1,235 @@
+// Allocation-free sparse product y = G x (include/pdcs.h: pdcs_spmv_noalloc).
+//
+// The paper has no counterpart: this is a service entry point for callers that
+// must not allocate device memory at the time of the call, for example code
+// running while a caching allocator owns the device's whole memory budget, or
+// a latency-critical path where cudaMalloc's implicit device synchronisation
+// cannot be afforded.  It is a variant of the solver's k_spmv: rows of up to
+// kNaChunk nonzeros are summed by one warp each; longer rows are split into
+// kNaChunk-nonzero chunks whose partial sums are combined, in chunk order, by
+// the warp that finishes a row's last chunk (the same ticket scheme as k_spmv).
+// Where k_spmv keeps its task plan, chunk partials and tickets in memory the
+// solver handle allocated, this variant keeps them in one file-scope device
+// array of fixed size (g_na_scratch, below) and builds the chunk list on the
+// device, so a call allocates nothing.
+//
+// Scratch facts (documented in the header as well):
+//  * the tickets must be zero when a call starts.  Static device memory is
+//    zero when the library is loaded, and every call that completes leaves the
+//    tickets zero again; a call cut short by a device error leaves them
+//    undefined, and later results are then wrong;
+//  * all calls on one device share the scratch, so calls that overlap in time
+//    (two streams, or two host threads, without ordering between them) race
+//    and give wrong results: serialise them;
+//  * the first call on a device looks up the scratch's device address
+//    (cudaGetSymbolAddress, with that device current) and caches it; that
+//    one-time set-up should come before any stream capture.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+
+#include "../../include/pdcs.h"
+#include "common.cuh"
+
+namespace pdcs {
+extern thread_local std::string g_last_error;  // defined with the rest of the ABI
+}
+
+namespace {
+
+using pdcs::warp_sum;
+
+constexpr int64_t kNaChunk = 4096;       // nonzeros per chunk; longer rows are split
+constexpr int kNaMaxLongRows = 4096;     // rows longer than kNaChunk, per call
+constexpr int kNaMaxChunks = 65536;      // chunks of those rows, per call
+constexpr int kNaMaxDevices = 64;
+constexpr int kNaScanThreads = 1024;
+
+struct NaStatus {
+  long long long_rows;  // rows longer than kNaChunk
+  long long chunks;     // their chunks
+  int overflow;         // 1: more than the scratch holds (nothing computed)
+  int pad;
+};
+
+// Everything a call needs beyond the caller's arrays (about 0.8 MB).
+struct NaScratch {
+  double partial[kNaMaxChunks];          // chunk partial sums
+  int chunk_slot[kNaMaxChunks];          // long-row slot of each chunk
+  int first[kNaMaxLongRows + 1];         // first chunk of each slot (prefix sums)
+  long long row[kNaMaxLongRows];         // row index of each slot
+  unsigned int ticket[kNaMaxLongRows];   // chunks finished per slot; zero between calls
+  NaStatus status;
+};
+
+static __device__ __align__(256) NaScratch g_na_scratch;
+
+// Device address of g_na_scratch per device (looked up once per device).
+NaScratch* g_na_addr[kNaMaxDevices] = {};
+std::mutex g_na_mutex;
+
+// One CTA: list the rows longer than kNaChunk in row order, with their chunk
+// ranges.  Thread t owns a contiguous range of rows; a block-wide exclusive
+// scan of the per-thread counts gives each thread its output offsets.
+__global__ void __launch_bounds__(kNaScanThreads) k_na_scan(const int64_t* __restrict__ rp,
+                                                            int64_t m, NaScratch* s) {
+  __shared__ long long sh_rows[kNaScanThreads], sh_chunks[kNaScanThreads];
+  const int t = threadIdx.x;
+  const int64_t per = (m + kNaScanThreads - 1) / kNaScanThreads;
+  const int64_t r0 = min(m, (int64_t)t * per), r1 = min(m, r0 + per);
+  long long nr = 0, nc = 0;
+  for (int64_t r = r0; r < r1; ++r) {
+    const int64_t len = rp[r + 1] - rp[r];
+    if (len > kNaChunk) {
+      ++nr;
+      nc += (len + kNaChunk - 1) / kNaChunk;
+    }
+  }
+  sh_rows[t] = nr;
+  sh_chunks[t] = nc;
+  __syncthreads();
+  // inclusive Hillis-Steele scan (integers: order does not matter)
+  for (int off = 1; off < kNaScanThreads; off <<= 1) {
+    const long long a = t >= off ? sh_rows[t - off] : 0, b = t >= off ? sh_chunks[t - off] : 0;
+    __syncthreads();
+    sh_rows[t] += a;
+    sh_chunks[t] += b;
+    __syncthreads();
+  }
+  const long long tot_rows = sh_rows[kNaScanThreads - 1], tot_chunks = sh_chunks[kNaScanThreads - 1];
+  const bool overflow = tot_rows > kNaMaxLongRows || tot_chunks > kNaMaxChunks;
+  if (t == 0) {
+    s->status.long_rows = tot_rows;
+    s->status.chunks = tot_chunks;
+    s->status.overflow = overflow ? 1 : 0;
+    if (!overflow) s->first[tot_rows] = (int)tot_chunks;
+  }
+  if (overflow) return;
+  long long slot = sh_rows[t] - nr, chunk = sh_chunks[t] - nc;
+  for (int64_t r = r0; r < r1; ++r) {
+    const int64_t len = rp[r + 1] - rp[r];
+    if (len <= kNaChunk) continue;
+    const long long k = (len + kNaChunk - 1) / kNaChunk;
+    s->row[slot] = r;
+    s->first[slot] = (int)chunk;
+    for (long long c = 0; c < k; ++c) s->chunk_slot[chunk + c] = (int)slot;
+    ++slot;
+    chunk += k;
+  }
+}
+
+// y = G x: warps take the short rows (one row each), then the chunks of the
+// long rows; the warp finishing a long row's last chunk adds its partials in
+// chunk order (lane-strided, then a fixed butterfly) and resets the ticket.
+__global__ void __launch_bounds__(256) k_na_spmv(const int64_t* __restrict__ rp,
+                                                 const int32_t* __restrict__ ci,
+                                                 const double* __restrict__ val,
+                                                 const double* __restrict__ x, double* __restrict__ y,
+                                                 int64_t m, NaScratch* s) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = wid; r < m; r += nw) {
+    const int64_t a = rp[r], b = rp[r + 1];
+    if (b - a > kNaChunk) continue;  // done chunk by chunk below
+    double acc = 0.0;
+    for (int64_t e = a + lane; e < b; e += 32) acc = fma(val[e], x[ci[e]], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[r] = acc;
+  }
+  const int64_t nch = s->status.chunks;
+  for (int64_t c = wid; c < nch; c += nw) {
+    const int slot = s->chunk_slot[c];
+    const int64_t r = s->row[slot];
+    const int f0 = s->first[slot], f1 = s->first[slot + 1];
+    const int64_t a = rp[r] + (c - f0) * kNaChunk, b = min(rp[r + 1], a + kNaChunk);
+    double acc = 0.0;
+    for (int64_t e = a + lane; e < b; e += 32) acc = fma(val[e], x[ci[e]], acc);
+    acc = warp_sum(acc);
+    unsigned int done = 0;
+    if (lane == 0) {
+      s->partial[c] = acc;
+      __threadfence();
+      done = atomicAdd(&s->ticket[slot], 1u) + 1u;
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done == (unsigned int)(f1 - f0)) {
+      __threadfence();
+      double tot = 0.0;
+      for (int j = f0 + lane; j < f1; j += 32) tot += __ldcg(s->partial + j);
+      tot = warp_sum(tot);
+      if (lane == 0) {
+        y[r] = tot;
+        s->ticket[slot] = 0u;
+      }
+    }
+  }
+}
+
+int na_fail(int code, const char* msg) {
+  pdcs::g_last_error = msg;
+  return code;
+}
+
+// Device memory (or managed) on the current device?
+bool na_device_ptr(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
+}  // namespace
+
+extern "C" int pdcs_spmv_noalloc(int64_t m, int64_t n, const int64_t* row_ptr,
+                                 const int32_t* col_idx, const double* val, const double* x,
+                                 double* y, void* cuda_stream) {
+  if (m < 0 || n < 0) return na_fail(PDCS_ERR_INVALID, "pdcs_spmv_noalloc: m and n must be >= 0");
+  if (m == 0) return PDCS_OK;
+  if (!row_ptr || !y || (n > 0 && (!col_idx || !val || !x)))
+    return na_fail(PDCS_ERR_INVALID, "pdcs_spmv_noalloc: NULL array");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
+    return na_fail(PDCS_ERR_CUDA, "pdcs_spmv_noalloc: no usable current device");
+  if (!na_device_ptr(row_ptr, dev) || !na_device_ptr(y, dev) ||
+      (n > 0 && (!na_device_ptr(col_idx, dev) || !na_device_ptr(val, dev) ||
+                 !na_device_ptr(x, dev))))
+    return na_fail(PDCS_ERR_INVALID,
+                   "pdcs_spmv_noalloc: every array must be device memory of the current device");
+  NaScratch* s = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_addr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+      if (e != cudaSuccess) return na_fail(PDCS_ERR_CUDA, cudaGetErrorString(e));
+      g_na_addr[dev] = static_cast<NaScratch*>(p);
+    }
+    s = g_na_addr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  k_na_scan<<<1, kNaScanThreads, 0, st>>>(row_ptr, m, s);
+  NaStatus hs;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, &s->status, sizeof(hs), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return na_fail(PDCS_ERR_CUDA, cudaGetErrorString(e));
+  if (hs.overflow)
+    return na_fail(PDCS_ERR_INVALID,
+                   "pdcs_spmv_noalloc: more than 4096 rows with over 4096 nonzeros, or more than "
+                   "65536 chunks of 4096 nonzeros in them: beyond the fixed scratch");
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    sms = 148;
+  const int64_t warps = m + hs.chunks;
+  const int64_t blocks = std::min<int64_t>((warps + 7) / 8, (int64_t)sms * 16);
+  k_na_spmv<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(row_ptr, col_idx, val, x, y,
+                                                                    m, s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return na_fail(PDCS_ERR_CUDA, cudaGetErrorString(e));
+  return PDCS_OK;
+}
