@@ -252,6 +252,54 @@ void pdcs_free(pdcs_handle* handle);
 /* Message for the calling thread's most recent failure. */
 const char* pdcs_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Warm-start network (the paper has no counterpart: a learned starting point
+ * for parameterised problem families).  A fully connected ReLU network
+ * in_dim -> hidden (n_hidden layers) -> out_dim trained with mean squared
+ * error and Adam; GEMMs on the tensor cores in BF16 with FP32 accumulation,
+ * master weights and Adam moments in FP32.  Weights start Glorot-uniform
+ * (SplitMix64 stream from seed), biases at zero.
+ * Data arguments are row-major FP32 (batch x in_dim inputs, batch x out_dim
+ * targets / outputs), host or device memory; the calls return when their
+ * outputs are in place.  Errors: PDCS_ERR_INVALID (arguments),
+ * PDCS_ERR_NOMEM / PDCS_ERR_CUDA, PDCS_ERR_TIMEOUT (a GEMM wait gave up). */
+typedef struct pdcs_mlp pdcs_mlp;
+
+typedef struct {
+  int64_t in_dim;     /* inputs per sample */
+  int64_t hidden;     /* width of every hidden layer */
+  int32_t n_hidden;   /* hidden layers (>= 1) */
+  int32_t pad;
+  int64_t out_dim;    /* outputs per sample */
+  int64_t max_batch;  /* largest batch of any call */
+  double lr, beta1, beta2, eps;  /* Adam */
+  uint64_t seed;
+} pdcs_mlp_config;
+
+void pdcs_mlp_default_config(pdcs_mlp_config* cfg); /* hidden 512 x 3, batch 256, Adam 1e-3 */
+int pdcs_mlp_create(pdcs_mlp** out, const pdcs_mlp_config* cfg, void* cuda_stream);
+/* One Adam step on the batch's mean squared error; *loss (may be NULL)
+ * receives the loss before the step. */
+int pdcs_mlp_train_step(pdcs_mlp* net, const float* X, const float* T, int64_t batch, double* loss);
+/* Gradients of the batch loss for one layer (dW: d_out x d_in, db: d_out;
+ * either may be NULL), without updating anything. */
+int pdcs_mlp_gradients(pdcs_mlp* net, const float* X, const float* T, int64_t batch, int32_t layer,
+                       float* dW, float* db, double* loss);
+int pdcs_mlp_predict(pdcs_mlp* net, const float* X, int64_t batch, float* Y);
+/* Master (FP32) weights of layer 0 .. n_hidden: W is d_out x d_in row-major.
+ * set_layer also resets the Adam moments and step count. */
+int pdcs_mlp_get_layer(pdcs_mlp* net, int32_t layer, float* W, float* b);
+int pdcs_mlp_set_layer(pdcs_mlp* net, int32_t layer, const float* W, const float* b);
+void pdcs_mlp_free(pdcs_mlp* net); /* NULL-safe */
+
+/* KKT errors of a given point (original variables; x: n, y: m, host or
+ * device; NULL = zeros) under the termination definitions of Sec. 3.2.3:
+ * res receives pobj, dobj and the err_* fields as pdcs_solve reports them,
+ * exit_code 0 if the point meets the termination test and -1 otherwise,
+ * iters = attempts = restarts = 0.  Replaces the handle's iterate, like a
+ * solve would. */
+int pdcs_kkt(pdcs_handle* handle, const double* x, const double* y, pdcs_result* res);
+
 /* y = G x for a CSR matrix held in device memory, without allocating.  The
  * paper has no counterpart: this is a service for callers that must not
  * allocate device memory when they call (for example while a caching

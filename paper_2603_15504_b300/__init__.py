@@ -48,6 +48,14 @@ class PdcsResult(ctypes.Structure):
                 ("attempts", ctypes.c_int64), ("restarts", ctypes.c_int64)]
 
 
+class PdcsMlpConfig(ctypes.Structure):
+    _fields_ = [("in_dim", ctypes.c_int64), ("hidden", ctypes.c_int64),
+                ("n_hidden", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("out_dim", ctypes.c_int64), ("max_batch", ctypes.c_int64),
+                ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class PdcsState(ctypes.Structure):
     _fields_ = [("iter", ctypes.c_int64), ("kbar", ctypes.c_int64), ("k", ctypes.c_int64),
                 ("period", ctypes.c_int64), ("restarts", ctypes.c_int64),
@@ -75,7 +83,9 @@ KERNEL_CLASSES = ("spmv_g", "spmv_gt", "spmv_check", "soc_grid", "soc_cta", "exp
 EXPORTS = ("pdcs_default_options", "pdcs_setup", "pdcs_solve", "pdcs_resume", "pdcs_get_state",
            "pdcs_set_state", "pdcs_get_iterate", "pdcs_get_trace", "pdcs_get_profile",
            "pdcs_get_kernel_times", "pdcs_get_sizes", "pdcs_free", "pdcs_last_error",
-           "pdcs_spmv_noalloc")
+           "pdcs_mlp_default_config", "pdcs_mlp_create", "pdcs_mlp_train_step",
+           "pdcs_mlp_gradients", "pdcs_mlp_predict", "pdcs_mlp_get_layer", "pdcs_mlp_set_layer",
+           "pdcs_mlp_free", "pdcs_kkt", "pdcs_spmv_noalloc")
 
 _LIB = None
 
@@ -124,6 +134,24 @@ def lib():
     L.pdcs_last_error.restype = ctypes.c_char_p
     L.pdcs_spmv_noalloc.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp]
     L.pdcs_spmv_noalloc.restype = ctypes.c_int
+    L.pdcs_kkt.argtypes = [vp, vp, vp, ctypes.POINTER(PdcsResult)]
+    L.pdcs_kkt.restype = ctypes.c_int
+    L.pdcs_mlp_default_config.argtypes = [ctypes.POINTER(PdcsMlpConfig)]
+    L.pdcs_mlp_default_config.restype = None
+    L.pdcs_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PdcsMlpConfig), vp]
+    L.pdcs_mlp_create.restype = ctypes.c_int
+    L.pdcs_mlp_train_step.argtypes = [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_double)]
+    L.pdcs_mlp_train_step.restype = ctypes.c_int
+    L.pdcs_mlp_gradients.argtypes = [vp, vp, vp, i64, i32, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    L.pdcs_mlp_gradients.restype = ctypes.c_int
+    L.pdcs_mlp_predict.argtypes = [vp, vp, i64, vp]
+    L.pdcs_mlp_predict.restype = ctypes.c_int
+    L.pdcs_mlp_get_layer.argtypes = [vp, i32, vp, vp]
+    L.pdcs_mlp_get_layer.restype = ctypes.c_int
+    L.pdcs_mlp_set_layer.argtypes = [vp, i32, vp, vp]
+    L.pdcs_mlp_set_layer.restype = ctypes.c_int
+    L.pdcs_mlp_free.argtypes = [vp]
+    L.pdcs_mlp_free.restype = None
     _LIB = L
     return L
 
@@ -220,6 +248,19 @@ class Solver:
     def _result(self, res, x, y, s):
         d = {k: getattr(res, k) for k, _ in PdcsResult._fields_ if k != "pad"}
         d.update(x=x, y=y, s=s, status=EXIT_NAMES.get(res.exit_code, "?"))
+        return d
+
+    def kkt(self, x=None, y=None):
+        """KKT errors of a point in the original variables (pdcs_kkt); replaces
+        the handle's iterate.  Returns the pdcs_result fields."""
+        res = PdcsResult()
+        if x is not None and not hasattr(x, "data_ptr"):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+        if y is not None and not hasattr(y, "data_ptr"):
+            y = np.ascontiguousarray(y, dtype=np.float64)
+        _check(lib().pdcs_kkt(self._h, _ptr(x), _ptr(y), ctypes.byref(res)))
+        d = {k: getattr(res, k) for k, _ in PdcsResult._fields_ if k != "pad"}
+        d["max_rel"] = max(res.err_rel_p, res.err_rel_d, res.err_rel_gap)
         return d
 
     def solve(self, x0=None, y0=None, out=None):
@@ -324,6 +365,79 @@ def spmv_noalloc(row_ptr, col_idx, val, x, y, n=None, stream=None):
     _check(lib().pdcs_spmv_noalloc(int(m), n, _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x),
                                    _ptr(y), ctypes.c_void_p(st.cuda_stream)))
     return y
+
+
+class Mlp:
+    """The warm-start network (pdcs_mlp_*).  Arrays are FP32 NumPy arrays or
+    CUDA tensors, row-major (batch x features)."""
+
+    def __init__(self, in_dim, out_dim, hidden=512, n_hidden=3, max_batch=256, lr=1e-3,
+                 beta1=0.9, beta2=0.999, eps=1e-8, seed=20260105, stream=None):
+        cfg = PdcsMlpConfig()
+        lib().pdcs_mlp_default_config(ctypes.byref(cfg))
+        cfg.in_dim, cfg.out_dim, cfg.hidden, cfg.n_hidden = in_dim, out_dim, hidden, n_hidden
+        cfg.max_batch, cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, cfg.seed = (
+            max_batch, lr, beta1, beta2, eps, seed)
+        self.cfg = cfg
+        self.dims = [in_dim] + [hidden] * n_hidden + [out_dim]
+        self._h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        _check(lib().pdcs_mlp_create(ctypes.byref(self._h), ctypes.byref(cfg), st))
+
+    @staticmethod
+    def _f32(a):
+        if a is None or hasattr(a, "data_ptr"):
+            return a
+        return np.ascontiguousarray(a, dtype=np.float32)
+
+    def train_step(self, X, T):
+        X, T = self._f32(X), self._f32(T)
+        loss = ctypes.c_double()
+        _check(lib().pdcs_mlp_train_step(self._h, _ptr(X), _ptr(T), int(X.shape[0]),
+                                         ctypes.byref(loss)))
+        return loss.value
+
+    def gradients(self, X, T, layer):
+        X, T = self._f32(X), self._f32(T)
+        dW = np.empty((self.dims[layer + 1], self.dims[layer]), np.float32)
+        db = np.empty(self.dims[layer + 1], np.float32)
+        loss = ctypes.c_double()
+        _check(lib().pdcs_mlp_gradients(self._h, _ptr(X), _ptr(T), int(X.shape[0]), int(layer),
+                                        _ptr(dW), _ptr(db), ctypes.byref(loss)))
+        return loss.value, dW, db
+
+    def predict(self, X, out=None):
+        X = self._f32(X)
+        Y = out if out is not None else np.empty((X.shape[0], self.dims[-1]), np.float32)
+        _check(lib().pdcs_mlp_predict(self._h, _ptr(X), int(X.shape[0]), _ptr(Y)))
+        return Y
+
+    def get_layer(self, layer):
+        W = np.empty((self.dims[layer + 1], self.dims[layer]), np.float32)
+        b = np.empty(self.dims[layer + 1], np.float32)
+        _check(lib().pdcs_mlp_get_layer(self._h, int(layer), _ptr(W), _ptr(b)))
+        return W, b
+
+    def set_layer(self, layer, W, b):
+        W, b = self._f32(W), self._f32(b)
+        _check(lib().pdcs_mlp_set_layer(self._h, int(layer), _ptr(W), _ptr(b)))
+
+    def close(self):
+        if self._h:
+            lib().pdcs_mlp_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def solve(problem, x0=None, y0=None, **options):

@@ -267,6 +267,7 @@ struct SolverBase {
   virtual void solve(const double* x0, const double* y0, double* x, double* y, double* s,
                      pdcs_result* res) = 0;
   virtual void resume(int64_t max_iter, double* x, double* y, double* s, pdcs_result* res) = 0;
+  virtual void evaluate(const double* x, const double* y, pdcs_result* res) = 0;
   virtual void get_state(pdcs_state* st, double* x, double* y, double* x0, double* y0,
                          double* xs, double* ys) = 0;
   virtual void set_state(const pdcs_state* st, const double* x, const double* y,
@@ -1001,6 +1002,25 @@ struct Solver : SolverBase {
     run(xo, yo, so, res, t0);
   }
 
+  // KKT errors of a given point: load it as the iterate, refresh the products
+  // and take the final statistics (Sec. 3.2.3) without any iteration.
+  void evaluate(const double* x0u, const double* y0u, pdcs_result* res) override {
+    const auto t0 = std::chrono::steady_clock::now();
+    order_after_user();
+    init_ctl();
+    upload_ctl();
+    start_point(x0u, y0u);
+    finish(0, nullptr, nullptr, nullptr, res, t0);
+    if (res) {
+      const PointStats& s3 = hctl->st[3];
+      bool ok = std::max(s3.inf_rel_p, std::max(s3.inf_rel_d, s3.inf_rel_gap)) <= opt.rel_tol;
+      if (opt.require_abs)
+        ok = ok && std::max(s3.inf_abs_p, std::max(s3.inf_abs_d, s3.gap)) <= opt.abs_tol;
+      res->exit_code = ok ? 0 : -1;
+      res->iters = res->attempts = res->restarts = 0;
+    }
+  }
+
   void resume(int64_t max_iter, double* xo, double* yo, double* so, pdcs_result* res) override {
     const auto t0 = std::chrono::steady_clock::now();
     order_after_user();
@@ -1326,6 +1346,10 @@ int pdcs_setup(pdcs_handle** out, int64_t m, int64_t n, const int64_t* row_ptr,
 int pdcs_solve(pdcs_handle* hd, const double* x0, const double* y0, double* x, double* y,
                double* s, pdcs_result* res) {
   PDCS_API_BODY(hd->solver->solve(x0, y0, x, y, s, res))
+}
+
+int pdcs_kkt(pdcs_handle* hd, const double* x, const double* y, pdcs_result* res) {
+  PDCS_API_BODY(hd->solver->evaluate(x, y, res))
 }
 
 int pdcs_resume(pdcs_handle* hd, int64_t max_iter, double* x, double* y, double* s,
