@@ -1,0 +1,43 @@
+"""Learned warm start on a small parameterised portfolio family: solutions
+from the plain solver train the network; held-out instances are solved from
+its prediction unless pdcs_kkt rates the prediction worse than the cold start.
+Checks: every solve reaches 1e-6, the start rule follows the two KKT errors,
+the fallback keeps the iteration count within 10 % of the cold start's on
+average, and the measured gain is printed."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def test_warm_start_pipeline_on_a_small_family():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_15504_b300 as P
+    from paper_2603_15504_b300 import warmstart as W
+
+    fam = workloads.portfolio_family(n=300, k=15, n_limits=3, seed=77)
+    make = lambda split, i: workloads.portfolio_family_instance(fam, i, split_seed=split)  # noqa: E731
+    params, sols, res = W.collect([(lambda i=i: make(0, i)) for i in range(96)], workers=8,
+                                  rel_tol=1e-6, time_limit=60.0)
+    assert all(r["exit_code"] == 0 for r in res)
+    ws = W.WarmStart(params, sols, n=301, hidden=256, n_hidden=3, batch=64, lr=1e-3)
+    losses = ws.fit(400)
+    assert np.mean(losses[-20:]) < 0.5 * losses[0]
+    cold, warm, used = [], [], 0
+    for i in range(8):
+        prob, p = make(1, i)
+        with P.Solver(prob, rel_tol=1e-6, time_limit=60.0) as s:
+            c = s.solve()
+        w = ws.solve(prob, p, rel_tol=1e-6, time_limit=60.0)
+        assert c["exit_code"] == 0 and w["exit_code"] == 0
+        assert w["warm"] == (w["kkt_pred"] <= w["kkt_cold"])
+        cold.append(c["iters"])
+        warm.append(w["iters"])
+        used += int(w["warm"])
+    ratio = np.mean(warm) / np.mean(cold)
+    print("warm / cold iterations: %.3f (prediction used %d of %d)" % (ratio, used, len(warm)))
+    assert ratio <= 1.10
