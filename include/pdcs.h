@@ -246,11 +246,47 @@ int pdcs_get_kernel_times(pdcs_handle* handle, double* seconds, int64_t* launche
 /* Sizes after set-up (m, n of the reformulated problem, nnz of G). */
 int pdcs_get_sizes(pdcs_handle* handle, int64_t* m, int64_t* n, int64_t* nnz);
 
-/* Release the handle and its device memory.  NULL-safe. */
+/* Release a handle (single problem or batch) and its device memory.  NULL-safe. */
 void pdcs_free(pdcs_handle* handle);
 
 /* Message for the calling thread's most recent failure. */
 const char* pdcs_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Batched solves: many independent problems in one persistent kernel launch
+ * (one thread block per problem at a time, largest first; every problem has
+ * its own step sizes, primal weight, restarts and termination).  Each problem
+ * is described as pdcs_setup's arguments; arrays may be host or device memory
+ * and are copied.  Limits: SOC blocks of at most 4096 elements
+ * (PDCS_ERR_UNSUPPORTED beyond), fewer than 2^31 columns in all.  Set-up also
+ * picks the lanes per row of the sparse products for four size buckets by
+ * timing a few problems of each (autotuning).  options.time_limit applies to
+ * each problem from its start. */
+typedef struct {
+  int64_t m, n;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+  const double* h;
+  const double* c;
+  int64_t nb;
+  const double* lb;
+  const double* ub;
+  const pdcs_cone* row_cones;
+  int64_t n_row_cones;
+  const pdcs_cone* col_cones;
+  int64_t n_col_cones;
+} pdcs_instance;
+
+int pdcs_setup_batch(pdcs_handle** out, const pdcs_instance* instances, int64_t count,
+                     const pdcs_options* opt, void* cuda_stream);
+/* Solve every problem from the cold start.  x (sum of n), y and s (sum of m):
+ * the problems' outputs concatenated in input order (any may be NULL); res:
+ * count results (solve_time_s = that problem's own time on its thread
+ * block); finish_s (may be NULL): count times from the first problem's start
+ * to each problem's end. */
+int pdcs_solve_batch(pdcs_handle* handle, double* x, double* y, double* s, pdcs_result* res,
+                     double* finish_s);
 
 /* ------------------------------------------------------------------------
  * Warm-start network (the paper has no counterpart: a learned starting point

@@ -48,6 +48,15 @@ class PdcsResult(ctypes.Structure):
                 ("attempts", ctypes.c_int64), ("restarts", ctypes.c_int64)]
 
 
+class PdcsInstance(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p), ("h", ctypes.c_void_p),
+                ("c", ctypes.c_void_p), ("nb", ctypes.c_int64), ("lb", ctypes.c_void_p),
+                ("ub", ctypes.c_void_p), ("row_cones", ctypes.c_void_p),
+                ("n_row_cones", ctypes.c_int64), ("col_cones", ctypes.c_void_p),
+                ("n_col_cones", ctypes.c_int64)]
+
+
 class PdcsMlpConfig(ctypes.Structure):
     _fields_ = [("in_dim", ctypes.c_int64), ("hidden", ctypes.c_int64),
                 ("n_hidden", ctypes.c_int32), ("pad", ctypes.c_int32),
@@ -85,7 +94,8 @@ EXPORTS = ("pdcs_default_options", "pdcs_setup", "pdcs_solve", "pdcs_resume", "p
            "pdcs_get_kernel_times", "pdcs_get_sizes", "pdcs_free", "pdcs_last_error",
            "pdcs_mlp_default_config", "pdcs_mlp_create", "pdcs_mlp_train_step",
            "pdcs_mlp_gradients", "pdcs_mlp_predict", "pdcs_mlp_get_layer", "pdcs_mlp_set_layer",
-           "pdcs_mlp_free", "pdcs_kkt", "pdcs_spmv_noalloc")
+           "pdcs_mlp_free", "pdcs_kkt", "pdcs_setup_batch", "pdcs_solve_batch",
+           "pdcs_spmv_noalloc")
 
 _LIB = None
 
@@ -134,6 +144,11 @@ def lib():
     L.pdcs_last_error.restype = ctypes.c_char_p
     L.pdcs_spmv_noalloc.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp]
     L.pdcs_spmv_noalloc.restype = ctypes.c_int
+    L.pdcs_setup_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PdcsInstance), i64,
+                                   ctypes.POINTER(PdcsOptions), vp]
+    L.pdcs_setup_batch.restype = ctypes.c_int
+    L.pdcs_solve_batch.argtypes = [vp, vp, vp, vp, ctypes.POINTER(PdcsResult), vp]
+    L.pdcs_solve_batch.restype = ctypes.c_int
     L.pdcs_kkt.argtypes = [vp, vp, vp, ctypes.POINTER(PdcsResult)]
     L.pdcs_kkt.restype = ctypes.c_int
     L.pdcs_mlp_default_config.argtypes = [ctypes.POINTER(PdcsMlpConfig)]
@@ -365,6 +380,75 @@ def spmv_noalloc(row_ptr, col_idx, val, x, y, n=None, stream=None):
     _check(lib().pdcs_spmv_noalloc(int(m), n, _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x),
                                    _ptr(y), ctypes.c_void_p(st.cuda_stream)))
     return y
+
+
+class Batch:
+    """Many independent problems solved in one persistent kernel launch
+    (pdcs_setup_batch / pdcs_solve_batch).  `problems` is a list of problem
+    dicts as for Solver (host arrays)."""
+
+    def __init__(self, problems, stream=None, **options):
+        self._h = ctypes.c_void_p()
+        self.count = len(problems)
+        keep = []
+        inst = (PdcsInstance * self.count)()
+        self.sizes = []
+        for k, p in enumerate(problems):
+            def arr(key, dtype):
+                a = np.ascontiguousarray(p[key], dtype=dtype)
+                keep.append(a)
+                return a.ctypes.data
+            m, n, nb = int(p["m"]), int(p["n"]), int(p["nb"])
+            rc, cc = _cones(p["row_cones"]), _cones(p["col_cones"])
+            keep += [rc, cc]
+            inst[k] = PdcsInstance(m, n, arr("row_ptr", np.int64), arr("col_idx", np.int32),
+                                   arr("val", np.float64), arr("h", np.float64),
+                                   arr("c", np.float64), nb,
+                                   arr("lo", np.float64) if nb else None,
+                                   arr("hi", np.float64) if nb else None,
+                                   ctypes.cast(rc, ctypes.c_void_p), len(p["row_cones"]),
+                                   ctypes.cast(cc, ctypes.c_void_p), len(p["col_cones"]))
+            self.sizes.append((m, n))
+        self.options = default_options(**options)
+        st = stream if stream is not None else _current_stream()
+        _check(lib().pdcs_setup_batch(ctypes.byref(self._h), inst, self.count,
+                                      ctypes.byref(self.options), st))
+
+    def solve(self):
+        """Returns (list of per-problem result dicts with x, y, s, finish time
+        from the first start)."""
+        nt = sum(n for _, n in self.sizes)
+        mt = sum(m for m, _ in self.sizes)
+        x, y, s = np.empty(nt), np.empty(mt), np.empty(mt)
+        res = (PdcsResult * self.count)()
+        fin = np.empty(self.count)
+        _check(lib().pdcs_solve_batch(self._h, _ptr(x), _ptr(y), _ptr(s), res, _ptr(fin)))
+        out, r0, c0 = [], 0, 0
+        for k, (m, n) in enumerate(self.sizes):
+            d = {f: getattr(res[k], f) for f, _ in PdcsResult._fields_ if f != "pad"}
+            d.update(x=x[c0:c0 + n], y=y[r0:r0 + m], s=s[r0:r0 + m], finish_s=fin[k],
+                     status=EXIT_NAMES.get(res[k].exit_code, "?"))
+            out.append(d)
+            r0 += m
+            c0 += n
+        return out
+
+    def close(self):
+        if self._h:
+            lib().pdcs_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Mlp:

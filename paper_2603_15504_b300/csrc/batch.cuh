@@ -1,0 +1,392 @@
+// Batched persistent solver: many independent conic programs solved in one
+// kernel launch, one CTA per instance at a time.
+//
+// The instances are laid out as one block-diagonal problem (set up, scaled
+// and transposed by the ordinary set-up; Ruiz / Pock-Chambolle scaling,
+// transposition and the RSOC rotation act block by block, so this equals
+// setting every instance up on its own).  Each CTA of the persistent grid
+// takes the next instance from a queue (largest first) and runs Algorithm 1
+// with the restart checks of Algorithm 3 on it to the end: the same per-element
+// functions as the grid-wide engine over the instance's row and column ranges,
+// CTA-wide reductions in place of grid-wide ones, and the same thread-0
+// control functions on the instance's own control block (kept in shared
+// memory).  So every instance has its own step sizes, primal weight, restarts
+// and termination.  SOC blocks (up to 4096 elements) are projected by the CTA
+// (soc_proj_cta), exponential cones per thread.  The products use `tile`
+// lanes per row, chosen per size bucket by an autotuner on the host.
+#pragma once
+#include "iterate.cuh"
+#include "spmv.cuh"
+
+namespace pdcs {
+
+constexpr int kBatchThreads = 512;
+constexpr int kBatchSocEpt = 8;  // SOC blocks of up to 512 * 8 = 4096 elements
+constexpr int kBatchSh = kStatSums * kBatchThreads + kStatSums;
+
+struct BInst {
+  int64_t r0, m, c0, n;                      // row / column ranges in the batch problem
+  int32_t soc_r0, soc_rn, soc_c0, soc_cn;    // ranges in the row / column SOC lists
+  int32_t exp_r0, exp_rn, exp_c0, exp_cn;    // ranges in the row / column exp lists
+  int32_t tile, pad;                         // lanes per row of the products
+};
+
+template <typename T>
+struct BatchArgs {
+  Prob<T> p;  // batch-problem data, global indices
+  const int64_t *rp, *rpT;
+  const int32_t *ci, *ciT;
+  const T *vv, *vvT;
+  T *x, *y, *xh, *yh, *gx, *gty, *gxh, *gtyh, *x0, *y0, *gx0, *gty0;
+  T *xb, *yb, *gxb, *gtyb, *xc, *yc, *gxc, *gtyc;
+  double *xs, *ys;
+  double *tm[2], *tn[2], *um[2], *un[2], *px[2], *py[2];
+  const int64_t *soc_rs, *soc_cs;
+  const int32_t *soc_rd, *soc_cd;
+  const int64_t *exp_rs, *exp_cs;
+  const uint8_t *exp_risd, *exp_cisd;
+  const BInst* inst;
+  const int32_t* order;   // queue order of the instances
+  int32_t count;          // instances in the queue
+  Ctl* ctls;              // per instance: final control block
+  const Ctl* tmpl;        // options part of the control block
+  unsigned int* queue;    // next queue position (zero at launch)
+  unsigned long long* times;  // per instance: start and end (global ns)
+  double time_limit_s;    // per instance
+};
+
+#define PDCS_BLOCK_LOOP(i, lo, hi) for (int64_t i = (lo) + threadIdx.x; i < (hi); i += blockDim.x)
+
+// y[r0 + r] = sum_e v[e] x[ci[e]] for the rows r < nr, `tile` lanes per row
+// (a power of two <= 32); every group runs the same number of trips so the
+// shuffles stay converged.
+template <typename T>
+PDCS_DEV void b_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                     const T* __restrict__ vv, const T* __restrict__ x, T* __restrict__ y,
+                     int64_t r0, int64_t nr, int tile) {
+  const int gid = threadIdx.x / tile, lane = threadIdx.x % tile, ng = blockDim.x / tile;
+  const int64_t trips = (nr + ng - 1) / ng;
+  for (int64_t q = 0; q < trips; ++q) {
+    const int64_t r = gid + q * ng;
+    Acc<T> acc;
+    if (r < nr) {
+      const int64_t s = rp[r0 + r], e = rp[r0 + r + 1];
+      for (int64_t k = s + lane; k < e; k += tile) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
+    }
+    double v = acc.get();
+    for (int o = tile / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, tile);
+    if (lane == 0 && r < nr) y[r0 + r] = (T)v;
+  }
+}
+
+// SOC blocks [first, first + count) of a list, onto diag(e) K_soc (e from d, inv).
+template <typename B>
+PDCS_DEV void b_proj_soc(B* v, const int64_t* __restrict__ starts, const int32_t* __restrict__ dims,
+                         int first, int count, const double* __restrict__ d, int inv, double* sh) {
+  for (int j = first; j < first + count; ++j) {
+    const int64_t s = starts[j];
+    const int dim = dims[j];
+    double vv[kBatchSocEpt], ee[kBatchSocEpt];
+#pragma unroll
+    for (int k = 0; k < kBatchSocEpt; ++k) {
+      const int i = threadIdx.x + k * kBatchThreads;
+      vv[k] = i < dim ? (double)v[s + i] : 0.0;
+      ee[k] = i < dim ? cone_scale(d, s + i, inv) : 1.0;
+    }
+    soc_proj_cta<kBatchThreads, kBatchSocEpt>(vv, ee, dim, sh);
+#pragma unroll
+    for (int k = 0; k < kBatchSocEpt; ++k) {
+      const int i = threadIdx.x + k * kBatchThreads;
+      if (i < dim) v[s + i] = (B)vv[k];
+    }
+    __syncthreads();
+  }
+}
+
+// Exponential-cone 3-blocks [first, first + count) of a list, one per thread.
+template <typename B>
+PDCS_DEV void b_proj_exp(B* v, const int64_t* __restrict__ starts, const uint8_t* __restrict__ isd,
+                         int first, int count, const double* __restrict__ d, int inv, int dual) {
+  for (int j = threadIdx.x; j < count; j += blockDim.x) {
+    const int64_t s = starts[first + j];
+    const double in[3] = {(double)v[s], (double)v[s + 1], (double)v[s + 2]};
+    const double e[3] = {cone_scale(d, s, inv), cone_scale(d, s + 1, inv), cone_scale(d, s + 2, inv)};
+    double out[3];
+    proj_exp_family(in, e, (isd[first + j] != 0) != (dual != 0), out);
+    v[s] = (B)out[0];
+    v[s + 1] = (B)out[1];
+    v[s + 2] = (B)out[2];
+  }
+}
+
+// The cone blocks of one instance's rows / columns (the product cone's zero /
+// nonnegative / box parts are projected by the element functions).
+template <typename T, typename B>
+PDCS_DEV void b_project_rows(const BatchArgs<T>& a, const BInst& I, B* v, const double* d, int inv,
+                             int dual, double* sh) {
+  b_proj_exp(v, a.exp_rs, a.exp_risd, I.exp_r0, I.exp_rn, d, inv, dual);
+  __syncthreads();
+  b_proj_soc(v, a.soc_rs, a.soc_rd, I.soc_r0, I.soc_rn, d, inv, sh);
+}
+
+template <typename T, typename B>
+PDCS_DEV void b_project_cols(const BatchArgs<T>& a, const BInst& I, B* v, const double* d, int inv,
+                             int dual, double* sh) {
+  b_proj_exp(v, a.exp_cs, a.exp_cisd, I.exp_c0, I.exp_cn, d, inv, dual);
+  __syncthreads();
+  b_proj_soc(v, a.soc_cs, a.soc_cd, I.soc_c0, I.soc_cn, d, inv, sh);
+}
+
+// Statistics of one point into sc.st[slot] (k_res_prep, the projections and
+// k_point_stats of the grid engine, restricted to the instance).
+template <typename T, bool FULL>
+PDCS_DEV void b_point_stats(const BatchArgs<T>& a, const BInst& I, Ctl& sc, int slot,
+                            const PointRef<T>& pt, const T* x0, const T* y0, int buf, double* sh) {
+  const Prob<T>& p = a.p;
+  const TmpRef tr{a.tm[buf], a.tn[buf], FULL ? a.um[buf] : nullptr, FULL ? a.un[buf] : nullptr};
+  PDCS_BLOCK_LOOP(i, I.r0, I.r0 + I.m) res_prep_row(p, pt, tr, i);
+  PDCS_BLOCK_LOOP(j, I.c0, I.c0 + I.n) res_prep_col(p, pt, tr, j);
+  __syncthreads();
+  b_project_rows(a, I, tr.tm, p.d1, 0, 0, sh);
+  __syncthreads();
+  b_project_cols(a, I, tr.tn, p.d2, 0, 1, sh);
+  __syncthreads();
+  if (FULL) {
+    b_project_rows(a, I, tr.um, (const double*)nullptr, 0, 0, sh);
+    __syncthreads();
+    b_project_cols(a, I, tr.un, (const double*)nullptr, 0, 1, sh);
+    __syncthreads();
+  }
+  double s[kStatSums], mx[kStatMax];
+#pragma unroll
+  for (int k = 0; k < kStatSums; ++k) s[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < kStatMax; ++k) mx[k] = 0.0;
+  PDCS_BLOCK_LOOP(i, I.r0, I.r0 + I.m) stats_row<T, FULL>(p, pt, y0, tr, i, s, mx);
+  PDCS_BLOCK_LOOP(j, I.c0, I.c0 + I.n) stats_col<T, FULL>(p, pt, x0, tr, j, s, mx);
+  block_sum<kStatSums>(s, sh);
+  block_max<kStatMax>(mx, sh);
+  if (threadIdx.x == 0) ctl_stats_finalize(sc, slot, s, mx);
+  __syncthreads();
+}
+
+// One attempt of Function 1 and, if accepted, maxErr, beta and the reflected
+// Halpern step (the attempt body of the grid engine).
+template <typename T>
+PDCS_DEV void b_attempt(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh) {
+  const Prob<T>& p = a.p;
+  const int64_t r0 = I.r0, r1 = I.r0 + I.m, c0 = I.c0, c1 = I.c0 + I.n;
+  const double tau = sc.eta / sc.omega, sigma = sc.eta * sc.omega;
+  PDCS_BLOCK_LOOP(j, c0, c1) primal_elem(p, tau, a.x, a.gty, a.xh, j);
+  __syncthreads();
+  b_project_cols(a, I, a.xh, p.d2, 1, 0, sh);
+  __syncthreads();
+  b_spmv(a.rp, a.ci, a.vv, a.xh, a.gxh, r0, I.m, I.tile);
+  __syncthreads();
+  PDCS_BLOCK_LOOP(i, r0, r1) dual_elem(p, sigma, a.y, a.gxh, a.gx, a.yh, i);
+  __syncthreads();
+  b_project_rows(a, I, a.yh, p.d1, 1, 1, sh);
+  __syncthreads();
+  double s3[3] = {0.0, 0.0, 0.0};
+  PDCS_BLOCK_LOOP(j, c0, c1) {
+    const double d = (double)a.xh[j] - (double)a.x[j];
+    s3[0] += d * d;
+  }
+  PDCS_BLOCK_LOOP(i, r0, r1) {
+    const double d = (double)a.yh[i] - (double)a.y[i];
+    s3[1] += d * d;
+    s3[2] += d * ((double)a.gxh[i] - (double)a.gx[i]);
+  }
+  block_sum<3>(s3, sh);
+  if (threadIdx.x == 0) ctl_step_finalize(sc, s3[0], s3[1], s3[2]);
+  __syncthreads();
+  if (!sc.g_accept) return;
+  b_spmv(a.rpT, a.ciT, a.vvT, a.yh, a.gtyh, c0, I.n, I.tile);
+  __syncthreads();
+  const PointRef<T> ph{a.xh, a.yh, a.gxh, a.gtyh};
+  b_point_stats<T, false>(a, I, sc, 0, ph, nullptr, nullptr, 0, sh);
+  const double kk = (double)sc.k, beta = sc.beta, eta = sc.eta_acc;
+  const double ca = (kk + 1.0) / (kk + 2.0), cb = 1.0 / (kk + 2.0);
+  PDCS_BLOCK_LOOP(j, c0, c1) halpern_elem(ca, cb, beta, eta, a.x, a.gty, a.xh, a.gtyh, a.x0, a.gty0, a.xs, j);
+  PDCS_BLOCK_LOOP(i, r0, r1) halpern_elem(ca, cb, beta, eta, a.y, a.gx, a.yh, a.gxh, a.y0, a.gx0, a.ys, i);
+  __syncthreads();
+  if (threadIdx.x == 0) ctl_halpern_finalize(sc, eta, beta, nullptr);
+  __syncthreads();
+}
+
+// The restart / termination check (average, candidate statistics, Algorithm 3
+// for both candidates, decision, candidate copy and the restart's products).
+template <typename T>
+PDCS_DEV void b_check(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh) {
+  const Prob<T>& p = a.p;
+  const int64_t r0 = I.r0, r1 = I.r0 + I.m, c0 = I.c0, c1 = I.c0 + I.n;
+  const double w = sc.wsum;
+  PDCS_BLOCK_LOOP(j, c0, c1) a.xb[j] = (T)(a.xs[j] / w);
+  PDCS_BLOCK_LOOP(i, r0, r1) a.yb[i] = (T)(a.ys[i] / w);
+  __syncthreads();
+  b_spmv(a.rp, a.ci, a.vv, a.xb, a.gxb, r0, I.m, I.tile);
+  b_spmv(a.rpT, a.ciT, a.vvT, a.yb, a.gtyb, c0, I.n, I.tile);
+  __syncthreads();
+  const PointRef<T> z{a.x, a.y, a.gx, a.gty}, zb{a.xb, a.yb, a.gxb, a.gtyb};
+  b_point_stats<T, true>(a, I, sc, 1, z, a.x0, a.y0, 0, sh);
+  b_point_stats<T, true>(a, I, sc, 2, zb, a.x0, a.y0, 1, sh);
+  if (threadIdx.x == 0) ctl_bisect_init(sc);
+  __syncthreads();
+  while (sc.bs[0].active || sc.bs[1].active) {
+    for (int c = 0; c < 2; ++c) {
+      if (!sc.bs[c].active) continue;  // uniform
+      const PointRef<T> pt = c == 0 ? z : zb;
+      const double t = probe_t(sc.bs[c]);
+      const double tt = t * sc.bs[c].tau, ts = t * sc.bs[c].sigma;
+      PDCS_BLOCK_LOOP(j, c0, c1) probe_prep_col(p, pt, tt, a.px[c], j);
+      PDCS_BLOCK_LOOP(i, r0, r1) probe_prep_row(p, pt, ts, a.py[c], i);
+      __syncthreads();
+      b_project_cols(a, I, a.px[c], p.d2, 1, 0, sh);
+      __syncthreads();
+      b_project_rows(a, I, a.py[c], p.d1, 1, 1, sh);
+      __syncthreads();
+    }
+    double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int c = 0; c < 2; ++c) {
+      if (!sc.bs[c].active) continue;
+      const PointRef<T> pt = c == 0 ? z : zb;
+      double s4[4] = {0.0, 0.0, 0.0, 0.0};
+      PDCS_BLOCK_LOOP(j, c0, c1) probe_sum_col(p, pt, a.px[c], j, s4);
+      PDCS_BLOCK_LOOP(i, r0, r1) probe_sum_row(p, pt, a.py[c], i, s4);
+      for (int k = 0; k < 4; ++k) s8[4 * c + k] = s4[k];
+    }
+    block_sum<8>(s8, sh);
+    if (threadIdx.x == 0) {
+      const double SS[2][4] = {{s8[0], s8[1], s8[2], s8[3]}, {s8[4], s8[5], s8[6], s8[7]}};
+      ctl_probe_finalize(sc, SS);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ctl_check_decide(sc, nullptr);
+  __syncthreads();
+  const PointRef<T> s = sc.cand ? zb : z;
+  const bool rs = sc.g_restart != 0;
+  PDCS_BLOCK_LOOP(j, c0, c1) {
+    const T v = s.x[j];
+    a.gtyc[j] = s.gty[j];
+    a.xc[j] = v;
+    if (rs) { a.x0[j] = v; a.x[j] = v; a.xs[j] = 0.0; }
+  }
+  PDCS_BLOCK_LOOP(i, r0, r1) {
+    const T v = s.y[i];
+    a.gxc[i] = s.gx[i];
+    a.yc[i] = v;
+    if (rs) { a.y0[i] = v; a.y[i] = v; a.ys[i] = 0.0; }
+  }
+  __syncthreads();
+  if (rs) {
+    b_spmv(a.rp, a.ci, a.vv, a.x0, a.gx0, r0, I.m, I.tile);
+    b_spmv(a.rpT, a.ciT, a.vvT, a.y0, a.gty0, c0, I.n, I.tile);
+    __syncthreads();
+    PDCS_BLOCK_LOOP(j, c0, c1) a.gty[j] = a.gty0[j];
+    PDCS_BLOCK_LOOP(i, r0, r1) a.gx[i] = a.gx0[i];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ctl_check_end(sc);
+  __syncthreads();
+}
+
+// One instance from a cold start to termination; the returned point is left
+// in (xc, yc, gxc, gtyc) and its statistics in sc.st[3].
+template <typename T>
+PDCS_DEV void b_solve(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh,
+                      unsigned long long t_begin) {
+  const Prob<T>& p = a.p;
+  const int64_t r0 = I.r0, r1 = I.r0 + I.m, c0 = I.c0, c1 = I.c0 + I.n;
+  // per-instance norms: ||hhat||_1, ||hhat||_2^2, ||chat||_1, ||chat||_2^2,
+  // ||h||_inf, ||c||_inf (unscaled) and max |Ghat| (eta0 = 1 / max |Ghat|)
+  double s4[4] = {0.0, 0.0, 0.0, 0.0}, mx3[3] = {0.0, 0.0, 0.0};
+  PDCS_BLOCK_LOOP(i, r0, r1) {
+    const double h = (double)p.h[i];
+    s4[0] += fabs(h);
+    s4[1] += h * h;
+    mx3[0] = fmax(mx3[0], fabs(h / p.d1[i]));
+  }
+  PDCS_BLOCK_LOOP(j, c0, c1) {
+    const double c = (double)p.c[j];
+    s4[2] += fabs(c);
+    s4[3] += c * c;
+    mx3[1] = fmax(mx3[1], fabs(c / p.d2[j]));
+  }
+  if (I.m > 0) {
+    PDCS_BLOCK_LOOP(e, a.rp[r0], a.rp[r1]) mx3[2] = fmax(mx3[2], fabs((double)a.vv[e]));
+  }
+  block_sum<4>(s4, sh);
+  block_max<3>(mx3, sh);
+  if (threadIdx.x == 0) {
+    sc = *a.tmpl;
+    const double nh2 = sqrt(s4[1]), nc2 = sqrt(s4[3]);
+    const double omega0 = (nc2 > 1e-10 && nh2 > 1e-10) ? nc2 / nh2 : 1.0;  // Sec. 2.5
+    const double eta0 = mx3[2] > 0.0 ? 1.0 / mx3[2] : 1.0;                  // 1 / ||Ghat||_inf
+    sc.eta = sc.eta_hat = sc.eta_acc = sc.eta0 = eta0;
+    sc.omega = sc.omega0 = omega0;
+    sc.h1 = s4[0];
+    sc.c1 = s4[2];
+    sc.hinf = mx3[0];
+    sc.cinf = mx3[1];
+    sc.status = kRunning;
+  }
+  // cold start: x = y = 0, so every product is zero
+  PDCS_BLOCK_LOOP(j, c0, c1) {
+    a.x[j] = a.x0[j] = a.gty[j] = a.gty0[j] = (T)0.0;
+    a.xs[j] = 0.0;
+  }
+  PDCS_BLOCK_LOOP(i, r0, r1) {
+    a.y[i] = a.y0[i] = a.gx[i] = a.gx0[i] = (T)0.0;
+    a.ys[i] = 0.0;
+  }
+  __syncthreads();
+  const unsigned long long limit = (unsigned long long)(a.time_limit_s * 1e9);
+  while (true) {
+    if (threadIdx.x == 0) ctl_period_begin(sc);
+    __syncthreads();
+    while (sc.g_attempt) {
+      b_attempt(a, I, sc, sh);
+      if (threadIdx.x == 0) ctl_loop_ctl(sc);
+      __syncthreads();
+    }
+    if (sc.g_check) b_check(a, I, sc, sh);
+    if (threadIdx.x == 0 && sc.status == kRunning && global_ns() - t_begin > limit) sc.status = 6;
+    __syncthreads();
+    if (sc.status != kRunning) break;
+  }
+  // returned point: the last candidate, else the current iterate
+  if (!sc.have_cand) {
+    PDCS_BLOCK_LOOP(j, c0, c1) { a.xc[j] = a.x[j]; a.gtyc[j] = a.gty[j]; }
+    PDCS_BLOCK_LOOP(i, r0, r1) { a.yc[i] = a.y[i]; a.gxc[i] = a.gx[i]; }
+    __syncthreads();
+  }
+  const PointRef<T> pr{a.xc, a.yc, a.gxc, a.gtyc};
+  b_point_stats<T, true>(a, I, sc, 3, pr, nullptr, nullptr, 0, sh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchThreads) k_batch(BatchArgs<T> a) {
+  __shared__ double sh[kBatchSh];
+  __shared__ Ctl sc;
+  __shared__ int s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int q = s_next;
+    __syncthreads();
+    if (q >= a.count) break;
+    const int idx = a.order[q];
+    const BInst I = a.inst[idx];
+    const unsigned long long t_begin = global_ns();
+    b_solve(a, I, sc, sh, t_begin);
+    if (threadIdx.x == 0) {
+      a.ctls[idx] = sc;
+      a.times[2 * idx] = t_begin;
+      a.times[2 * idx + 1] = global_ns();
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace pdcs

@@ -93,6 +93,17 @@ struct TmpRef {
 // xhat = Proj_X(x - tau (c - G^T y)), tau = eta / omega (eq. PDHG); cone columns
 // are projected afterwards by the cone kernels.
 template <typename T>
+PDCS_DEV void primal_elem(const Prob<T>& p, double tau, const T* __restrict__ x,
+                          const T* __restrict__ gty, T* __restrict__ xh, int64_t j) {
+  double v = (double)x[j] - tau * ((double)p.c[j] - (double)gty[j]);
+  const uint8_t kd = p.ck[j];
+  if (kd == CK_BOX) v = fmin(fmax(v, p.lo[j]), p.hi[j]);
+  else if (kd == CK_ZERO) v = 0.0;
+  else if (kd == CK_NONNEG) v = fmax(v, 0.0);
+  xh[j] = (T)v;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_primal(Prob<T> p, const Ctl* __restrict__ ctl,
                                                        const T* __restrict__ x,
                                                        const T* __restrict__ gty,
@@ -100,18 +111,20 @@ __global__ void __launch_bounds__(kEwThreads) k_primal(Prob<T> p, const Ctl* __r
   if (!ctl->g_attempt) return;
   ktimer_begin(tslot(p.tm, TM_PRIMAL));
   const double tau = ctl->eta / ctl->omega;
-  PDCS_GRID_LOOP(j, p.n) {
-    double v = (double)x[j] - tau * ((double)p.c[j] - (double)gty[j]);
-    const uint8_t kd = p.ck[j];
-    if (kd == CK_BOX) v = fmin(fmax(v, p.lo[j]), p.hi[j]);
-    else if (kd == CK_ZERO) v = 0.0;
-    else if (kd == CK_NONNEG) v = fmax(v, 0.0);
-    xh[j] = (T)v;
-  }
+  PDCS_GRID_LOOP(j, p.n) primal_elem(p, tau, x, gty, xh, j);
   ktimer_end(tslot(p.tm, TM_PRIMAL));
 }
 
 // yhat = Proj_Y(y + sigma (h - G (2 xhat - x))), sigma = eta omega.
+template <typename T>
+PDCS_DEV void dual_elem(const Prob<T>& p, double sigma, const T* __restrict__ y,
+                        const T* __restrict__ gxh, const T* __restrict__ gx, T* __restrict__ yh,
+                        int64_t i) {
+  double v = (double)y[i] + sigma * ((double)p.h[i] - 2.0 * (double)gxh[i] + (double)gx[i]);
+  if (p.rk[i] == RK_NONNEG) v = fmax(v, 0.0);
+  yh[i] = (T)v;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_dual(Prob<T> p, const Ctl* __restrict__ ctl,
                                                      const T* __restrict__ y,
@@ -121,16 +134,37 @@ __global__ void __launch_bounds__(kEwThreads) k_dual(Prob<T> p, const Ctl* __res
   if (!ctl->g_attempt) return;
   ktimer_begin(tslot(p.tm, TM_DUAL));
   const double sigma = ctl->eta * ctl->omega;
-  PDCS_GRID_LOOP(i, p.m) {
-    double v = (double)y[i] + sigma * ((double)p.h[i] - 2.0 * (double)gxh[i] + (double)gx[i]);
-    if (p.rk[i] == RK_NONNEG) v = fmax(v, 0.0);
-    yh[i] = (T)v;
-  }
+  PDCS_GRID_LOOP(i, p.m) dual_elem(p, sigma, y, gxh, gx, yh, i);
   ktimer_end(tslot(p.tm, TM_DUAL));
 }
 
-// Step-size test of Function 1 (eq. adaptive_step_size).  kbar counts every
-// attempt and is incremented before the exponents use (kbar + 1).
+// Step-size test of Function 1 (eq. adaptive_step_size) from the reduced
+// ||dx||^2, ||dy||^2 and dy^T G dx.  kbar counts every attempt and is
+// incremented before the exponents use (kbar + 1).  (Thread-0 logic shared by
+// the grid-wide and the per-instance batched engines.)
+PDCS_DEV void ctl_step_finalize(Ctl& c, double dx2, double dy2, double inter) {
+  inter = fabs(inter);
+  const double omega = c.omega, eta = c.eta;
+  c.kbar += 1;
+  const double kb1 = (double)(c.kbar + 1);
+  const double num = 0.5 * (omega * dx2 + dy2 / omega);
+  const double eta_bar = inter > 0.0 ? num / inter : INFINITY;
+  const double eta_p = fmin((1.0 - pow(kb1, -0.3)) * eta_bar, (1.0 + pow(kb1, -0.6)) * eta);
+  const int acc = eta < eta_bar ? 1 : 0;
+  c.accepted = acc;
+  if (acc) {
+    c.eta_acc = eta;
+    c.eta_hat = eta_p;
+  }
+  c.eta = eta_p;
+  c.g_accept = acc;
+  if (!(eta_p > 0.0) || !isfinite(eta_p)) {
+    c.status = 8;  // numerical error
+    c.g_accept = 0;
+    c.g_attempt = 0;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict__ ctl,
                                                      const T* __restrict__ x,
@@ -162,28 +196,8 @@ __global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict_
   double S3[3];
   cta_reduce_sums<3>(part, gridDim.x, 3, S3, sh);
   if (threadIdx.x != 0) return;
-  double dx2 = S3[0], dy2 = S3[1], inter = S3[2];
   ctl->cnt[CNT_STEP] = 0u;
-  inter = fabs(inter);
-  const double omega = ctl->omega, eta = ctl->eta;
-  ctl->kbar += 1;
-  const double kb1 = (double)(ctl->kbar + 1);
-  const double num = 0.5 * (omega * dx2 + dy2 / omega);
-  const double eta_bar = inter > 0.0 ? num / inter : INFINITY;
-  const double eta_p = fmin((1.0 - pow(kb1, -0.3)) * eta_bar, (1.0 + pow(kb1, -0.6)) * eta);
-  const int acc = eta < eta_bar ? 1 : 0;
-  ctl->accepted = acc;
-  if (acc) {
-    ctl->eta_acc = eta;
-    ctl->eta_hat = eta_p;
-  }
-  ctl->eta = eta_p;
-  ctl->g_accept = acc;
-  if (!(eta_p > 0.0) || !isfinite(eta_p)) {
-    ctl->status = 8;  // numerical error
-    ctl->g_accept = 0;
-    ctl->g_attempt = 0;
-  }
+  ctl_step_finalize(*ctl, S3[0], S3[1], S3[2]);
 }
 
 // ------------------------------------------------------------- cone kernels
@@ -259,6 +273,24 @@ __global__ void __launch_bounds__(NT) k_cone_soc(B* v0, B* v1, const int64_t* __
 // projection buffers, scaled and (optionally) unscaled.  blockIdx.y selects the
 // point when two are processed together.
 template <typename T>
+PDCS_DEV void res_prep_row(const Prob<T>& p, const PointRef<T>& pt, const TmpRef& tr, int64_t i) {
+  if (p.rk[i] >= RK_SOC) {
+    const double u = (double)pt.gx[i] - (double)p.h[i];
+    tr.tm[i] = u;
+    if (tr.um) tr.um[i] = u / p.d1[i];
+  }
+}
+
+template <typename T>
+PDCS_DEV void res_prep_col(const Prob<T>& p, const PointRef<T>& pt, const TmpRef& tr, int64_t j) {
+  if (p.ck[j] >= CK_SOC) {
+    const double l = (double)p.c[j] - (double)pt.gty[j];
+    tr.tn[j] = l;
+    if (tr.un) tr.un[j] = l / p.d2[j];
+  }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_res_prep(Prob<T> p, const int* __restrict__ gate,
                                                          PointRef<T> a, PointRef<T> b,
                                                          TmpRef ta, TmpRef tb) {
@@ -266,20 +298,8 @@ __global__ void __launch_bounds__(kEwThreads) k_res_prep(Prob<T> p, const int* _
   ktimer_begin(tslot(p.tm, TM_RES_PREP));
   const PointRef<T> pt = blockIdx.y == 0 ? a : b;
   const TmpRef tr = blockIdx.y == 0 ? ta : tb;
-  PDCS_GRID_LOOP(i, p.m) {
-    if (p.rk[i] >= RK_SOC) {
-      const double u = (double)pt.gx[i] - (double)p.h[i];
-      tr.tm[i] = u;
-      if (tr.um) tr.um[i] = u / p.d1[i];
-    }
-  }
-  PDCS_GRID_LOOP(j, p.n) {
-    if (p.ck[j] >= CK_SOC) {
-      const double l = (double)p.c[j] - (double)pt.gty[j];
-      tr.tn[j] = l;
-      if (tr.un) tr.un[j] = l / p.d2[j];
-    }
-  }
+  PDCS_GRID_LOOP(i, p.m) res_prep_row(p, pt, tr, i);
+  PDCS_GRID_LOOP(j, p.n) res_prep_col(p, pt, tr, j);
   ktimer_end(tslot(p.tm, TM_RES_PREP));
 }
 
@@ -314,6 +334,88 @@ PDCS_DEV void finish_stats(const Ctl* ctl, PointStats& st, const double* s, cons
   st.inf_max = fmax(st.inf_rel_p, fmax(st.inf_rel_d, st.inf_rel_gap));
 }
 
+// Statistics of one point from its reduced sums / maxima; slot 0 also sets the
+// reflection parameter beta (eq. adaptive_reflection) from maxErr.
+PDCS_DEV void ctl_stats_finalize(Ctl& c, int slot, const double* S, const double* M) {
+  PointStats& st = c.st[slot];
+  finish_stats(&c, st, S, M);
+  if (slot == 0) {
+    const double me = st.max_err;
+    double beta = me > 0.0 ? -0.1 * log10(me) + 0.2 : 1.0;
+    beta = fmin(1.0, fmax(0.0, beta));
+    if (isnan(me)) beta = 0.0;
+    c.beta = beta;
+  }
+}
+
+// Per-element contributions to the point statistics (row i / column j).
+template <typename T, bool FULL>
+PDCS_DEV void stats_row(const Prob<T>& p, const PointRef<T>& pt, const T* __restrict__ y0,
+                        const TmpRef& tr, int64_t i, double (&s)[kStatSums],
+                        double (&mx)[kStatMax]) {
+  const double gx = (double)pt.gx[i], h = (double)p.h[i], y = (double)pt.y[i];
+  const double u = gx - h;
+  const uint8_t kd = p.rk[i];
+  double P;
+  if (kd == RK_FREE) P = 0.0;
+  else if (kd == RK_NONNEG) P = fmax(u, 0.0);
+  else P = tr.tm[i];
+  const double r = u - P;
+  s[0] += r * r;
+  s[3] += h * y;
+  s[4] += u * u;
+  if (FULL) {
+    const double d1 = p.d1[i];
+    const double uu = u / d1;
+    double Pu;
+    if (kd == RK_FREE) Pu = 0.0;
+    else if (kd == RK_NONNEG) Pu = fmax(uu, 0.0);
+    else Pu = tr.um[i];
+    mx[0] = fmax(mx[0], fabs(uu - Pu));
+    mx[1] = fmax(mx[1], fabs(gx / d1));
+    mx[2] = fmax(mx[2], fabs(Pu));
+    if (y0) {
+      const double dy = y - (double)y0[i];
+      s[7] += dy * dy;
+    }
+  }
+}
+
+template <typename T, bool FULL>
+PDCS_DEV void stats_col(const Prob<T>& p, const PointRef<T>& pt, const T* __restrict__ x0,
+                        const TmpRef& tr, int64_t j, double (&s)[kStatSums],
+                        double (&mx)[kStatMax]) {
+  const double gty = (double)pt.gty[j], c = (double)p.c[j], x = (double)pt.x[j];
+  const double lam = c - gty;
+  const uint8_t kd = p.ck[j];
+  double res;
+  if (kd == CK_BOX) {
+    const double lo = p.lo[j], hi = p.hi[j];
+    res = lam - proj_lambda(lam, lo, hi);
+    if (isfinite(lo)) s[3] += lo * fmax(lam, 0.0);
+    if (isfinite(hi)) s[3] -= hi * fmax(-lam, 0.0);
+  } else if (kd == CK_ZERO) {
+    res = 0.0;
+  } else if (kd == CK_NONNEG) {
+    res = fmin(lam, 0.0);
+  } else {
+    res = lam - tr.tn[j];
+  }
+  s[1] += res * res;
+  s[2] += c * x;
+  s[5] += lam * lam;
+  if (FULL) {
+    const double d2 = p.d2[j];
+    const double resu = kd >= CK_SOC ? lam / d2 - tr.un[j] : res / d2;
+    mx[3] = fmax(mx[3], fabs(resu));
+    mx[4] = fmax(mx[4], fabs(gty / d2));
+    if (x0) {
+      const double dx = x - (double)x0[j];
+      s[6] += dx * dx;
+    }
+  }
+}
+
 // Residual norms (eqs. tolerance-3 / tolerance-2 on the rescaled problem and
 // eq. PDCS_terminate_tolerance_rel on the unscaled one), objectives, and the
 // norms needed by Algorithm 3 and Sec. 2.5, for one point.  slot 0 also sets
@@ -334,65 +436,8 @@ __global__ void __launch_bounds__(kEwThreads) k_point_stats(Prob<T> p, Ctl* __re
   for (int k = 0; k < kStatSums; ++k) s[k] = 0.0;
 #pragma unroll
   for (int k = 0; k < kStatMax; ++k) mx[k] = 0.0;
-  PDCS_GRID_LOOP(i, p.m) {
-    const double gx = (double)pt.gx[i], h = (double)p.h[i], y = (double)pt.y[i];
-    const double u = gx - h;
-    const uint8_t kd = p.rk[i];
-    double P;
-    if (kd == RK_FREE) P = 0.0;
-    else if (kd == RK_NONNEG) P = fmax(u, 0.0);
-    else P = tr.tm[i];
-    const double r = u - P;
-    s[0] += r * r;
-    s[3] += h * y;
-    s[4] += u * u;
-    if (FULL) {
-      const double d1 = p.d1[i];
-      const double uu = u / d1;
-      double Pu;
-      if (kd == RK_FREE) Pu = 0.0;
-      else if (kd == RK_NONNEG) Pu = fmax(uu, 0.0);
-      else Pu = tr.um[i];
-      mx[0] = fmax(mx[0], fabs(uu - Pu));
-      mx[1] = fmax(mx[1], fabs(gx / d1));
-      mx[2] = fmax(mx[2], fabs(Pu));
-      if (y0) {
-        const double dy = y - (double)y0[i];
-        s[7] += dy * dy;
-      }
-    }
-  }
-  PDCS_GRID_LOOP(j, p.n) {
-    const double gty = (double)pt.gty[j], c = (double)p.c[j], x = (double)pt.x[j];
-    const double lam = c - gty;
-    const uint8_t kd = p.ck[j];
-    double res;
-    if (kd == CK_BOX) {
-      const double lo = p.lo[j], hi = p.hi[j];
-      res = lam - proj_lambda(lam, lo, hi);
-      if (isfinite(lo)) s[3] += lo * fmax(lam, 0.0);
-      if (isfinite(hi)) s[3] -= hi * fmax(-lam, 0.0);
-    } else if (kd == CK_ZERO) {
-      res = 0.0;
-    } else if (kd == CK_NONNEG) {
-      res = fmin(lam, 0.0);
-    } else {
-      res = lam - tr.tn[j];
-    }
-    s[1] += res * res;
-    s[2] += c * x;
-    s[5] += lam * lam;
-    if (FULL) {
-      const double d2 = p.d2[j];
-      const double resu = kd >= CK_SOC ? lam / d2 - tr.un[j] : res / d2;
-      mx[3] = fmax(mx[3], fabs(resu));
-      mx[4] = fmax(mx[4], fabs(gty / d2));
-      if (x0) {
-        const double dx = x - (double)x0[j];
-        s[6] += dx * dx;
-      }
-    }
-  }
+  PDCS_GRID_LOOP(i, p.m) stats_row<T, FULL>(p, pt, y0, tr, i, s, mx);
+  PDCS_GRID_LOOP(j, p.n) stats_col<T, FULL>(p, pt, x0, tr, j, s, mx);
   block_sum<kStatSums>(s, sh);
   block_max<kStatMax>(mx, sh);
   if (threadIdx.x == 0) {
@@ -405,18 +450,48 @@ __global__ void __launch_bounds__(kEwThreads) k_point_stats(Prob<T> p, Ctl* __re
   cta_reduce_parts<kStatSums, kStatMax>(part, gridDim.x, kStatK, S, M, sh);
   if (threadIdx.x != 0) return;
   ctl->cnt[CNT_STATS0 + slot] = 0u;
-  PointStats& st = ctl->st[slot];
-  finish_stats(ctl, st, S, M);
-  if (slot == 0) {
-    const double me = st.max_err;
-    double beta = me > 0.0 ? -0.1 * log10(me) + 0.2 : 1.0;
-    beta = fmin(1.0, fmax(0.0, beta));
-    if (isnan(me)) beta = 0.0;
-    ctl->beta = beta;
-  }
+  ctl_stats_finalize(*ctl, slot, S, M);
 }
 
 // ------------------------------------------------------- Halpern + average
+// One coordinate of the reflected Halpern step for a vector v and its
+// maintained product q (x with G^T y, or y with G x), plus the FP64 average sum.
+template <typename T>
+PDCS_DEV void halpern_elem(double a, double b, double beta, double eta, T* __restrict__ v,
+                           T* __restrict__ q, const T* __restrict__ vh, const T* __restrict__ qh,
+                           const T* __restrict__ v0, const T* __restrict__ q0,
+                           double* __restrict__ vs, int64_t i) {
+  const T vn = (T)(a * ((1.0 + beta) * (double)vh[i] - beta * (double)v[i]) + b * (double)v0[i]);
+  v[i] = vn;
+  vs[i] += eta * (double)vn;
+  q[i] = (T)(a * ((1.0 + beta) * (double)qh[i] - beta * (double)q[i]) + b * (double)q0[i]);
+}
+
+// Counters after an accepted step; sets the check / stop flags.
+PDCS_DEV void ctl_halpern_finalize(Ctl& c, double eta, double beta, double* trace) {
+  c.k += 1;
+  c.iter += 1;
+  c.wsum += eta;
+  const long long it = c.iter;
+  if (trace != nullptr && it <= c.trace_cap) {
+    double* r = trace + (it - 1) * 12;
+    r[0] = (double)it; r[1] = (double)c.kbar; r[2] = (double)c.period; r[3] = eta;
+    r[4] = c.eta_hat; r[5] = beta; r[6] = c.omega; r[7] = c.st[0].max_err;
+    r[8] = 0.0; r[9] = -1.0; r[10] = 0.0; r[11] = NAN;
+  }
+  if (!isfinite(c.st[0].max_err)) {
+    c.status = 8;
+    c.g_attempt = 0;
+  } else if (it % c.check_freq == 0) {
+    c.period_done = 1;
+    c.g_attempt = 0;
+    c.g_check = 1;
+  } else if (it >= c.max_iter) {
+    c.status = 1;
+    c.g_attempt = 0;
+  }
+}
+
 // z^{t,k+1} = (k+1)/(k+2) ((1+beta) zhat - beta z) + z^{t,0}/(k+2) (Algorithm
 // 1), applied to (x, y) and, by linearity, to the maintained products G x and
 // G^T y; the average accumulators add eta * z^{t,k+1} in FP64.
@@ -432,61 +507,41 @@ __global__ void __launch_bounds__(kEwThreads) k_halpern(
   const double kk = (double)ctl->k;
   const double beta = ctl->beta, eta = ctl->eta_acc;
   const double a = (kk + 1.0) / (kk + 2.0), b = 1.0 / (kk + 2.0);
-  PDCS_GRID_LOOP(j, p.n) {
-    const T xn = (T)(a * ((1.0 + beta) * (double)xh[j] - beta * (double)x[j]) + b * (double)x0[j]);
-    x[j] = xn;
-    xs[j] += eta * (double)xn;
-    gty[j] = (T)(a * ((1.0 + beta) * (double)gtyh[j] - beta * (double)gty[j]) + b * (double)gty0[j]);
-  }
-  PDCS_GRID_LOOP(i, p.m) {
-    const T yn = (T)(a * ((1.0 + beta) * (double)yh[i] - beta * (double)y[i]) + b * (double)y0[i]);
-    y[i] = yn;
-    ys[i] += eta * (double)yn;
-    gx[i] = (T)(a * ((1.0 + beta) * (double)gxh[i] - beta * (double)gx[i]) + b * (double)gx0[i]);
-  }
+  PDCS_GRID_LOOP(j, p.n) halpern_elem(a, b, beta, eta, x, gty, xh, gtyh, x0, gty0, xs, j);
+  PDCS_GRID_LOOP(i, p.m) halpern_elem(a, b, beta, eta, y, gx, yh, gxh, y0, gx0, ys, i);
   ktimer_end(tslot(p.tm, TM_HALPERN));
   if (!last_block_done(&ctl->cnt[CNT_HALPERN])) return;
   if (threadIdx.x != 0) return;
   ctl->cnt[CNT_HALPERN] = 0u;
-  ctl->k += 1;
-  ctl->iter += 1;
-  ctl->wsum += eta;
-  const long long it = ctl->iter;
-  if (trace != nullptr && it <= ctl->trace_cap) {
-    double* r = trace + (it - 1) * 12;
-    r[0] = (double)it; r[1] = (double)ctl->kbar; r[2] = (double)ctl->period; r[3] = eta;
-    r[4] = ctl->eta_hat; r[5] = beta; r[6] = ctl->omega; r[7] = ctl->st[0].max_err;
-    r[8] = 0.0; r[9] = -1.0; r[10] = 0.0; r[11] = NAN;
-  }
-  if (!isfinite(ctl->st[0].max_err)) {
-    ctl->status = 8;
-    ctl->g_attempt = 0;
-  } else if (it % ctl->check_freq == 0) {
-    ctl->period_done = 1;
-    ctl->g_attempt = 0;
-    ctl->g_check = 1;
-  } else if (it >= ctl->max_iter) {
-    ctl->status = 1;
-    ctl->g_attempt = 0;
-  }
+  ctl_halpern_finalize(*ctl, eta, beta, trace);
 }
 
 // Body terminator of the attempt loop: continue while the period needs more
 // accepted iterations (bounded by guard_cap bodies per graph launch).
 // (use_cond = 0: launched eagerly from the host, which reads g_attempt itself.)
+PDCS_DEV int ctl_loop_ctl(Ctl& c) {
+  c.guard += 1;
+  c.bodies_a += 1;
+  const int go = (c.status == kRunning && !c.period_done && c.guard < c.guard_cap);
+  c.g_attempt = go;
+  return go;
+}
+
+PDCS_DEV int ctl_period_begin(Ctl& c) {
+  c.guard = 0;
+  const int go = (c.status == kRunning && !c.period_done);
+  c.g_attempt = go;
+  c.g_accept = 0;
+  return go;
+}
+
 __global__ void k_loop_ctl(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
-  ctl->guard += 1;
-  ctl->bodies_a += 1;
-  const int go = (ctl->status == kRunning && !ctl->period_done && ctl->guard < ctl->guard_cap);
-  ctl->g_attempt = go;
+  const int go = ctl_loop_ctl(*ctl);
   if (use_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 __global__ void k_period_begin(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
-  ctl->guard = 0;
-  const int go = (ctl->status == kRunning && !ctl->period_done);
-  ctl->g_attempt = go;
-  ctl->g_accept = 0;
+  const int go = ctl_period_begin(*ctl);
   if (use_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
@@ -508,11 +563,11 @@ __global__ void __launch_bounds__(kEwThreads) k_average(int64_t n, int64_t m, co
 // Algorithm 3 set-up for both candidates: r = ||z_c - z^{t,0}||_N, and the first
 // trial t0 = r / sqrt(tau ||b1||^2 + sigma ||b2||^2) (the unconstrained step that
 // reaches radius r).
-__global__ void k_bisect_init(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
+PDCS_DEV int ctl_bisect_init(Ctl& cl) {
   int any = 0;
-  const double tau = ctl->eta_acc / ctl->omega, sigma = ctl->eta_acc * ctl->omega;
+  const double tau = cl.eta_acc / cl.omega, sigma = cl.eta_acc * cl.omega;
   for (int c = 0; c < 2; ++c) {
-    Bisect& b = ctl->bs[c];
+    Bisect& b = cl.bs[c];
     b.phase = BS_DONE;
     b.active = 0;
     b.result = c == 0 ? 0.0 : INFINITY;
@@ -521,9 +576,9 @@ __global__ void k_bisect_init(Ctl* ctl, cudaGraphConditionalHandle h, int use_co
     b.tau = tau;
     b.sigma = sigma;
     b.last_dot = 0.0;
-    if (!ctl->g_check) continue;
-    if (c == 1 && ctl->method != 0) continue;
-    const PointStats& st = ctl->st[1 + c];
+    if (!cl.g_check) continue;
+    if (c == 1 && cl.method != 0) continue;
+    const PointStats& st = cl.st[1 + c];
     const double r = sqrt(st.dx2 / tau + st.dy2 / sigma);
     const double scale = sqrt(tau * st.lam2 + sigma * st.u2);
     b.r = r;
@@ -536,11 +591,54 @@ __global__ void k_bisect_init(Ctl* ctl, cudaGraphConditionalHandle h, int use_co
     b.active = 1;
     any = 1;
   }
-  ctl->probes = 0;
+  cl.probes = 0;
+  return any;
+}
+
+__global__ void k_bisect_init(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
+  const int any = ctl_bisect_init(*ctl);
   if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 PDCS_DEV double probe_t(const Bisect& b) { return b.phase == BS_EXP ? b.t : 0.5 * (b.tl + b.tr); }
+
+template <typename T>
+PDCS_DEV void probe_prep_col(const Prob<T>& p, const PointRef<T>& pt, double tt,
+                             double* __restrict__ px, int64_t j) {
+  const double b1 = (double)pt.gty[j] - (double)p.c[j];
+  double v = (double)pt.x[j] + tt * b1;
+  const uint8_t kd = p.ck[j];
+  if (kd == CK_BOX) v = fmin(fmax(v, p.lo[j]), p.hi[j]);
+  else if (kd == CK_ZERO) v = 0.0;
+  else if (kd == CK_NONNEG) v = fmax(v, 0.0);
+  px[j] = v;
+}
+
+template <typename T>
+PDCS_DEV void probe_prep_row(const Prob<T>& p, const PointRef<T>& pt, double ts,
+                             double* __restrict__ py, int64_t i) {
+  const double b2 = (double)p.h[i] - (double)pt.gx[i];
+  double v = (double)pt.y[i] + ts * b2;
+  if (p.rk[i] == RK_NONNEG) v = fmax(v, 0.0);
+  py[i] = v;
+}
+
+// Accumulates ||dx||^2, b1^T dx (column j) and ||dy||^2, b2^T dy (row i).
+template <typename T>
+PDCS_DEV void probe_sum_col(const Prob<T>& p, const PointRef<T>& pt, const double* __restrict__ px,
+                            int64_t j, double (&s)[4]) {
+  const double dx = px[j] - (double)pt.x[j];
+  s[0] += dx * dx;
+  s[2] += ((double)pt.gty[j] - (double)p.c[j]) * dx;
+}
+
+template <typename T>
+PDCS_DEV void probe_sum_row(const Prob<T>& p, const PointRef<T>& pt, const double* __restrict__ py,
+                            int64_t i, double (&s)[4]) {
+  const double dy = py[i] - (double)pt.y[i];
+  s[1] += dy * dy;
+  s[3] += ((double)p.h[i] - (double)pt.gx[i]) * dy;
+}
 
 // z(t) = (Proj_X(x + t tau b1), Proj_Y(y + t sigma b2)), b = (G^T y - c, h - G x)
 // (eq. compute_zt_2), elementwise part; blockIdx.y = candidate.
@@ -565,23 +663,58 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_prep(Prob<T> p, const Ctl*
   double* py = c == 0 ? py0 : py1;
   const double t = probe_t(bs);
   const double tt = t * bs.tau, ts = t * bs.sigma;
-  PDCS_GRID_LOOP(j, p.n) {
-    const double b1 = (double)pt.gty[j] - (double)p.c[j];
-    double v = (double)pt.x[j] + tt * b1;
-    const uint8_t kd = p.ck[j];
-    if (kd == CK_BOX) v = fmin(fmax(v, p.lo[j]), p.hi[j]);
-    else if (kd == CK_ZERO) v = 0.0;
-    else if (kd == CK_NONNEG) v = fmax(v, 0.0);
-    px[j] = v;
-  }
-  PDCS_GRID_LOOP(i, p.m) {
-    const double b2 = (double)p.h[i] - (double)pt.gx[i];
-    double v = (double)pt.y[i] + ts * b2;
-    if (p.rk[i] == RK_NONNEG) v = fmax(v, 0.0);
-    py[i] = v;
-  }
+  PDCS_GRID_LOOP(j, p.n) probe_prep_col(p, pt, tt, px, j);
+  PDCS_GRID_LOOP(i, p.m) probe_prep_row(p, pt, ts, py, i);
   ktimer_end(tm);
 }
+
+// Advances the exponential search / bisection state machines of Algorithm 3
+// for both candidates from the reduced sums SS[c] = (||dx||^2, ||dy||^2,
+// b1^T dx, b2^T dy); returns whether any candidate still needs probes.
+PDCS_DEV int ctl_probe_finalize(Ctl& c, const double (&SS)[2][4]) {
+  int any = 0;
+  for (int cc = 0; cc < 2; ++cc) {
+    Bisect& b = c.bs[cc];
+    if (!b.active) continue;
+    const double* S = SS[cc];
+    const double dist = sqrt(S[0] / b.tau + S[1] / b.sigma);
+    b.last_dot = S[2] + S[3];
+    if (b.phase == BS_EXP) {
+      if (dist > b.r) {
+        if (b.k == 0) { b.tl = 0.0; b.tr = b.t; }
+        else { b.tl = 0.5 * b.t; b.tr = b.t; }
+        b.phase = BS_BISECT;
+      } else {
+        b.t *= 2.0;
+        b.k += 1;
+        b.tl = 0.5 * b.t;
+        b.tr = b.t;
+        if (b.k >= 64) b.phase = BS_BISECT;
+      }
+    } else {
+      const double tm = 0.5 * (b.tl + b.tr);
+      if (dist < b.r) b.tl = tm; else b.tr = tm;
+      b.nb += 1;
+    }
+    if (b.phase == BS_BISECT && (b.tr - b.tl <= c.bisect_tol * b.tr || b.nb >= 64)) {
+      b.phase = BS_DONE;
+      b.active = 0;
+      b.result = b.last_dot / b.r;
+    }
+    any |= b.active;
+  }
+  c.probes += 1;
+  c.bodies_b += 1;
+  if (c.probes >= c.probe_cap) {
+    for (int cc = 0; cc < 2; ++cc) {
+      Bisect& b = c.bs[cc];
+      if (b.active) { b.active = 0; b.phase = BS_DONE; b.result = b.last_dot / b.r; }
+    }
+    any = 0;
+  }
+  return any;
+}
+
 
 // ||z(t) - z||_N and b^T (z(t) - z) for both candidates; the last CTA advances
 // the exponential search / bisection state machines of Algorithm 3.
@@ -604,16 +737,8 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __r
     const PointRef<T> pt = c == 0 ? a : bpt;
     const double* px = c == 0 ? px0 : px1;
     const double* py = c == 0 ? py0 : py1;
-    PDCS_GRID_LOOP(j, p.n) {
-      const double dx = px[j] - (double)pt.x[j];
-      s[0] += dx * dx;
-      s[2] += ((double)pt.gty[j] - (double)p.c[j]) * dx;
-    }
-    PDCS_GRID_LOOP(i, p.m) {
-      const double dy = py[i] - (double)pt.y[i];
-      s[1] += dy * dy;
-      s[3] += ((double)p.h[i] - (double)pt.gx[i]) * dy;
-    }
+    PDCS_GRID_LOOP(j, p.n) probe_sum_col(p, pt, px, j, s);
+    PDCS_GRID_LOOP(i, p.m) probe_sum_row(p, pt, py, i, s);
   }
   block_sum<4>(s, sh);
   if (threadIdx.x == 0) {
@@ -629,46 +754,7 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __r
   }
   if (threadIdx.x != 0) return;
   ctl->cnt[CNT_PROBE] = 0u;
-  int any = 0;
-  for (int cc = 0; cc < 2; ++cc) {
-    Bisect& b = ctl->bs[cc];
-    if (!b.active) continue;
-    const double* S = SS[cc];
-    const double dist = sqrt(S[0] / b.tau + S[1] / b.sigma);
-    b.last_dot = S[2] + S[3];
-    if (b.phase == BS_EXP) {
-      if (dist > b.r) {
-        if (b.k == 0) { b.tl = 0.0; b.tr = b.t; }
-        else { b.tl = 0.5 * b.t; b.tr = b.t; }
-        b.phase = BS_BISECT;
-      } else {
-        b.t *= 2.0;
-        b.k += 1;
-        b.tl = 0.5 * b.t;
-        b.tr = b.t;
-        if (b.k >= 64) b.phase = BS_BISECT;
-      }
-    } else {
-      const double tm = 0.5 * (b.tl + b.tr);
-      if (dist < b.r) b.tl = tm; else b.tr = tm;
-      b.nb += 1;
-    }
-    if (b.phase == BS_BISECT && (b.tr - b.tl <= ctl->bisect_tol * b.tr || b.nb >= 64)) {
-      b.phase = BS_DONE;
-      b.active = 0;
-      b.result = b.last_dot / b.r;
-    }
-    any |= b.active;
-  }
-  ctl->probes += 1;
-  ctl->bodies_b += 1;
-  if (ctl->probes >= ctl->probe_cap) {
-    for (int cc = 0; cc < 2; ++cc) {
-      Bisect& b = ctl->bs[cc];
-      if (b.active) { b.active = 0; b.phase = BS_DONE; b.result = b.last_dot / b.r; }
-    }
-    any = 0;
-  }
+  const int any = ctl_probe_finalize(*ctl, SS);
   if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
@@ -678,72 +764,74 @@ PDCS_DEV double kkt_w(double ep, double ed, double eg, double w) {
 
 // GetRestartCandidate, termination, restart conditions, KKT_omega fallback,
 // primal-weight update (Secs. 2.3, 2.5, 3.2.3).
-__global__ void k_check_decide(Ctl* ctl, double* trace) {
-  if (!ctl->g_check) return;
-  const bool avg = ctl->method == 0;
-  const double rho_h = ctl->bs[0].result;
-  const double rho_a = avg ? ctl->bs[1].result : INFINITY;
-  const double w = ctl->omega;
-  const bool fb = rho_h < 0.0 || (avg && rho_a < 0.0) || (ctl->has_ref && ctl->ref_rho < 0.0) ||
-                  (ctl->has_prev && ctl->prev_rho < 0.0);
-  const PointStats& s1 = ctl->st[1];
-  const PointStats& s2 = ctl->st[2];
+PDCS_DEV void ctl_check_decide(Ctl& c, double* trace) {
+  if (!c.g_check) return;
+  const bool avg = c.method == 0;
+  const double rho_h = c.bs[0].result;
+  const double rho_a = avg ? c.bs[1].result : INFINITY;
+  const double w = c.omega;
+  const bool fb = rho_h < 0.0 || (avg && rho_a < 0.0) || (c.has_ref && c.ref_rho < 0.0) ||
+                  (c.has_prev && c.prev_rho < 0.0);
+  const PointStats& s1 = c.st[1];
+  const PointStats& s2 = c.st[2];
   const double m_h = fb ? kkt_w(s1.abs_p, s1.abs_d, s1.gap, w) : rho_h;
   const double m_a = avg ? (fb ? kkt_w(s2.abs_p, s2.abs_d, s2.gap, w) : rho_a) : INFINITY;
   const int cand = (m_h <= m_a) ? 0 : 1;
   const double val = cand ? m_a : m_h;
   const double rho_c = cand ? rho_a : rho_h;
-  const PointStats& sc = ctl->st[1 + cand];
-  ctl->cand = cand;
-  ctl->have_cand = 1;
-  const long long it = ctl->iter;
-  if (trace != nullptr && it >= 1 && it <= ctl->trace_cap) {
+  const PointStats& sc = c.st[1 + cand];
+  c.cand = cand;
+  c.have_cand = 1;
+  const long long it = c.iter;
+  if (trace != nullptr && it >= 1 && it <= c.trace_cap) {
     double* r = trace + (it - 1) * 12;
     r[8] = 1.0; r[9] = (double)cand; r[11] = val;
   }
-  bool done = sc.inf_max <= ctl->rel_tol;
-  if (ctl->require_abs) done = done && fmax(sc.inf_abs_p, fmax(sc.inf_abs_d, sc.gap)) <= ctl->abs_tol;
-  ctl->g_restart = 0;
-  if (done) { ctl->status = 0; return; }
-  if (!isfinite(sc.inf_max)) { ctl->status = 8; return; }
+  bool done = sc.inf_max <= c.rel_tol;
+  if (c.require_abs) done = done && fmax(sc.inf_abs_p, fmax(sc.inf_abs_d, sc.gap)) <= c.abs_tol;
+  c.g_restart = 0;
+  if (done) { c.status = 0; return; }
+  if (!isfinite(sc.inf_max)) { c.status = 8; return; }
   bool restart = false;
-  if (ctl->adaptive_restart) {
-    const bool cond3 = (double)ctl->k >= 0.223 * (double)ctl->kbar;
-    if (!ctl->has_ref) {
+  if (c.adaptive_restart) {
+    const bool cond3 = (double)c.k >= 0.223 * (double)c.kbar;
+    if (!c.has_ref) {
       restart = cond3;
     } else {
-      const double ref = fb ? kkt_w(ctl->ref_ep, ctl->ref_ed, ctl->ref_eg, w) : ctl->ref_rho;
+      const double ref = fb ? kkt_w(c.ref_ep, c.ref_ed, c.ref_eg, w) : c.ref_rho;
       const bool c1 = val <= 0.4 * ref;
       bool c2 = false;
-      if (ctl->has_prev) {
-        const double pv = fb ? kkt_w(ctl->prev_ep, ctl->prev_ed, ctl->prev_eg, w) : ctl->prev_rho;
+      if (c.has_prev) {
+        const double pv = fb ? kkt_w(c.prev_ep, c.prev_ed, c.prev_eg, w) : c.prev_rho;
         c2 = val <= 0.8 * ref && val > pv;
       }
       restart = c1 || c2 || cond3;
     }
   }
   if (restart) {
-    if (trace != nullptr && it >= 1 && it <= ctl->trace_cap) trace[(it - 1) * 12 + 10] = 1.0;
+    if (trace != nullptr && it >= 1 && it <= c.trace_cap) trace[(it - 1) * 12 + 10] = 1.0;
     const double dx = sqrt(sc.dx2), dy = sqrt(sc.dy2);
-    double om = ctl->omega;
+    double om = c.omega;
     if (dx > 1e-10 && dy > 1e-10) om = exp(0.5 * log(dy / dx) + 0.5 * log(om));
-    if (om > 1e5 || om < 1e-5) om = ctl->omega0;
-    ctl->omega = om;
-    ctl->has_ref = 1;
-    ctl->ref_rho = rho_c;
-    ctl->ref_ep = sc.abs_p; ctl->ref_ed = sc.abs_d; ctl->ref_eg = sc.gap;
-    ctl->has_prev = 0;
-    ctl->period += 1;
-    ctl->restarts += 1;
-    ctl->k = 0;
-    ctl->wsum = 0.0;
-    ctl->g_restart = 1;
+    if (om > 1e5 || om < 1e-5) om = c.omega0;
+    c.omega = om;
+    c.has_ref = 1;
+    c.ref_rho = rho_c;
+    c.ref_ep = sc.abs_p; c.ref_ed = sc.abs_d; c.ref_eg = sc.gap;
+    c.has_prev = 0;
+    c.period += 1;
+    c.restarts += 1;
+    c.k = 0;
+    c.wsum = 0.0;
+    c.g_restart = 1;
   } else {
-    ctl->has_prev = 1;
-    ctl->prev_rho = rho_c;
-    ctl->prev_ep = sc.abs_p; ctl->prev_ed = sc.abs_d; ctl->prev_eg = sc.gap;
+    c.has_prev = 1;
+    c.prev_rho = rho_c;
+    c.prev_ep = sc.abs_p; c.prev_ed = sc.abs_d; c.prev_eg = sc.gap;
   }
 }
+
+__global__ void k_check_decide(Ctl* ctl, double* trace) { ctl_check_decide(*ctl, trace); }
 
 // Keep the chosen candidate (the returned point) and, on restart, make it the
 // new anchor and current iterate and clear the average.
@@ -782,14 +870,16 @@ __global__ void __launch_bounds__(kEwThreads) k_copy_products(int64_t n, int64_t
   ktimer_end(tm);
 }
 
-__global__ void k_check_end(Ctl* ctl) {
-  if (!ctl->g_check) return;
-  ctl->period_done = 0;
-  ctl->g_restart = 0;
-  ctl->g_check = 0;
-  if (ctl->status == kRunning && ctl->iter >= ctl->max_iter) ctl->status = 1;
-  ctl->g_attempt = ctl->status == kRunning;
+PDCS_DEV void ctl_check_end(Ctl& c) {
+  if (!c.g_check) return;
+  c.period_done = 0;
+  c.g_restart = 0;
+  c.g_check = 0;
+  if (c.status == kRunning && c.iter >= c.max_iter) c.status = 1;
+  c.g_attempt = c.status == kRunning;
 }
+
+__global__ void k_check_end(Ctl* ctl) { ctl_check_end(*ctl); }
 
 // ----------------------------------------------------------- init / output
 template <typename T>

@@ -28,6 +28,7 @@
 #include "iterate.cuh"
 #include "setup.cuh"
 #include "spmv.cuh"
+#include "batch.cuh"
 
 namespace pdcs {
 
@@ -280,9 +281,15 @@ struct SolverBase {
   int64_t m = 0, n = 0, nnz = 0;
 };
 
+struct BatchBase {
+  virtual ~BatchBase() {}
+  virtual void solve(double* x, double* y, double* s, pdcs_result* res, double* finish_s) = 0;
+};
+
 struct pdcs_handle {
   int device = 0;
-  SolverBase* solver = nullptr;
+  SolverBase* solver = nullptr;  // single problem
+  BatchBase* batch = nullptr;    // batch of problems (pdcs_setup_batch)
 };
 
 namespace pdcs {
@@ -359,10 +366,20 @@ struct Solver : SolverBase {
   }
 
   // -------------------------------------------------------------- set-up
+  // Column layout of a block-diagonal batch: each segment is one instance's
+  // columns [off, end): nb boxed columns, then its column cones.
+  struct ColSeg {
+    int64_t off, nb, end;
+    std::vector<pdcs_cone> cones;
+  };
+
+  // segs == NULL: the columns are nb_in boxed columns then the cones cc, and
+  // lb / ub hold nb_in entries.  Otherwise the segments give the layout and
+  // lb / ub hold n0 entries (read only at boxed columns).
   void setup(int64_t m0, int64_t n0, const int64_t* rp_in, const int32_t* ci_in, const double* v_in,
              const double* h_in, const double* c_in, int64_t nb_in, const double* lb,
              const double* ub, const std::vector<pdcs_cone>& rc, const std::vector<pdcs_cone>& cc,
-             const pdcs_options& o, cudaStream_t stream) {
+             const pdcs_options& o, cudaStream_t stream, const std::vector<ColSeg>* segs = nullptr) {
     user_st = stream;
     opt = o;
     m = m0;
@@ -405,15 +422,23 @@ struct Solver : SolverBase {
     if (herr & 8u) invalid("non-finite matrix value");
     if (herr & 16u) invalid("non-finite entry in h");
     if (herr & 32u) invalid("non-finite entry in c");
-    std::vector<double> hlo((size_t)nb), hhi((size_t)nb);
-    if (nb > 0) {
+    const int64_t nbl = segs ? n : nb;  // length of the bound arrays
+    std::vector<std::pair<int64_t, int64_t>> boxes;  // boxed column ranges
+    if (segs) {
+      for (const auto& sg : *segs) boxes.push_back({sg.off, sg.off + sg.nb});
+    } else {
+      boxes.push_back({0, nb});
+    }
+    std::vector<double> hlo((size_t)nbl), hhi((size_t)nbl);
+    if (nbl > 0) {
       if (!lb || !ub) invalid("lb and ub are required when nb > 0");
-      CK(cudaMemcpy(hlo.data(), lb, sizeof(double) * nb, cudaMemcpyDefault));
-      CK(cudaMemcpy(hhi.data(), ub, sizeof(double) * nb, cudaMemcpyDefault));
-      for (int64_t j = 0; j < nb; ++j) {
-        if (std::isnan(hlo[j]) || std::isnan(hhi[j]) || hlo[j] > hhi[j]) invalid("bounds must satisfy lb <= ub");
-        if (hlo[j] == INFINITY || hhi[j] == -INFINITY) invalid("infinite bound on the wrong side");
-      }
+      CK(cudaMemcpy(hlo.data(), lb, sizeof(double) * nbl, cudaMemcpyDefault));
+      CK(cudaMemcpy(hhi.data(), ub, sizeof(double) * nbl, cudaMemcpyDefault));
+      for (const auto& bx : boxes)
+        for (int64_t j = bx.first; j < bx.second; ++j) {
+          if (std::isnan(hlo[j]) || std::isnan(hhi[j]) || hlo[j] > hhi[j]) invalid("bounds must satisfy lb <= ub");
+          if (hlo[j] == INFINITY || hhi[j] == -INFINITY) invalid("infinite bound on the wrong side");
+        }
     }
     // ---- cone layout and RSOC pairs
     std::vector<int64_t> rpairs, cpairs;
@@ -423,8 +448,15 @@ struct Solver : SolverBase {
     std::vector<int64_t> rexp, cexp;
     std::vector<uint8_t> rexpd, cexpd;
     layout(rc, 0, m, true, hrk, rpairs, rsoc, rbig, rexp, rexpd);
-    for (int64_t j = 0; j < nb; ++j) hck[j] = CK_BOX;
-    layout(cc, nb, n, false, hck, cpairs, csoc, cbig, cexp, cexpd);
+    if (segs) {
+      for (const auto& sg : *segs) {
+        for (int64_t j = sg.off; j < sg.off + sg.nb; ++j) hck[j] = CK_BOX;
+        layout(sg.cones, sg.off + sg.nb, sg.end, false, hck, cpairs, csoc, cbig, cexp, cexpd);
+      }
+    } else {
+      for (int64_t j = 0; j < nb; ++j) hck[j] = CK_BOX;
+      layout(cc, nb, n, false, hck, cpairs, csoc, cbig, cexp, cexpd);
+    }
     // ---- RSOC reformulation on rows
     if (!rpairs.empty()) {
       merge_row_pairs(hrp, drp, dci, dv, rpairs, m);
@@ -491,15 +523,15 @@ struct Solver : SolverBase {
     c = ar.alloc<T>(n);
     k_convert<double, T><<<ew_grid(m), 256, 0, st>>>(sh_, h, m);
     k_convert<double, T><<<ew_grid(n), 256, 0, st>>>(sc_, c, n);
-    lo = ar.alloc<double>(nb);
-    hi = ar.alloc<double>(nb);
-    if (nb > 0) {
-      double* tmp = ar.alloc<double>(nb);
-      copy_in(tmp, hlo.data(), nb, st);
-      k_scale_vec<<<ew_grid(nb), 256, 0, st>>>(tmp, d2, nb, 1, lo);
+    lo = ar.alloc<double>(nbl);
+    hi = ar.alloc<double>(nbl);
+    if (nbl > 0) {
+      double* tmp = ar.alloc<double>(nbl);
+      copy_in(tmp, hlo.data(), nbl, st);
+      k_scale_vec<<<ew_grid(nbl), 256, 0, st>>>(tmp, d2, nbl, 1, lo);
       CK(cudaStreamSynchronize(st));
-      copy_in(tmp, hhi.data(), nb, st);
-      k_scale_vec<<<ew_grid(nb), 256, 0, st>>>(tmp, d2, nb, 1, hi);
+      copy_in(tmp, hhi.data(), nbl, st);
+      k_scale_vec<<<ew_grid(nbl), 256, 0, st>>>(tmp, d2, nbl, 1, hi);
       CK(cudaStreamSynchronize(st));
       ar.release(tmp);
     }
@@ -1233,6 +1265,273 @@ struct Solver : SolverBase {
   }
 };
 
+
+// ------------------------------------------------------------------ batch
+// Many independent problems as one block-diagonal problem: set up by the
+// ordinary set-up (column layout in segments), solved by k_batch (one CTA per
+// instance at a time).
+template <typename T>
+struct BatchSolver : BatchBase {
+  Solver<T> sv;
+  int64_t count = 0;
+  std::vector<BInst> hinst;
+  std::vector<int32_t> horder;
+  BInst* dinst = nullptr;
+  int32_t* dorder = nullptr;
+  Ctl* dctls = nullptr;
+  Ctl* dtmpl = nullptr;
+  unsigned int* dqueue = nullptr;
+  unsigned long long* dtimes = nullptr;
+  int64_t *soc_rs = nullptr, *soc_cs = nullptr, *exp_rs = nullptr, *exp_cs = nullptr;
+  int32_t *soc_rd = nullptr, *soc_cd = nullptr;
+  uint8_t *exp_risd = nullptr, *exp_cisd = nullptr;
+  int grid = 0;
+  double time_limit = 0.0;
+
+  template <typename U>
+  U* upload(const std::vector<U>& v) {
+    U* d = sv.ar.template alloc<U>((int64_t)v.size());
+    if (!v.empty()) copy_in(d, v.data(), (int64_t)v.size(), sv.st);
+    return d;
+  }
+
+  void setup(const pdcs_instance* in, int64_t cnt, const pdcs_options& o, cudaStream_t stream) {
+    count = cnt;
+    int64_t M = 0, N = 0, NNZ = 0;
+    std::vector<int64_t> nnz_i((size_t)cnt);
+    for (int64_t i = 0; i < cnt; ++i) {
+      int64_t last = 0;
+      CK(cudaMemcpy(&last, in[i].row_ptr + in[i].m, sizeof(int64_t), cudaMemcpyDefault));
+      nnz_i[i] = last;
+      M += in[i].m;
+      N += in[i].n;
+      NNZ += last;
+    }
+    std::vector<int64_t> rp((size_t)M + 1);
+    std::vector<int32_t> ci((size_t)NNZ);
+    std::vector<double> val((size_t)NNZ), h((size_t)M), c((size_t)N);
+    std::vector<double> lb((size_t)N, -INFINITY), ub((size_t)N, INFINITY);
+    std::vector<pdcs_cone> rcones;
+    std::vector<typename Solver<T>::ColSeg> segs;
+    std::vector<int64_t> srs, scs, ers, ecs;
+    std::vector<int32_t> srd, scd;
+    std::vector<uint8_t> erd, ecd;
+    hinst.resize((size_t)cnt);
+    int64_t r0 = 0, c0 = 0, e0 = 0;
+    rp[0] = 0;
+    for (int64_t i = 0; i < cnt; ++i) {
+      const pdcs_instance& I = in[i];
+      if (N + 0 > INT32_MAX) invalid("batch has more than 2^31 columns");
+      std::vector<int64_t> lrp((size_t)I.m + 1);
+      CK(cudaMemcpy(lrp.data(), I.row_ptr, sizeof(int64_t) * (I.m + 1), cudaMemcpyDefault));
+      const int64_t nz = nnz_i[i];
+      if (nz > 0) {
+        std::vector<int32_t> lci((size_t)nz);
+        CK(cudaMemcpy(lci.data(), I.col_idx, sizeof(int32_t) * nz, cudaMemcpyDefault));
+        CK(cudaMemcpy(val.data() + e0, I.val, sizeof(double) * nz, cudaMemcpyDefault));
+        for (int64_t e = 0; e < nz; ++e) {
+          if (lci[e] < 0 || lci[e] >= I.n) invalid("column index out of range in a batch instance");
+          ci[e0 + e] = (int32_t)(lci[e] + c0);
+        }
+      }
+      for (int64_t r = 0; r < I.m; ++r) rp[r0 + r + 1] = e0 + lrp[r + 1];
+      if (I.m > 0) CK(cudaMemcpy(h.data() + r0, I.h, sizeof(double) * I.m, cudaMemcpyDefault));
+      CK(cudaMemcpy(c.data() + c0, I.c, sizeof(double) * I.n, cudaMemcpyDefault));
+      if (I.nb > 0) {
+        CK(cudaMemcpy(lb.data() + c0, I.lb, sizeof(double) * I.nb, cudaMemcpyDefault));
+        CK(cudaMemcpy(ub.data() + c0, I.ub, sizeof(double) * I.nb, cudaMemcpyDefault));
+      }
+      BInst& b = hinst[(size_t)i];
+      b = BInst{};
+      b.r0 = r0; b.m = I.m; b.c0 = c0; b.n = I.n; b.tile = 32;
+      b.soc_r0 = (int32_t)srs.size(); b.exp_r0 = (int32_t)ers.size();
+      int64_t off = r0;
+      for (int64_t k = 0; k < I.n_row_cones; ++k) {
+        const pdcs_cone& cn = I.row_cones[k];
+        rcones.push_back(cn);
+        if (cn.type == PDCS_CONE_SOC || cn.type == PDCS_CONE_RSOC) {
+          if (cn.dim > kBatchThreads * kBatchSocEpt) throw Fail{PDCS_ERR_UNSUPPORTED, "batched SOC blocks are limited to 4096 elements"};
+          srs.push_back(off); srd.push_back((int32_t)cn.dim);
+        } else if (cn.type == PDCS_CONE_EXP || cn.type == PDCS_CONE_DUAL_EXP) {
+          ers.push_back(off); erd.push_back(cn.type == PDCS_CONE_DUAL_EXP ? 1 : 0);
+        }
+        off += cn.dim;
+      }
+      b.soc_rn = (int32_t)srs.size() - b.soc_r0; b.exp_rn = (int32_t)ers.size() - b.exp_r0;
+      typename Solver<T>::ColSeg sg;
+      sg.off = c0; sg.nb = I.nb; sg.end = c0 + I.n;
+      sg.cones.assign(I.col_cones, I.col_cones + I.n_col_cones);
+      segs.push_back(sg);
+      b.soc_c0 = (int32_t)scs.size(); b.exp_c0 = (int32_t)ecs.size();
+      off = c0 + I.nb;
+      for (int64_t k = 0; k < I.n_col_cones; ++k) {
+        const pdcs_cone& cn = I.col_cones[k];
+        if (cn.type == PDCS_CONE_SOC || cn.type == PDCS_CONE_RSOC) {
+          if (cn.dim > kBatchThreads * kBatchSocEpt) throw Fail{PDCS_ERR_UNSUPPORTED, "batched SOC blocks are limited to 4096 elements"};
+          scs.push_back(off); scd.push_back((int32_t)cn.dim);
+        } else if (cn.type == PDCS_CONE_EXP || cn.type == PDCS_CONE_DUAL_EXP) {
+          ecs.push_back(off); ecd.push_back(cn.type == PDCS_CONE_DUAL_EXP ? 1 : 0);
+        }
+        off += cn.dim;
+      }
+      b.soc_cn = (int32_t)scs.size() - b.soc_c0; b.exp_cn = (int32_t)ecs.size() - b.exp_c0;
+      r0 += I.m;
+      c0 += I.n;
+      e0 += nz;
+    }
+    pdcs_options so = o;
+    so.eager = 1;    // the batch runs its own kernel: no single-problem graphs
+    so.profile = 0;
+    so.trace_capacity = 0;
+    time_limit = o.time_limit;
+    const std::vector<pdcs_cone> none;
+    sv.setup(M, N, rp.data(), ci.data(), val.data(), h.data(), c.data(), 0, lb.data(), ub.data(),
+             rcones, none, so, stream, &segs);
+    soc_rs = upload(srs); soc_rd = upload(srd); soc_cs = upload(scs); soc_cd = upload(scd);
+    exp_rs = upload(ers); exp_risd = upload(erd); exp_cs = upload(ecs); exp_cisd = upload(ecd);
+    // queue order: most nonzeros first
+    horder.resize((size_t)cnt);
+    for (int64_t i = 0; i < cnt; ++i) horder[i] = (int32_t)i;
+    std::stable_sort(horder.begin(), horder.end(),
+                     [&](int32_t a, int32_t b) { return nnz_i[a] > nnz_i[b]; });
+    dorder = sv.ar.template alloc<int32_t>(cnt);
+    dinst = sv.ar.template alloc<BInst>(cnt);
+    dctls = sv.ar.template alloc<Ctl>(cnt);
+    dtmpl = sv.ar.template alloc<Ctl>(1);
+    dqueue = sv.ar.template alloc<unsigned int>(1);
+    dtimes = sv.ar.template alloc<unsigned long long>(2 * cnt);
+    sv.init_ctl();
+    CK(cudaMemcpyAsync(dtmpl, sv.hctl, sizeof(Ctl), cudaMemcpyHostToDevice, sv.st));
+    int dev = 0, sms = 0, occ = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<T>, kBatchThreads, 0));
+    grid = std::max(1, sms * std::max(1, occ));
+    autotune(nnz_i);
+  }
+
+  BatchArgs<T> args(int32_t n_queue) {
+    BatchArgs<T> a;
+    a.p = sv.prob();
+    a.p.tm = nullptr;
+    a.rp = sv.rp; a.rpT = sv.rpT; a.ci = sv.ci; a.ciT = sv.ciT; a.vv = sv.vv; a.vvT = sv.vvT;
+    a.x = sv.x; a.y = sv.y; a.xh = sv.xh; a.yh = sv.yh; a.gx = sv.gx; a.gty = sv.gty;
+    a.gxh = sv.gxh; a.gtyh = sv.gtyh; a.x0 = sv.x0; a.y0 = sv.y0; a.gx0 = sv.gx0; a.gty0 = sv.gty0;
+    a.xb = sv.xb; a.yb = sv.yb; a.gxb = sv.gxb; a.gtyb = sv.gtyb;
+    a.xc = sv.xc; a.yc = sv.yc; a.gxc = sv.gxc; a.gtyc = sv.gtyc;
+    a.xs = sv.xs; a.ys = sv.ys;
+    for (int k = 0; k < 2; ++k) {
+      a.tm[k] = sv.tm[k]; a.tn[k] = sv.tn[k]; a.um[k] = sv.um[k]; a.un[k] = sv.un[k];
+      a.px[k] = sv.px[k]; a.py[k] = sv.py[k];
+    }
+    a.soc_rs = soc_rs; a.soc_cs = soc_cs; a.soc_rd = soc_rd; a.soc_cd = soc_cd;
+    a.exp_rs = exp_rs; a.exp_cs = exp_cs; a.exp_risd = exp_risd; a.exp_cisd = exp_cisd;
+    a.inst = dinst; a.order = dorder; a.count = n_queue; a.ctls = dctls; a.tmpl = dtmpl;
+    a.queue = dqueue; a.times = dtimes; a.time_limit_s = time_limit;
+    return a;
+  }
+
+  void launch(int32_t n_queue) {
+    CK(cudaMemsetAsync(dqueue, 0, sizeof(unsigned int), sv.st));
+    k_batch<T><<<grid, kBatchThreads, 0, sv.st>>>(args(n_queue));
+    CK(cudaGetLastError());
+  }
+
+  // Lanes per row of the products, per size bucket (columns < 256, < 512,
+  // < 1024, larger): a few instances of the bucket are solved for three check
+  // periods with each candidate, and the fastest is kept.
+  void autotune(const std::vector<int64_t>& nnz_i) {
+    const int tiles[4] = {4, 8, 16, 32};
+    const int64_t edges[4] = {256, 512, 1024, INT64_MAX};
+    auto bucket = [&](int64_t i) {
+      int b = 0;
+      while (hinst[i].n >= edges[b]) ++b;
+      return b;
+    };
+    Ctl short_tmpl = *sv.hctl;
+    short_tmpl.max_iter = std::max<long long>(1, 3 * short_tmpl.check_freq);
+    CK(cudaMemcpyAsync(dtmpl, &short_tmpl, sizeof(Ctl), cudaMemcpyHostToDevice, sv.st));
+    int best[4] = {32, 32, 32, 32};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int b = 0; b < 4; ++b) {
+      std::vector<int32_t> sample;
+      for (int64_t q = 0; q < count && (int)sample.size() < 4; ++q)
+        if (bucket(horder[q]) == b) sample.push_back(horder[q]);
+      if (sample.empty()) continue;
+      float best_ms = 1e30f;
+      for (int t : tiles) {
+        for (int32_t i : sample) hinst[i].tile = t;
+        CK(cudaMemcpyAsync(dinst, hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, sv.st));
+        CK(cudaMemcpyAsync(dorder, sample.data(), sizeof(int32_t) * sample.size(), cudaMemcpyHostToDevice, sv.st));
+        CK(cudaEventRecord(e0, sv.st));
+        launch((int32_t)sample.size());
+        CK(cudaEventRecord(e1, sv.st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) { best_ms = ms; best[b] = t; }
+      }
+    }
+    CK(cudaEventDestroy(e0));
+    CK(cudaEventDestroy(e1));
+    for (int64_t i = 0; i < count; ++i) hinst[i].tile = best[bucket(i)];
+    CK(cudaMemcpyAsync(dinst, hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, sv.st));
+    CK(cudaMemcpyAsync(dorder, horder.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, sv.st));
+    CK(cudaMemcpyAsync(dtmpl, sv.hctl, sizeof(Ctl), cudaMemcpyHostToDevice, sv.st));
+    CK(cudaStreamSynchronize(sv.st));
+    for (int b = 0; b < 4; ++b) tile_of_bucket[b] = best[b];
+  }
+  int tile_of_bucket[4] = {32, 32, 32, 32};
+
+  void solve(double* xo, double* yo, double* so, pdcs_result* res, double* finish_s) override {
+    sv.order_after_user();
+    launch((int32_t)count);
+    const Prob<T> p = sv.prob();
+    const int gmx = ew_grid(std::max(sv.m, sv.n));
+    k_unscale<T><<<gmx, 256, 0, sv.st>>>(p, sv.xc, sv.yc, sv.gxc, sv.obuf_n, sv.obuf_m, sv.obuf_s);
+    if (sv.ncol_rot) k_rotate_pairs<<<ew_grid(sv.ncol_rot), 256, 0, sv.st>>>(sv.obuf_n, sv.col_rot, sv.ncol_rot);
+    if (sv.nrow_rot) {
+      k_rotate_pairs<<<ew_grid(sv.nrow_rot), 256, 0, sv.st>>>(sv.obuf_m, sv.row_rot, sv.nrow_rot);
+      k_rotate_pairs<<<ew_grid(sv.nrow_rot), 256, 0, sv.st>>>(sv.obuf_s, sv.row_rot, sv.nrow_rot);
+    }
+    CK(cudaGetLastError());
+    if (xo) CK(cudaMemcpyAsync(xo, sv.obuf_n, sizeof(double) * sv.n, cudaMemcpyDefault, sv.st));
+    if (yo && sv.m) CK(cudaMemcpyAsync(yo, sv.obuf_m, sizeof(double) * sv.m, cudaMemcpyDefault, sv.st));
+    if (so && sv.m) CK(cudaMemcpyAsync(so, sv.obuf_s, sizeof(double) * sv.m, cudaMemcpyDefault, sv.st));
+    std::vector<Ctl> hc((size_t)count);
+    std::vector<unsigned long long> ht((size_t)(2 * count));
+    CK(cudaMemcpyAsync(hc.data(), dctls, sizeof(Ctl) * count, cudaMemcpyDeviceToHost, sv.st));
+    CK(cudaMemcpyAsync(ht.data(), dtimes, sizeof(unsigned long long) * 2 * count, cudaMemcpyDeviceToHost, sv.st));
+    CK(cudaStreamSynchronize(sv.st));
+    unsigned long long t0 = ~0ull;
+    for (int64_t i = 0; i < count; ++i) t0 = std::min(t0, ht[2 * i]);
+    for (int64_t i = 0; i < count; ++i) {
+      const Ctl& c = hc[i];
+      if (res) {
+        pdcs_result& r = res[i];
+        std::memset(&r, 0, sizeof(r));
+        const PointStats& s3 = c.st[3];
+        r.exit_code = c.status;
+        r.pobj = s3.pobj;
+        r.dobj = s3.dobj;
+        r.err_rel_p = s3.inf_rel_p;
+        r.err_rel_d = s3.inf_rel_d;
+        r.err_rel_gap = s3.inf_rel_gap;
+        r.err_abs_p = s3.inf_abs_p;
+        r.err_abs_d = s3.inf_abs_d;
+        r.err_abs_gap = s3.gap;
+        r.iters = c.iter;
+        r.attempts = c.kbar;
+        r.restarts = c.restarts;
+        r.solve_time_s = 1e-9 * (double)(ht[2 * i + 1] - ht[2 * i]);
+      }
+      if (finish_s) finish_s[i] = 1e-9 * (double)(ht[2 * i + 1] - t0);
+    }
+  }
+};
+
 }  // namespace pdcs
 
 // ----------------------------------------------------------------- C ABI
@@ -1401,11 +1700,70 @@ int pdcs_get_sizes(pdcs_handle* hd, int64_t* m, int64_t* n, int64_t* nnz) {
   return PDCS_OK;
 }
 
+int pdcs_setup_batch(pdcs_handle** out, const pdcs_instance* inst, int64_t count,
+                     const pdcs_options* opt, void* cuda_stream) {
+  if (!out) return fail(PDCS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !inst) return fail(PDCS_ERR_INVALID, "need count >= 1 instances");
+  for (int64_t i = 0; i < count; ++i) {
+    const pdcs_instance& I = inst[i];
+    if (I.m < 0 || I.n < 1 || I.nb < 0 || I.nb > I.n)
+      return fail(PDCS_ERR_INVALID, "batch instance " + std::to_string(i) + ": bad sizes");
+    if (!I.row_ptr || (I.m > 0 && !I.h) || !I.c || (I.nb > 0 && (!I.lb || !I.ub)))
+      return fail(PDCS_ERR_INVALID, "batch instance " + std::to_string(i) + ": missing array");
+    if ((I.n_row_cones > 0 && !I.row_cones) || (I.n_col_cones > 0 && !I.col_cones) ||
+        I.n_row_cones < 0 || I.n_col_cones < 0)
+      return fail(PDCS_ERR_INVALID, "batch instance " + std::to_string(i) + ": bad cone list");
+    int rc_ = check_cones(I.row_cones, I.n_row_cones, I.m, "row");
+    if (rc_ != PDCS_OK) return rc_;
+    rc_ = check_cones(I.col_cones, I.n_col_cones, I.n - I.nb, "column");
+    if (rc_ != PDCS_OK) return rc_;
+  }
+  pdcs_options o;
+  if (opt) o = *opt; else pdcs_default_options(&o);
+  if (o.precision != 0 && o.precision != 1) return fail(PDCS_ERR_INVALID, "precision must be 0 or 1");
+  if (o.check_freq < 1 || o.max_iter < 1 || o.ruiz_iters < 0 || !(o.bisect_rel_tol > 0.0) ||
+      (o.method != 0 && o.method != 1))
+    return fail(PDCS_ERR_INVALID, "invalid options");
+  pdcs_handle* hd = new pdcs_handle();
+  try {
+    CK(cudaGetDevice(&hd->device));
+    if (o.precision == 0) {
+      auto* b = new BatchSolver<double>();
+      hd->batch = b;
+      b->setup(inst, count, o, (cudaStream_t)cuda_stream);
+    } else {
+      auto* b = new BatchSolver<float>();
+      hd->batch = b;
+      b->setup(inst, count, o, (cudaStream_t)cuda_stream);
+    }
+  } catch (const Fail& f) {
+    delete hd->batch;
+    delete hd;
+    return fail(f.code, f.msg);
+  }
+  *out = hd;
+  return PDCS_OK;
+}
+
+int pdcs_solve_batch(pdcs_handle* hd, double* x, double* y, double* s, pdcs_result* res,
+                     double* finish_s) {
+  if (!hd || !hd->batch) return fail(PDCS_ERR_INVALID, "not a batch handle");
+  try {
+    CK(cudaSetDevice(hd->device));
+    hd->batch->solve(x, y, s, res, finish_s);
+  } catch (const Fail& f) {
+    return fail(f.code, f.msg);
+  }
+  return PDCS_OK;
+}
+
 void pdcs_free(pdcs_handle* hd) {
   if (!hd) return;
-  if (hd->solver) {
+  if (hd->solver || hd->batch) {
     cudaSetDevice(hd->device);
     delete hd->solver;
+    delete hd->batch;
   }
   delete hd;
 }

@@ -32,7 +32,8 @@ def test_library_exports_every_declared_function():
 def test_struct_layouts_match_header():
     structs = {"pdcs_cone": P.PdcsCone, "pdcs_options": P.PdcsOptions,
                "pdcs_result": P.PdcsResult, "pdcs_state": P.PdcsState,
-               "pdcs_profile": P.PdcsProfile, "pdcs_mlp_config": P.PdcsMlpConfig}
+               "pdcs_profile": P.PdcsProfile, "pdcs_mlp_config": P.PdcsMlpConfig,
+               "pdcs_instance": P.PdcsInstance}
     src = ['#include <stdio.h>', '#include <stddef.h>', '#include "%s"' % HEADER, "int main(void){"]
     for cname, cls in structs.items():
         src.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
