@@ -57,6 +57,9 @@ def _args():
     ap.add_argument("--n", type=int, default=200_000)
     ap.add_argument("--k", type=int, default=200)
     ap.add_argument("--limits", type=int, default=1000)
+    ap.add_argument("--workload", default="portfolio", choices=["portfolio", "logistic"],
+                    help="portfolio: the factor-model SOCP (the headline); logistic: the "
+                         "L1-logistic regression with 200,000 exponential cones")
     ap.add_argument("--tts-cap", type=float, default=90.0,
                     help="time limit (s) of the time-to-tolerance solve; 0 skips it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -76,6 +79,12 @@ def _dist():
 
 def _workload(args, rank):
     import workloads
+    if getattr(args, "workload", "portfolio") == "logistic":
+        p = workloads.logistic_l1(seed=20260103 + rank)
+        desc = ("L1-logistic regression in exponential-cone form, 100000 samples x 2000 "
+                "features (m=%d, n=%d, nnz=%d, %d exponential cones), %s"
+                % (p["m"], p["n"], len(p["val"]), 2 * 100000, args.precision.upper()))
+        return p, desc
     p = workloads.portfolio(n=args.n, k=args.k, n_limits=args.limits, seed=20260102 + rank)
     desc = ("factor-model portfolio SOCP n=%d k=%d limits=%d (m=%d, n=%d, nnz=%d), %s"
             % (args.n, args.k, args.limits, p["m"], p["n"], len(p["val"]), args.precision.upper()))
@@ -312,7 +321,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": 1000.0 * tmax / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else "f32",
-                "data": "synthetic (seeded factor-model portfolio generator)",
+                "data": "synthetic (seeded %s generator)" % (
+                    "L1-logistic" if args.workload == "logistic" else "factor-model portfolio"),
                 "config": {"workload": desc, "step": "%d accepted PDHG iterations + 1 restart check"
                            % CHECK_FREQ, "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (two CSR copies of G, %.0f MB)"
