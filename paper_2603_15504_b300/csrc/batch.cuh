@@ -110,9 +110,10 @@ PDCS_DEV void b_proj_exp(B* v, const int64_t* __restrict__ starts, const uint8_t
   for (int j = threadIdx.x; j < count; j += blockDim.x) {
     const int64_t s = starts[first + j];
     const double in[3] = {(double)v[s], (double)v[s + 1], (double)v[s + 2]};
-    const double e[3] = {cone_scale(d, s, inv), cone_scale(d, s + 1, inv), cone_scale(d, s + 2, inv)};
+    double e[3], ie[3];
+    cone_scale_pair(d, s, inv, e, ie);
     double out[3];
-    proj_exp_family(in, e, (isd[first + j] != 0) != (dual != 0), out);
+    proj_exp_family(in, e, ie, (isd[first + j] != 0) != (dual != 0), out);
     v[s] = (B)out[0];
     v[s + 1] = (B)out[1];
     v[s + 2] = (B)out[2];

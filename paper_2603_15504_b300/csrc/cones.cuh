@@ -120,11 +120,37 @@ PDCS_HD double exp_ray_point(double r, const double p[3], const double e[3], dou
   return (p[0] - c[0]) * (p[0] - c[0]) + (p[1] - c[1]) * (p[1] - c[1]) + (p[2] - c[2]) * (p[2] - c[2]);
 }
 
-// Projection of p onto diag(e) K_exp.
-PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], double q[3]) {
-  const double u0 = p[0] / e[0], u1 = p[1] / e[1], u2 = p[2] / e[2];
-  if (exp_member(u0, u1, u2)) { q[0] = p[0]; q[1] = p[1]; q[2] = p[2]; return; }
-  if (exp_dual_member(-e[0] * p[0], -e[1] * p[1], -e[2] * p[2])) {
+// Membership tests screened in FP32: the FP32 value of the defining
+// inequality decides unless it lies within a relative margin of the boundary,
+// where the FP64 test decides (so the decisions are those of the FP64 tests,
+// which cost logarithms in the scarce FP64 pipe).
+PDCS_HD bool exp_member_fast(double x, double y, double z) {
+  if (y > 0.0 && z > 0.0) {
+    const float xf = (float)x, yf = (float)y, zf = (float)z;
+    const float l = yf * logf(zf / yf);
+    const float t = l - xf;
+    if (fabsf(t) > 1e-4f * (fabsf(xf) + fabsf(l)) + 1e-30f && isfinite(t)) return t >= 0.0f;
+  }
+  return exp_member(x, y, z);
+}
+
+PDCS_HD bool exp_dual_member_fast(double u, double v, double w) {
+  if (u < 0.0 && w > 0.0) {
+    const float uf = (float)u, vf = (float)v, wf = (float)w;
+    const float a = logf(-uf), b = vf / uf, c = logf(wf);
+    const float t = 1.0f + c - a - b;
+    if (fabsf(t) > 1e-4f * (fabsf(a) + fabsf(b) + 1.0f + fabsf(c)) && isfinite(t)) return t >= 0.0f;
+  }
+  return exp_dual_member(u, v, w);
+}
+
+// Projection of p onto diag(e) K_exp (ie = 1 / e, elementwise).
+PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], const double ie[3], double q[3]) {
+  if (exp_member_fast(p[0] * ie[0], p[1] * ie[1], p[2] * ie[2])) {
+    q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+    return;
+  }
+  if (exp_dual_member_fast(-e[0] * p[0], -e[1] * p[1], -e[2] * p[2])) {
     q[0] = q[1] = q[2] = 0.0;
     return;
   }
@@ -155,28 +181,40 @@ PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], double q[3]) 
     }
     const double P0 = e[0] * p[0], P1 = e[1] * p[1], P2 = e[2] * p[2];
     const double S0 = e[0] * e[0], S1 = e[1] * e[1], S2 = e[2] * e[2];
+    const float P0f = (float)P0, P1f = (float)P1, P2f = (float)P2;
+    const float S0f = (float)S0, S1f = (float)S1, S2f = (float)S2;
     for (int pass = 0; pass < 2; ++pass) {
       const int bi = pass == 0 ? i1 : i2;
       if (bi < 0) continue;
-      const double rb = (double)exp_grid_r(bi);
+      const float rbf = exp_grid_r(bi);
+      const double rb = (double)rbf;
+      // neighbourhood of the grid maximum: phi rises then falls in it, so
+      // g > 0 at its left end and g < 0 at its right end
+      const double lo_n = bi > 0 ? (double)exp_grid_r(bi - 1) : rb;
+      const double hi_n = bi < kExpGrid - 1 ? (double)exp_grid_r(bi + 1) : rb;
       double c[3];
-      double dd = exp_ray_point(rb, p, e, c);
-      if (dd < bd) { best[0] = c[0]; best[1] = c[1]; best[2] = c[2]; bd = dd; }
-      // the local maximum lies on the side where phi increases
-      double g, dg;
-      exp_g<double>(rb, P0, P1, P2, S0, S1, S2, g, dg);
-      double lo, hi;
-      if (g > 0.0) { lo = rb; hi = bi < kExpGrid - 1 ? (double)exp_grid_r(bi + 1) : rb; }
-      else { hi = rb; lo = bi > 0 ? (double)exp_grid_r(bi - 1) : rb; }
-      if (!(hi > lo)) continue;
-      const float P0f = (float)P0, P1f = (float)P1, P2f = (float)P2;
-      const float S0f = (float)S0, S1f = (float)S1, S2f = (float)S2;
-      float rf = exp_newton<float>((float)(0.5 * (lo + hi)), (float)lo, (float)hi, P0f, P1f, P2f,
-                                   S0f, S1f, S2f, 40, 1e-6f);
-      double r = (double)rf;
-      if (!(r > lo && r < hi)) r = 0.5 * (lo + hi);
-      r = exp_newton<double>(r, lo, hi, P0, P1, P2, S0, S1, S2, 12, 1e-15);
-      dd = exp_ray_point(r, p, e, c);
+      if (!(hi_n > lo_n)) {
+        const double dd = exp_ray_point(rb, p, e, c);
+        if (dd < bd) { best[0] = c[0]; best[1] = c[1]; best[2] = c[2]; bd = dd; }
+        continue;
+      }
+      // FP32: the side of the maximum, then Newton to FP32 accuracy
+      float gf, dgf;
+      exp_g<float>(rbf, P0f, P1f, P2f, S0f, S1f, S2f, gf, dgf);
+      const float lof = gf > 0.0f ? rbf : (float)lo_n, hif = gf > 0.0f ? (float)hi_n : rbf;
+      double r = rb;
+      if (hif > lof) {
+        const float rf = exp_newton<float>(0.5f * (lof + hif), lof, hif, P0f, P1f, P2f, S0f, S1f,
+                                           S2f, 40, 1e-6f);
+        r = (double)rf;
+      }
+      if (!(r > lo_n && r < hi_n)) r = 0.5 * (lo_n + hi_n);
+      // FP64 polish in the whole neighbourhood: Newton converges
+      // quadratically, so after a step below 1e-6 (1 + |r|) the root is
+      // accurate far beyond what the candidate comparison needs
+      r = exp_newton<double>(r, lo_n, hi_n, P0, P1, P2, S0, S1, S2, 12, 1e-6);
+      double dd = exp_ray_point(r, p, e, c);
+      if (!(dd < INFINITY)) dd = exp_ray_point(rb, p, e, c);
       if (dd < bd) { best[0] = c[0]; best[1] = c[1]; best[2] = c[2]; bd = dd; }
     }
   }
@@ -184,13 +222,13 @@ PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], double q[3]) 
 }
 
 // Projection onto diag(e) K' where K' = K_exp (dual == false) or K_exp^* (dual ==
-// true, via Moreau: P_{E K*}(v) = v + P_{E^{-1} K}(-v)).
-PDCS_HD void proj_exp_family(const double v[3], const double e[3], bool dual, double out[3]) {
-  if (!dual) { proj_exp_scaled(v, e, out); return; }
+// true, via Moreau: P_{E K*}(v) = v + P_{E^{-1} K}(-v)); ie = 1 / e.
+PDCS_HD void proj_exp_family(const double v[3], const double e[3], const double ie[3], bool dual,
+                             double out[3]) {
+  if (!dual) { proj_exp_scaled(v, e, ie, out); return; }
   const double nv[3] = {-v[0], -v[1], -v[2]};
-  const double ie[3] = {1.0 / e[0], 1.0 / e[1], 1.0 / e[2]};
   double q[3];
-  proj_exp_scaled(nv, ie, q);
+  proj_exp_scaled(nv, ie, e, q);
   out[0] = v[0] + q[0]; out[1] = v[1] + q[1]; out[2] = v[2] + q[2];
 }
 

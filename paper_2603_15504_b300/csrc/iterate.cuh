@@ -206,6 +206,18 @@ PDCS_DEV double cone_scale(const double* d, int64_t i, int inv) {
   return inv ? 1.0 / d[i] : d[i];
 }
 
+// e = d or 1/d (inv) or 1 (d == NULL) for the 3-block at s, and ie = 1 / e
+// (one division per element).
+PDCS_DEV void cone_scale_pair(const double* d, int64_t s, int inv, double (&e)[3], double (&ie)[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (d == nullptr) { e[k] = ie[k] = 1.0; continue; }
+    const double di = d[s + k], r = 1.0 / di;
+    e[k] = inv ? r : di;
+    ie[k] = inv ? di : r;
+  }
+}
+
 // Exponential-cone blocks: one thread per 3-vector.  Target cone diag(e) K' with
 // e = d or 1/d (inv) and K' = K_exp or K_exp^* (is_dual_exp[b] xor dual).
 // blockIdx.y selects one of two vectors (each with its own gate).
@@ -224,9 +236,10 @@ __global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
   if (on) PDCS_GRID_LOOP(b, count) {
     const int64_t s = starts[b];
     const double in[3] = {(double)v[s], (double)v[s + 1], (double)v[s + 2]};
-    const double e[3] = {cone_scale(d, s, inv), cone_scale(d, s + 1, inv), cone_scale(d, s + 2, inv)};
+    double e[3], ie[3];
+    cone_scale_pair(d, s, inv, e, ie);
     double out[3];
-    proj_exp_family(in, e, (isd[b] != 0) != (dual != 0), out);
+    proj_exp_family(in, e, ie, (isd[b] != 0) != (dual != 0), out);
     v[s] = (B)out[0];
     v[s + 1] = (B)out[1];
     v[s + 2] = (B)out[2];
