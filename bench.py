@@ -301,6 +301,19 @@ def run_ours(args):
                "iters": rt["iters"], "attempts": rt["attempts"], "restarts": rt["restarts"],
                "rel_kkt": max(rt["err_rel_p"], rt["err_rel_d"], rt["err_rel_gap"]),
                "status": rt["status"], "time_cap_s": args.tts_cap}
+        if args.precision == "fp32":
+            # error of the FP32-bulk result against the FP64 path (the path the
+            # parity tests tie to the FP64 oracle), same instance and cap
+            with P.Solver(prob, **dict(opts, precision="fp64", time_limit=args.tts_cap,
+                                       max_iter=2**62, profile=0)) as s64:
+                r64 = s64.solve()
+            def rel(a, b):
+                return float(np.linalg.norm(a - b) / max(1e-300, np.linalg.norm(b)))
+            tts["error_vs_fp64"] = {
+                "pobj_rel": abs(rt["pobj"] - r64["pobj"]) / (1.0 + abs(r64["pobj"])),
+                "x_rel": rel(rt["x"], r64["x"]), "y_rel": rel(rt["y"], r64["y"]),
+                "fp64_rel_kkt": max(r64["err_rel_p"], r64["err_rel_d"], r64["err_rel_gap"]),
+                "fp64_reached": r64["exit_code"] == 0}
     s.close()
 
     cpu = None

@@ -171,14 +171,24 @@ __device__ inline void load_block(uint8_t* dst, const __nv_bfloat16* __restrict_
 #endif
 
 // C = A * B^T with the epilogue; A: M x K (lda), B: N x K (ldb), K, lda, ldb
-// multiples of 8, A and B 16-byte aligned.  Grid: (ceil(N / 128), ceil(M / 128)).
+// multiples of 8, A and B 16-byte aligned.  Grid: (ceil(N / 128), ceil(M / 128),
+// splits).  Split-K (kchunk > 0, a multiple of 64): CTA z multiplies the K
+// slice [z kchunk, (z + 1) kchunk) and writes its FP32 partial tile (EPI_F32)
+// at ep.out + z * zstride floats; k_splitk_reduce adds the slices.
 // err: set to 1 if an mbarrier wait expired (the tile is then not written).
 __global__ void __launch_bounds__(kThreads) k_gemm_bf16_tn(const __nv_bfloat16* __restrict__ A,
                                                            const __nv_bfloat16* __restrict__ B,
                                                            int64_t M, int64_t N, int64_t K,
                                                            int64_t lda, int64_t ldb, EpiArgs ep,
-                                                           int* err) {
+                                                           int* err, int64_t kchunk, int64_t zstride) {
 #ifdef __CUDA_ARCH__
+  if (kchunk > 0) {
+    const int64_t kz = (int64_t)blockIdx.z * kchunk;
+    A += kz;
+    B += kz;
+    K = K - kz < kchunk ? K - kz : kchunk;
+    ep.out = reinterpret_cast<float*>(ep.out) + (int64_t)blockIdx.z * zstride;
+  }
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned stages: A0 B0 A1 B1
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -274,6 +284,27 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16_tn(const __nv_bfloat16* 
                  : "memory");
   }
 #endif
+}
+
+// Split-K epilogue: v = sum over the slices z (in order) of part[z][r][c], then
+// the epilogue of ep (r < M, c < N; the slices have leading dimension N).
+__global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int64_t M, int64_t N,
+                                int64_t zstride, EpiArgs ep) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M * N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / N, c = i - r * N;
+    float v = 0.0f;
+    for (int z = 0; z < splits; ++z) v += part[z * zstride + i];
+    if (ep.kind == EPI_F32) {
+      reinterpret_cast<float*>(ep.out)[r * ep.ldc + c] = v;
+    } else if (ep.kind == EPI_F32_BIAS) {
+      reinterpret_cast<float*>(ep.out)[r * ep.ldc + c] = v + ep.bias[c];
+    } else {
+      if (ep.kind == EPI_BF16_BIAS_RELU) v = fmaxf(v + ep.bias[c], 0.0f);
+      else if (__bfloat162float(ep.mask[r * ep.ldm + c]) <= 0.0f) v = 0.0f;
+      reinterpret_cast<__nv_bfloat16*>(ep.out)[r * ep.ldc + c] = __float2bfloat16(v);
+    }
+  }
 }
 
 // Dynamic shared memory of k_gemm_bf16_tn (two stages of A and B, plus the

@@ -129,12 +129,20 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ Y, const 
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void k_loss_finish(const double* __restrict__ part, int nparts, double denom,
-                              double* __restrict__ loss) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One CTA of 256 threads: thread t adds partials t, t + 256, ... in order,
+// then a fixed tree (deterministic).
+__global__ void __launch_bounds__(256) k_loss_finish(const double* __restrict__ part, int nparts,
+                                                     double denom, double* __restrict__ loss) {
+  __shared__ double sh[256];
   double s = 0.0;
-  for (int i = 0; i < nparts; ++i) s += part[i];
-  *loss = s / denom;
+  for (int i = threadIdx.x; i < nparts; i += 256) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = sh[0] / denom;
 }
 
 // db[c] = sum over rows of G[r, c] (FP32 or BF16 G), rows in order.
@@ -294,12 +302,36 @@ struct Mlp {
     k_transpose_bf16<<<g, dim3(32, 8), 0, st>>>(src, rows, cols, lds, dst, ldd);
   }
 
+  // Split-K when the output has fewer tiles than SMs and K is long: about two
+  // CTAs per SM in all, each slice at least 8 K blocks; the FP32 partial
+  // tiles go to `splitws` and k_splitk_reduce applies the epilogue.
+  float* splitws = nullptr;
+  int64_t splitws_len = 0;
+
   void gemm(const __nv_bfloat16* A, const __nv_bfloat16* Bm, int64_t M, int64_t N, int64_t K,
             int64_t lda, int64_t ldb, EpiArgs ep) {
-    dim3 g((unsigned)((N + pdcs::tc::kTileN - 1) / pdcs::tc::kTileN),
-           (unsigned)((M + pdcs::tc::kTileM - 1) / pdcs::tc::kTileM));
-    pdcs::tc::k_gemm_bf16_tn<<<g, pdcs::tc::kThreads, pdcs::tc::kGemmSmem, st>>>(A, Bm, M, N, K, lda,
-                                                                                 ldb, ep, err);
+    const int64_t tn = (N + pdcs::tc::kTileN - 1) / pdcs::tc::kTileN;
+    const int64_t tm = (M + pdcs::tc::kTileM - 1) / pdcs::tc::kTileM;
+    const int64_t nkb = (K + pdcs::tc::kTileK - 1) / pdcs::tc::kTileK;
+    int64_t splits = 1;
+    if (tn * tm < 148 && nkb >= 16) splits = std::min<int64_t>(nkb / 8, (2 * 148 + tn * tm - 1) / (tn * tm));
+    if (splits <= 1) {
+      pdcs::tc::k_gemm_bf16_tn<<<dim3((unsigned)tn, (unsigned)tm), pdcs::tc::kThreads,
+                                 pdcs::tc::kGemmSmem, st>>>(A, Bm, M, N, K, lda, ldb, ep, err, 0, 0);
+      return;
+    }
+    const int64_t kchunk = (nkb + splits - 1) / splits * pdcs::tc::kTileK;
+    splits = (K + kchunk - 1) / kchunk;
+    const int64_t zstride = M * N;
+    if (splits * zstride > splitws_len) {
+      splitws_len = splits * zstride;
+      splitws = alloc<float>(splitws_len);
+    }
+    EpiArgs part{pdcs::tc::EPI_F32, splitws, N, nullptr, nullptr, 0};
+    pdcs::tc::k_gemm_bf16_tn<<<dim3((unsigned)tn, (unsigned)tm, (unsigned)splits), pdcs::tc::kThreads,
+                               pdcs::tc::kGemmSmem, st>>>(A, Bm, M, N, K, lda, ldb, part, err, kchunk,
+                                                          zstride);
+    pdcs::tc::k_splitk_reduce<<<grid_for(M * N), 256, 0, st>>>(splitws, (int)splits, M, N, zstride, ep);
   }
 
   void check_err() {
@@ -340,7 +372,7 @@ struct Mlp {
     const int nl = (int)L.size();
     const int np = (int)grid_for(B * cfg.out_dim);
     k_mse<<<np, 256, 0, st>>>(Y, T, B, cfg.out_dim, dY, dpre[nl], up8(cfg.out_dim), part);
-    k_loss_finish<<<1, 32, 0, st>>>(part, np, (double)B * (double)cfg.out_dim, loss);
+    k_loss_finish<<<1, 256, 0, st>>>(part, np, (double)B * (double)cfg.out_dim, loss);
     for (int l = nl - 1; l >= 0; --l) {
       Layer& y = L[l];
       const __nv_bfloat16* Gb = dpre[l + 1];  // dLoss / d(pre-activation of layer l), B x dout

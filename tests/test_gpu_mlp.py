@@ -49,12 +49,16 @@ def _ref_forward_bf16(params, X):
 
 
 DIMS = [300, 136, 136, 200]  # ragged sizes: partial 128-tiles and 64-wide K blocks
+# long K with few output tiles: the first layer's forward product and the
+# backward product through the last layer take the split-K path
+DIMS_SPLIT = [2000, 136, 136, 4000]
 
 
-def test_forward_matches_the_reference():
+@pytest.mark.parametrize("dims", [DIMS, DIMS_SPLIT])
+def test_forward_matches_the_reference(dims):
     P = _P()
-    net, params, rng = _net(P, DIMS, 40)
-    X = rng.standard_normal((40, DIMS[0]))
+    net, params, rng = _net(P, dims, 40)
+    X = rng.standard_normal((40, dims[0]))
     with net:
         Y = net.predict(X)
     R = _ref_forward_bf16(params, X)
@@ -65,11 +69,12 @@ def _cos(a, b):
     return float(np.dot(a.ravel(), b.ravel()) / (np.linalg.norm(a) * np.linalg.norm(b)))
 
 
-def test_gradients_match_the_reference():
+@pytest.mark.parametrize("dims", [DIMS, DIMS_SPLIT])
+def test_gradients_match_the_reference(dims):
     P = _P()
-    net, params, rng = _net(P, DIMS, 40, seed=1)
-    X = rng.standard_normal((40, DIMS[0]))
-    T = rng.standard_normal((40, DIMS[-1]))
+    net, params, rng = _net(P, dims, 40, seed=1)
+    X = rng.standard_normal((40, dims[0]))
+    T = rng.standard_normal((40, dims[-1]))
     # reference gradients at the BF16-rounded point, with BF16 hidden activations
     Xb = bf16(X)
     _, grads = ref.gradients(params, Xb, T)
