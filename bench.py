@@ -77,6 +77,22 @@ def _dist():
     return ws, rank, local
 
 
+def _aggregate(elapsed, iters, ws, dev=None):
+    """Whole-job figures of the timed region: the maximum of the ranks'
+    barrier-bracketed times and the sum of their iterations (one instance per
+    rank, no data-path collective).  Works on any torch.distributed backend
+    (NCCL with CUDA tensors, gloo with CPU tensors)."""
+    if ws == 1:
+        return elapsed, iters
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(iters)], device=dev, dtype=torch.float64)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 def _workload(args, rank):
     import workloads
     if getattr(args, "workload", "portfolio") == "logistic":
@@ -235,15 +251,7 @@ def run_ours(args):
     ktimes = s.kernel_times()
     iters = r1["iters"] - it0
     attempts = r1["attempts"] - kb0
-    tmax = elapsed
-    it_all = iters
-    if ws > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-        c = torch.tensor([iters], device=dev, dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        it_all = int(c.item())
+    tmax, it_all = _aggregate(elapsed, iters, ws, dev)
     value = it_all / tmax
 
     # roofline of the dominant kernel (the two sparse products), measured live
