@@ -83,3 +83,15 @@ def test_invalid_arguments_rejected_before_device_work(patch, msg):
 def test_invalid_option_rejected():
     with pytest.raises(P.PdcsError, match="precision"):
         P.Solver(_tiny(), precision=3)
+
+
+def test_entry_point_build_reaches_the_library_build(monkeypatch):
+    """__graft_entry__.build() must call the compiler step of the package (the
+    package re-exports a function named build, which shadows the submodule)."""
+    import importlib
+    import __graft_entry__ as g
+    B = importlib.import_module("paper_2603_15504_b300.build")
+    calls = []
+    monkeypatch.setattr(B, "build", lambda force=False, verbose=False: calls.append((force, verbose)))
+    g.build()
+    assert calls == [(True, True)]
