@@ -139,10 +139,13 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
       ++r;
       continue;
     }
-    const int64_t max_rows = c == 0 ? 256 : (c == 1 ? 4 * (256 / small_g) : 32);
+    // kind 1: one row per lane group at least (the nonzero cap applies beyond that)
+    const int64_t groups = c == 1 ? kSpmvThreads / small_g : 1;
+    const int64_t max_rows = c == 0 ? 256 : (c == 1 ? 4 * groups : 32);
     const int64_t max_nnz = c == 2 ? 16384 : 8192;
     int64_t e = r, nnz = 0;
-    while (e < m && cls(e) == c && e - r < max_rows && (nnz == 0 || nnz + rp[e + 1] - rp[e] <= max_nnz)) {
+    while (e < m && cls(e) == c && e - r < max_rows &&
+           (nnz == 0 || e - r < groups || nnz + rp[e + 1] - rp[e] <= max_nnz)) {
       nnz += rp[e + 1] - rp[e];
       ++e;
     }

@@ -8,12 +8,16 @@
 //           else the smallest group whose loads still fill 32-byte sectors
 //           (G = 4 for FP64, 8 for FP32), which keeps the FP64 shuffle-add tree
 //           per row short (FP64 instructions are the scarce resource here);
+//           a task holds at least one row per group, so no group idles;
 //   kind 2  one chunk of <= kChunk nonzeros of a long row; the chunk sums are
 //           written to a partial buffer and the last chunk CTA of the row (an
 //           atomic ticket, no waiting) adds them in chunk order, so the result
 //           is deterministic.
 // Accumulation: FP64 in FP64 mode (one DFMA per nonzero); in FP32 mode FP32
 // products with a compensated (Kahan) FP32 sum per lane, combined in FP64.
+// Each lane issues the index, value and gather loads of kSpmvUnroll nonzeros
+// before it adds them (in their order, so the sum is the plain strided one):
+// the streams run near the read bandwidth only with that many loads in flight.
 #pragma once
 #include "common.cuh"
 
@@ -21,6 +25,7 @@ namespace pdcs {
 
 constexpr int kSpmvThreads = 256;
 constexpr int64_t kChunk = 8192;
+constexpr int kSpmvUnroll = 8;
 
 struct SpmvTask {
   int32_t kind;
@@ -75,7 +80,21 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
     Acc<T> acc;
     if (row < t.b) {
       const int64_t s = rp[row], e = rp[row + 1];
-      for (int64_t k = s + lane; k < e; k += G) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
+      constexpr int U = kSpmvUnroll;
+      int64_t k = s + lane;
+      for (; k + (U - 1) * G < e; k += U * G) {
+        int32_t c[U];
+        T v[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) c[u] = __ldg(ci + k + u * G);
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = __ldg(vv + k + u * G);
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc.add(v[u], xv[u]);
+      }
+      for (; k < e; k += G) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
     }
     const double r = group_sum<G>(acc.get());
     if (lane == 0 && row < t.b) y[row] = (T)r;
@@ -129,15 +148,18 @@ PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
   __shared__ double sh[kSpmvThreads + 1];
   Acc<T> acc;
   int64_t k = t.c + threadIdx.x;
-  for (; k + 3 * kSpmvThreads < t.d; k += 4 * kSpmvThreads) {
-    const int32_t c0 = __ldg(ci + k), c1 = __ldg(ci + k + kSpmvThreads);
-    const int32_t c2 = __ldg(ci + k + 2 * kSpmvThreads), c3 = __ldg(ci + k + 3 * kSpmvThreads);
-    const T v0 = __ldg(vv + k), v1 = __ldg(vv + k + kSpmvThreads);
-    const T v2 = __ldg(vv + k + 2 * kSpmvThreads), v3 = __ldg(vv + k + 3 * kSpmvThreads);
-    acc.add(v0, __ldg(x + c0));
-    acc.add(v1, __ldg(x + c1));
-    acc.add(v2, __ldg(x + c2));
-    acc.add(v3, __ldg(x + c3));
+  constexpr int U = kSpmvUnroll;
+  for (; k + (U - 1) * kSpmvThreads < t.d; k += U * kSpmvThreads) {
+    int32_t c[U];
+    T v[U], xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = __ldg(ci + k + u * kSpmvThreads);
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = __ldg(vv + k + u * kSpmvThreads);
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc.add(v[u], xv[u]);
   }
   for (; k < t.d; k += kSpmvThreads) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
   double r[1] = {acc.get()};
