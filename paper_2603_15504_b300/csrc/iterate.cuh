@@ -125,16 +125,22 @@ PDCS_DEV void dual_elem(const Prob<T>& p, double sigma, const T* __restrict__ y,
   yh[i] = (T)v;
 }
 
+// Dual step; when res is non-NULL it also stores u = G xhat - h on the cone
+// rows (the primal residual's argument, as res_prep_row), so the cone
+// projections of yhat and of u can run as one launch.
 template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_dual(Prob<T> p, const Ctl* __restrict__ ctl,
                                                      const T* __restrict__ y,
                                                      const T* __restrict__ gxh,
                                                      const T* __restrict__ gx,
-                                                     T* __restrict__ yh) {
+                                                     T* __restrict__ yh, double* __restrict__ res) {
   if (!ctl->g_attempt) return;
   ktimer_begin(tslot(p.tm, TM_DUAL));
   const double sigma = ctl->eta * ctl->omega;
-  PDCS_GRID_LOOP(i, p.m) dual_elem(p, sigma, y, gxh, gx, yh, i);
+  PDCS_GRID_LOOP(i, p.m) {
+    dual_elem(p, sigma, y, gxh, gx, yh, i);
+    if (res != nullptr && p.rk[i] >= RK_SOC) res[i] = (double)gxh[i] - (double)p.h[i];
+  }
   ktimer_end(tslot(p.tm, TM_DUAL));
 }
 
@@ -223,13 +229,20 @@ PDCS_DEV void cone_scale_pair(const double* d, int64_t s, int inv, double (&e)[3
 // blockIdx.y selects one of two vectors (each with its own gate).
 PDCS_DEV bool gate_on(const int* g) { return g == nullptr || *g != 0; }
 
+// Exponential-cone blocks, one thread per block.  flip1: vector 1 is
+// projected onto the other family member (1 - dual) under the inverse scales
+// (1 - inv), as for a dual iterate and a primal residual in one launch.
 template <typename B>
 __global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
                            const uint8_t* __restrict__ isd, int64_t count,
-                           const double* __restrict__ d, int inv, int dual,
+                           const double* __restrict__ d, int inv, int dual, int flip1,
                            const int* __restrict__ gate0, const int* __restrict__ gate1,
                            KTimer* tm) {
   B* v = blockIdx.y == 0 ? v0 : v1;
+  if (flip1 && blockIdx.y == 1) {
+    inv = 1 - inv;
+    dual = 1 - dual;
+  }
   const bool on = gate_on(blockIdx.y == 0 ? gate0 : gate1);
   if (!gate_on(gate0) && (gridDim.y == 1 || !gate_on(gate1))) return;  // whole launch idle
   ktimer_begin(tm);
@@ -248,14 +261,16 @@ __global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
 }
 
 // Second-order-cone blocks: one CTA per block (dims <= NT * EPT); target cone
-// diag(e) K_soc (self-dual, so the same routine serves both modes).
+// diag(e) K_soc (self-dual, so the same routine serves both modes); flip1:
+// vector 1 takes the inverse scales.
 template <typename B, int NT, int EPT>
 __global__ void __launch_bounds__(NT) k_cone_soc(B* v0, B* v1, const int64_t* __restrict__ starts,
                                                  const int32_t* __restrict__ dims,
-                                                 const double* __restrict__ d, int inv,
+                                                 const double* __restrict__ d, int inv, int flip1,
                                                  const int* __restrict__ gate0,
                                                  const int* __restrict__ gate1, KTimer* tm) {
   B* v = blockIdx.y == 0 ? v0 : v1;
+  if (flip1 && blockIdx.y == 1) inv = 1 - inv;
   if (!gate_on(gate0) && (gridDim.y == 1 || !gate_on(gate1))) return;  // whole launch idle
   ktimer_begin(tm);
   if (!gate_on(blockIdx.y == 0 ? gate0 : gate1)) {
@@ -287,7 +302,7 @@ __global__ void __launch_bounds__(NT) k_cone_soc(B* v0, B* v1, const int64_t* __
 // point when two are processed together.
 template <typename T>
 PDCS_DEV void res_prep_row(const Prob<T>& p, const PointRef<T>& pt, const TmpRef& tr, int64_t i) {
-  if (p.rk[i] >= RK_SOC) {
+  if (tr.tm != nullptr && p.rk[i] >= RK_SOC) {
     const double u = (double)pt.gx[i] - (double)p.h[i];
     tr.tm[i] = u;
     if (tr.um) tr.um[i] = u / p.d1[i];
@@ -1163,7 +1178,10 @@ PDCS_DEV float sg_probe_x(float topf, int j) {
 
 // Projection of the blocks (starts[b], dims[b]) of NV vectors onto
 // diag(e) K_soc, given the squared scales b_i = e_i^2 of each block (head
-// included) and their reciprocals (bq, bqi at offs[b]; NULL: e = 1).  part
+// included) and their reciprocals (bq, bqi at offs[b]; NULL: e = 1).  With
+// FLIP1 the second vector is projected onto diag(1/e) K_soc instead (its
+// squared scales are bqi and their reciprocals bq), so a dual iterate and a
+// primal residual share one launch and its barriers.  part
 // needs 2 * kSgHalf * gridDim.x doubles.  CTA c owns the tail elements 1 + c * chunk ... of each block.
 //
 // Root-finding (the secular equation and Halley steps of soc_proj_cta):
@@ -1176,7 +1194,11 @@ PDCS_DEV float sg_probe_x(float topf, int j) {
 // The tail is normalised by 2^-E, E the binary exponent of max |v| (exact, and
 // free in the integer conversions).  The NV vectors advance through the same
 // passes, so they share the barriers.
-template <typename B, int NV>
+// Squared scales of vector q: slot k (FP64, FP32) and element i from memory.
+#define SG_BD(q, k) ((FLIP1 && (q) == 1) ? bc1[FLIP1 ? (k) : 0] : bc[k])
+#define SG_BF(q, k) ((FLIP1 && (q) == 1) ? bfc1[FLIP1 ? (k) : 0] : bfc[k])
+#define SG_BM(q, i) (((FLIP1 && (q) == 1) ? bbi : bb) ? ((FLIP1 && (q) == 1) ? bbi : bb)[i] : 1.0)
+template <typename B, int NV, bool FLIP1>
 __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
     B* v0, B* v1, const int64_t* __restrict__ starts, const int64_t* __restrict__ dims,
     const int64_t* __restrict__ offs, int nblocks, const double* __restrict__ bq,
@@ -1225,12 +1247,15 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
     // and the FP32 probe sums; the slots' v and b stay in registers
     double bc[RC];
     float bfc[RC];
+    double bc1[FLIP1 ? RC : 1];  // vector 1's b_i (FLIP1: 1 / vector 0's)
+    float bfc1[FLIP1 ? RC : 1];
     double vc[NV][RC];
     float afc[NV][RC];
     double v0h[NV];
     double acc[2 * NV];
     long long amx[NV];
     const double b0 = bb ? bb[0] : 1.0;  // the head's squared scale
+    const double b0i = FLIP1 ? (bbi ? bbi[0] : 1.0) : b0;  // vector 1's, FLIP1
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       acc[2 * q] = 0.0;
@@ -1243,6 +1268,10 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
       const int64_t i = cbeg + t + k * nt;
       const bool in = i < cend;
       const double b = in && bb ? bb[i] : 1.0, bi = in && bbi ? bbi[i] : 1.0;
+      if (FLIP1) {
+        bc1[k] = bi;
+        bfc1[k] = f32_trunc(bi);
+      }
       bc[k] = b;
       bfc[k] = f32_trunc(b);
 #pragma unroll
@@ -1250,8 +1279,9 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
         const double vi = in && act[q] ? (double)vp[q][s + i] : 0.0;
         vc[q][k] = vi;
         const double v2 = vi * vi;
-        acc[2 * q] = fma(v2, bi, acc[2 * q]);
-        acc[2 * q + 1] = fma(v2, b, acc[2 * q + 1]);
+        const bool fl = FLIP1 && q == 1;
+        acc[2 * q] = fma(v2, fl ? b : bi, acc[2 * q]);
+        acc[2 * q + 1] = fma(v2, fl ? bi : b, acc[2 * q + 1]);
         amx[q] = max(amx[q], __double_as_longlong(vi) & 0x7fffffffffffffffll);
       }
     }
@@ -1261,8 +1291,9 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
       for (int q = 0; q < NV; ++q) {
         if (!act[q]) continue;
         const double vi = (double)vp[q][s + i], v2 = vi * vi;
-        acc[2 * q] = fma(v2, bi, acc[2 * q]);
-        acc[2 * q + 1] = fma(v2, b, acc[2 * q + 1]);
+        const bool fl = FLIP1 && q == 1;
+        acc[2 * q] = fma(v2, fl ? b : bi, acc[2 * q]);
+        acc[2 * q + 1] = fma(v2, fl ? bi : b, acc[2 * q + 1]);
         amx[q] = max(amx[q], __double_as_longlong(vi) & 0x7fffffffffffffffll);
       }
     }
@@ -1270,17 +1301,18 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
     // probes: thread t evaluates probe t % kSgProbes over elements
     // t / kSgProbes, + nt / kSgProbes, ... of the CTA (unnormalised FP32
     // terms; the root does not depend on the scale)
-    const float b0f = f32_trunc(b0);
+    const float b0f = f32_trunc(b0), b0f1 = FLIP1 ? f32_trunc(b0i) : b0f;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       if (!act[q] || !probes_ok) continue;  // uniform
       const bool posq = __double_as_longlong(v0h[q]) > 0ll;
-      const float topf = posq ? 0.5f * b0f : __frcp_rn(b0f);
+      const float hf = (FLIP1 && q == 1) ? b0f1 : b0f;
+      const float topf = posq ? 0.5f * hf : __frcp_rn(hf);
 #pragma unroll
       for (int k = 0; k < RC; ++k) {
         const float vf = f32_trunc(vc[q][k]);
-        pa[t + k * nt] = vf * vf * bfc[k];
-        pb[t + k * nt] = bfc[k];
+        pa[t + k * nt] = vf * vf * SG_BF(q, k);
+        pb[t + k * nt] = SG_BF(q, k);
       }
       __syncthreads();
       const int j = t % kSgProbes;
@@ -1328,11 +1360,11 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
       flip ^= 1;
     }
     if (w == 0) {
-      // e0^2 is the head's precomputed squared scale (exactly e0 * e0)
-      const double e02 = b0;
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         SocGridVec& g = sv[q];
+        // e0^2 is the head's precomputed squared scale (exactly e0 * e0)
+        const double e02 = (FLIP1 && q == 1) ? b0i : b0;
         if (lane == 0) {
           g.mode = SG_DONE;
           g.it = 0;
@@ -1379,7 +1411,8 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
         // within 2^+-40 for them to neither overflow nor underflow)
         if (g.mode == SG_F32 && probes_ok && g.esh >= -40 && g.esh <= 40) {
           const bool pos = g.pos != 0;
-          const float topf = pos ? 0.5f * b0f : __frcp_rn(b0f);  // as the probe abscissae
+          const float hf = (FLIP1 && q == 1) ? b0f1 : b0f;
+          const float topf = pos ? 0.5f * hf : __frcp_rn(hf);  // as the probe abscissae
           const float s2 = __uint_as_float((unsigned)(127 - 2 * g.esh) << 23);  // 2^-2E
           const float c0 = g.c0f, e02f = g.e02f, top = g.topf;
           int lo_b = 0, hi_b = __float_as_int(top);
@@ -1439,7 +1472,7 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
 #pragma unroll
       for (int k = 0; k < RC; ++k) {
         const float vf = f32 ? f32_trunc(vc[q][k], esh) : 0.0f;
-        afc[q][k] = vf * vf * bfc[k];
+        afc[q][k] = vf * vf * SG_BF(q, k);
       }
     }
     // ---- passes until every vector is written
@@ -1459,14 +1492,14 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
           for (int k = 0; k < RC; ++k) {
             const int64_t i = cbeg + t + k * nt;
             if (i >= cend) continue;
-            const double b = bc[k];
+            const double b = SG_BD(q, k);
             double out = 0.0;
             if (mode[q] == SG_WRITE_ZH) out = vc[q][k] * b / (b + e02);
             else if (mode[q] == SG_WRITE) out = vc[q][k] * (b * rcp_nr(b + mu2));
             vp[q][s + i] = (B)out;
           }
           for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
-            const double b = bb ? bb[i] : 1.0, vi = (double)vp[q][s + i];
+            const double b = SG_BM(q, i), vi = (double)vp[q][s + i];
             double out = 0.0;
             if (mode[q] == SG_WRITE_ZH) out = vi * b / (b + e02);
             else if (mode[q] == SG_WRITE) out = vi * (b * rcp_nr(b + mu2));
@@ -1500,7 +1533,7 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
           const float xf = g.xf;
 #pragma unroll
           for (int k = 0; k < RC; ++k) {
-            const float b = bfc[k], a = afc[q][k];  // a = 0 beyond the tail
+            const float b = SG_BF(q, k), a = afc[q][k];  // a = 0 beyond the tail
             const float r = pos ? __frcp_rn(fmaf(2.0f, xf, b)) : __frcp_rn(fmaf(b, xf, 1.0f));
             const float ar2 = a * r * r;
             fv[3 * q] += ar2;
@@ -1508,7 +1541,7 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
             fv[3 * q + 2] += pos ? ar2 * r * r : ar2 * b * b * r * r;
           }
           for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
-            const float bf = f32_trunc(bb ? bb[i] : 1.0), vf = f32_trunc((double)vp[q][s + i], g.esh);
+            const float bf = f32_trunc(SG_BM(q, i)), vf = f32_trunc((double)vp[q][s + i], g.esh);
             const float a = vf * vf * bf;
             const float r = pos ? __frcp_rn(fmaf(2.0f, xf, bf)) : __frcp_rn(fmaf(bf, xf, 1.0f));
             const float ar2 = a * r * r;
@@ -1521,11 +1554,11 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
 #pragma unroll
           for (int k = 0; k < RC; ++k) {
             if (cbeg + t + k * nt >= cend) continue;
-            const double vv = vc[q][k] * g.sc, b = bc[k];
+            const double vv = vc[q][k] * g.sc, b = SG_BD(q, k);
             soc_secular_terms(pos, vv * vv * b, b, g.x, f);
           }
           for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
-            const double b = bb ? bb[i] : 1.0, vv = (double)vp[q][s + i] * g.sc;
+            const double b = SG_BM(q, i), vv = (double)vp[q][s + i] * g.sc;
             soc_secular_terms(pos, vv * vv * b, b, g.x, f);
           }
           dv[3 * q] = f[0];
@@ -1537,11 +1570,11 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
 #pragma unroll
           for (int k = 0; k < RC; ++k) {
             if (cbeg + t + k * nt >= cend) continue;
-            const double b = bc[k], tt = vc[q][k] / (b + g.e02);
+            const double b = SG_BD(q, k), tt = vc[q][k] / (b + g.e02);
             wv += tt * tt * b;
           }
           for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
-            const double b = bb ? bb[i] : 1.0, tt = (double)vp[q][s + i] / (b + g.e02);
+            const double b = SG_BM(q, i), tt = (double)vp[q][s + i] / (b + g.e02);
             wv += tt * tt * b;
           }
           dv[3 * q] = wv;
@@ -1615,5 +1648,8 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
   }
   ktimer_end(tm);
 }
+#undef SG_BD
+#undef SG_BF
+#undef SG_BM
 
 }  // namespace pdcs

@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pdcs.h"
@@ -198,6 +199,7 @@ struct ConeTable {
   GridSync gsync = {nullptr, nullptr};
   int big_grid = 0;
   KTimer* timers = nullptr;  // profiling slots (NULL: off)
+  bool any() const { return nexp > 0 || nsoc[0] > 0 || nsoc[1] > 0 || nsoc[2] > 0 || nbig > 0; }
 };
 
 // b[i] = d[i]^2, bi[i] = 1 / d[i]^2 for i < n.
@@ -215,24 +217,26 @@ static const int kSocTierMax[3] = {128, 4096, 8192};
 
 // Projection of one or two vectors onto a product of cones: the blocks are
 // projected onto diag(e) K_b (dual = 0) or diag(e) K_b^* (dual = 1) with
-// e = d, 1/d (inv) or 1 (d == NULL).  Zero / nonnegative blocks are handled by
-// the producing kernels.
+// e = d, 1/d (inv) or 1 (d == NULL).  flip1 (two vectors, d != NULL): the
+// second vector takes the other mode and the inverse scales (1 - dual,
+// 1 - inv).  Zero / nonnegative blocks are handled by the producing kernels.
 template <typename B>
 static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d, int inv, int dual,
-                    const int* g0, const int* g1, cudaStream_t st) {
+                    const int* g0, const int* g1, cudaStream_t st, bool flip1 = false) {
   KTimer* tm = t.timers;
+  const int fl = flip1 ? 1 : 0;
   if (t.nexp > 0) {
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((t.nexp + 127) / 128, 148 * 8)), nvec);
-    k_cone_exp<B><<<grid, 128, 0, st>>>(v0, v1, t.exp_s, t.exp_isd, t.nexp, d, inv, dual, g0, g1,
+    k_cone_exp<B><<<grid, 128, 0, st>>>(v0, v1, t.exp_s, t.exp_isd, t.nexp, d, inv, dual, fl, g0, g1,
                                          tm ? tm + TM_EXP : nullptr);
   }
   KTimer* tsc = tm ? tm + TM_SOC_CTA : nullptr;
   if (t.nsoc[0] > 0)
-    k_cone_soc<B, 32, 4><<<dim3((unsigned)t.nsoc[0], nvec), 32, 0, st>>>(v0, v1, t.soc_s[0], t.soc_d[0], d, inv, g0, g1, tsc);
+    k_cone_soc<B, 32, 4><<<dim3((unsigned)t.nsoc[0], nvec), 32, 0, st>>>(v0, v1, t.soc_s[0], t.soc_d[0], d, inv, fl, g0, g1, tsc);
   if (t.nsoc[1] > 0)
-    k_cone_soc<B, 256, 16><<<dim3((unsigned)t.nsoc[1], nvec), 256, 0, st>>>(v0, v1, t.soc_s[1], t.soc_d[1], d, inv, g0, g1, tsc);
+    k_cone_soc<B, 256, 16><<<dim3((unsigned)t.nsoc[1], nvec), 256, 0, st>>>(v0, v1, t.soc_s[1], t.soc_d[1], d, inv, fl, g0, g1, tsc);
   if (t.nsoc[2] > 0)
-    k_cone_soc<B, 512, 16><<<dim3((unsigned)t.nsoc[2], nvec), 512, 0, st>>>(v0, v1, t.soc_s[2], t.soc_d[2], d, inv, g0, g1, tsc);
+    k_cone_soc<B, 512, 16><<<dim3((unsigned)t.nsoc[2], nvec), 512, 0, st>>>(v0, v1, t.soc_s[2], t.soc_d[2], d, inv, fl, g0, g1, tsc);
   if (t.nbig > 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)t.big_grid);
@@ -252,12 +256,15 @@ static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d,
     const int64_t* bs = t.big_s;
     const int64_t* bd = t.big_d;
     const int64_t* bo = t.big_o;
-    if (nvec == 2)
-      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 2>, v0, v1, bs, bd, bo, t.nbig, bq, bqi, g0,
-                            g1, t.gpart, t.gsync, tg));
+    if (nvec == 2 && flip1 && d != nullptr)
+      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 2, true>, v0, v1, bs, bd, bo, t.nbig, bq, bqi,
+                            g0, g1, t.gpart, t.gsync, tg));
+    else if (nvec == 2)
+      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 2, false>, v0, v1, bs, bd, bo, t.nbig, bq,
+                            bqi, g0, g1, t.gpart, t.gsync, tg));
     else
-      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 1>, v0, v1, bs, bd, bo, t.nbig, bq, bqi, g0,
-                            g1, t.gpart, t.gsync, tg));
+      CK(cudaLaunchKernelEx(&cfg, k_cone_soc_grid<B, 1, false>, v0, v1, bs, bd, bo, t.nbig, bq,
+                            bqi, g0, g1, t.gpart, t.gsync, tg));
   }
 }
 
@@ -650,13 +657,15 @@ struct Solver : SolverBase {
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         // one grid size for every variant (cooperative launches need all CTAs resident)
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<T, 1>, 512, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<T, 1, false>, 512, 0));
         occ = std::min(occ, o);
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<T, 2>, 512, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<T, 2, false>, 512, 0));
         occ = std::min(occ, o);
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<double, 1>, 512, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<double, 1, false>, 512, 0));
         occ = std::min(occ, o);
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<double, 2>, 512, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<double, 2, true>, 512, 0));
+        occ = std::min(occ, o);
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cone_soc_grid<double, 2, false>, 512, 0));
         occ = std::max(1, std::min(occ, o));
         big_grid = std::min(sms * occ, kMaxGridParts);
         gsync_count = ar.alloc<unsigned long long>(1);
@@ -858,14 +867,27 @@ struct Solver : SolverBase {
     k_primal<T><<<gn, kEwThreads, 0, s>>>(p, ctl, x, gty, xh);
     project<T>(cols, xh, xh, 1, d2, 1, 0, &ctl->g_attempt, nullptr, s);
     launch_spmv<T>(planG, rp, ci, vv, xh, gxh, &ctl->g_attempt, s, timers ? timers + TM_SPMV_G : nullptr);
-    k_dual<T><<<gm, kEwThreads, 0, s>>>(p, ctl, y, gxh, gx, yh);
-    project<T>(rows, yh, yh, 1, d1, 1, 1, &ctl->g_attempt, nullptr, s);
+    // FP64: the dual iterate (onto diag(1/d1) K*) and the primal residual's
+    // argument G xhat - h (onto diag(d1) K) are projected in one launch; the
+    // residual is then also formed for rejected attempts, where it is unused
+    const bool fuse = std::is_same<T, double>::value;
+    k_dual<T><<<gm, kEwThreads, 0, s>>>(p, ctl, y, gxh, gx, yh, fuse ? tm[0] : nullptr);
+    if (fuse)
+      project<T>(rows, yh, reinterpret_cast<T*>(tm[0]), 2, d1, 1, 1, &ctl->g_attempt,
+                 &ctl->g_attempt, s, true);
+    else
+      project<T>(rows, yh, yh, 1, d1, 1, 1, &ctl->g_attempt, nullptr, s);
     k_step<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, xh, y, yh, gxh, gx, part);
     launch_spmv<T>(planGT, rpT, ciT, vvT, yh, gtyh, &ctl->g_accept, s, timers ? timers + TM_SPMV_GT : nullptr);
     const PointRef<T> ph{xh, yh, gxh, gtyh};
     const TmpRef t0{tm[0], tn[0], nullptr, nullptr};
-    k_res_prep<T><<<dim3(gmx, 1), kEwThreads, 0, s>>>(p, &ctl->g_accept, ph, ph, t0, t0);
-    project<double>(rows, tm[0], tm[0], 1, d1, 0, 0, &ctl->g_accept, nullptr, s);
+    if (!fuse) {
+      k_res_prep<T><<<dim3(gmx, 1), kEwThreads, 0, s>>>(p, &ctl->g_accept, ph, ph, t0, t0);
+      project<double>(rows, tm[0], tm[0], 1, d1, 0, 0, &ctl->g_accept, nullptr, s);
+    } else if (cols.any()) {
+      const TmpRef tc{nullptr, tn[0], nullptr, nullptr};
+      k_res_prep<T><<<dim3(gmx, 1), kEwThreads, 0, s>>>(p, &ctl->g_accept, ph, ph, tc, tc);
+    }
     project<double>(cols, tn[0], tn[0], 1, d2, 0, 1, &ctl->g_accept, nullptr, s);
     k_point_stats<T, false><<<gmx, kEwThreads, 0, s>>>(p, ctl, &ctl->g_accept, 0, ph, nullptr, nullptr, t0, part);
     k_halpern<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, y, gx, gty, xh, yh, gxh, gtyh, x0, y0, gx0, gty0, xs, ys, trace);
