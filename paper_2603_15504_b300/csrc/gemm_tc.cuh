@@ -2,19 +2,25 @@
 //   C[M x N] = A[M x K] * B[N x K]^T   (A and B row-major with K contiguous),
 // FP32 accumulation in tensor memory (TMEM), with a fused epilogue.
 //
-// One CTA of 128 threads (4 warps) computes a 128 x 128 tile of C.  K is
-// walked in blocks of 64: the threads copy the A and B blocks from global
-// memory into shared memory in the canonical K-major layout without swizzle
-// (8-row x 16-byte core matrices; core matrices adjacent along K are 128 bytes
-// apart, along M / N 1024 bytes apart), two stages deep; one thread issues the
-// four 128 x 128 x 16 MMAs of a block and commits them to the stage's
-// mbarrier, which the threads wait on before they overwrite that stage.  The
-// accumulator tile occupies 128 TMEM columns; at the end warp w reads lanes
-// 32w .. 32w + 31 (rows of C) with tcgen05.ld and applies the epilogue.
+// One CTA of 128 threads (4 warps) computes a 128 x 128 tile of C, walking K
+// in blocks of 64 through a ring of kStages shared-memory stages:
+//   * lane 0 of warp 0 is the producer: per block it waits until the MMAs
+//     have released the stage, announces 32 KB on the stage's "full"
+//     mbarrier and issues two TMA tile loads (cp.async.bulk.tensor.2d) of the
+//     128 x 64 A and B boxes, which land 128-byte swizzled (the K-major
+//     SWIZZLE_128B layout of the MMA: 8-row x 128-byte atoms, 1024 bytes
+//     apart along M / N); rows past M / N and columns past K arrive as zeros;
+//   * lane 0 of warp 1 issues the four 128 x 128 x 16 MMAs of a block once its
+//     stage is full and commits them to the stage's "empty" mbarrier, and
+//     after the last block to a "done" mbarrier;
+//   * then warp w reads TMEM lanes 32w .. 32w + 31 (rows of C) with
+//     tcgen05.ld into shared memory, and the threads write the tile back
+//     column by column (coalesced rows) through the epilogue.
 // Every mbarrier wait is bounded: on expiry the kernel records an error,
-// stops issuing work, waits (bounded) for its last commit and still frees its
-// TMEM.
+// stops issuing, waits (bounded) for the loads and MMAs it has in flight and
+// still frees its TMEM.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,8 +29,9 @@ namespace pdcs {
 namespace tc {
 
 constexpr int kTileM = 128, kTileN = 128, kTileK = 64, kThreads = 128;
+constexpr int kStages = 4;
 constexpr int kStageBytes = kTileM * kTileK * 2;  // 16 KB per operand per stage
-constexpr uint32_t kLBO = 128, kSBO = 1024;        // canonical no-swizzle K-major layout
+constexpr uint32_t kSBO = 1024;                    // 8 rows x 128 B: one swizzle atom
 constexpr unsigned long long kSpinLimit = 1ull << 26;
 
 // Epilogues.  out[r * ldc + c] for r < M, c < N:
@@ -44,15 +51,21 @@ struct EpiArgs {
   int64_t ldm;
 };
 
-// Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits 0-13,
-// leading byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, the
-// descriptor version 1 in bits 46-47, no swizzle (bits 61-63 = 0).
-__host__ __device__ inline uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor (tcgen05) of a K-major operand in the
+// 128-byte swizzle layout: start address >> 4 in bits 0-13, leading byte
+// offset >> 4 in 16-29 (unused for this layout: one 16-element K step stays
+// inside a 128-byte row; set to 16 bytes), stride byte offset >> 4 in 32-45
+// (1024: the next 8-row atom), descriptor version 1 in bits 46-47, base
+// offset 0 (atoms 1024-byte aligned), swizzle mode 2 (128-byte) in bits 61-63.
+// The K step j of a 64-wide block starts 32 j bytes into the atom; the swizzle
+// is applied from the address bits, so the start address simply advances.
+__host__ __device__ inline uint64_t smem_desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
-  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)((kSBO & 0x3FFFFu) >> 4) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
@@ -69,9 +82,35 @@ __host__ __device__ inline uint32_t instr_desc_bf16(int m, int n) {
   return d;
 }
 
-// Byte offset of element (row r, k) of a 128 x 64 block in the canonical layout.
-__host__ __device__ inline uint32_t canon_off(int r, int k) {
-  return (uint32_t)((r >> 3) * kSBO + (k >> 3) * kLBO + (r & 7) * 16 + (k & 7) * 2);
+// Tensor map of a row-major rows x K BF16 matrix (leading dimension ld
+// elements) for 64 x 128 (K x rows) boxes with the 128-byte swizzle; zeros
+// outside the matrix.  Needs base 16-byte aligned and ld a multiple of 8.
+// Returns false if the driver refuses the map.
+inline bool make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K,
+                            int64_t ld) {
+  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (encode == nullptr) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || fn == nullptr)
+      return false;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  if (((uintptr_t)base & 15u) != 0 || (ld & 7) != 0 || rows <= 0 || K <= 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kTileK, (cuuint32_t)kTileM};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 
 #ifdef __CUDA_ARCH__
@@ -141,68 +180,61 @@ __device__ inline void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Copy rows [row0, row0 + 128) x columns [k0, k0 + 64) of a row-major
-// rows x K BF16 matrix (leading dimension ld, a multiple of 8) into the
-// canonical layout at dst; out-of-range elements are zero.  Thread t copies
-// 16-byte pieces v = t, t + 128, ...: chunk c = v / 128 (8 elements of K),
-// row r = v % 128, so a warp's stores fill 512 contiguous bytes.
-__device__ inline void load_block(uint8_t* dst, const __nv_bfloat16* __restrict__ src, int64_t rows,
-                                  int64_t K, int64_t ld, int64_t row0, int64_t k0) {
-#pragma unroll
-  for (int i = 0; i < (kTileM * kTileK / 8) / kThreads; ++i) {
-    const int v = threadIdx.x + i * kThreads;
-    const int c = v / kTileM, r = v % kTileM;
-    const int64_t gr = row0 + r, gk = k0 + c * 8;
-    uint4 val = make_uint4(0u, 0u, 0u, 0u);
-    if (gr < rows && gk < K) {
-      const __nv_bfloat16* p = src + gr * ld + gk;
-      if (gk + 8 <= K) {
-        val = __ldg(reinterpret_cast<const uint4*>(p));
-      } else {
-        __nv_bfloat16 tmp[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) tmp[e] = gk + e < K ? p[e] : __float2bfloat16(0.0f);
-        val = *reinterpret_cast<uint4*>(tmp);
-      }
-    }
-    *reinterpret_cast<uint4*>(dst + canon_off(r, c * 8)) = val;
-  }
+// Announce the bytes the stage's loads will deliver (counts as the one arrival).
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// TMA load of the box at (x = k, y = row) of the map into dst, completing on bar.
+__device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                   uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 #endif
 
-// C = A * B^T with the epilogue; A: M x K (lda), B: N x K (ldb), K, lda, ldb
-// multiples of 8, A and B 16-byte aligned.  Grid: (ceil(N / 128), ceil(M / 128),
-// splits).  Split-K (kchunk > 0, a multiple of 64): CTA z multiplies the K
-// slice [z kchunk, (z + 1) kchunk) and writes its FP32 partial tile (EPI_F32)
-// at ep.out + z * zstride floats; k_splitk_reduce adds the slices.
+// C = A * B^T with the epilogue; A: M x K, B: N x K, given as tensor maps
+// (make_kmajor_map).  Grid: (ceil(N / 128), ceil(M / 128), splits).  Split-K
+// (kchunk > 0, a multiple of 64): CTA z multiplies the K slice
+// [z kchunk, (z + 1) kchunk) and writes its FP32 partial tile (EPI_F32) at
+// ep.out + z * zstride floats; k_splitk_reduce adds the slices.
 // err: set to 1 if an mbarrier wait expired (the tile is then not written).
-__global__ void __launch_bounds__(kThreads) k_gemm_bf16_tn(const __nv_bfloat16* __restrict__ A,
-                                                           const __nv_bfloat16* __restrict__ B,
+// nst (1 .. kStages): stages in the ring; dynamic shared memory gemm_smem(nst).
+__global__ void __launch_bounds__(kThreads) k_gemm_bf16_tn(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB,
                                                            int64_t M, int64_t N, int64_t K,
-                                                           int64_t lda, int64_t ldb, EpiArgs ep,
-                                                           int* err, int64_t kchunk, int64_t zstride) {
+                                                           EpiArgs ep, int* err, int64_t kchunk,
+                                                           int64_t zstride, int nst) {
 #ifdef __CUDA_ARCH__
+  int64_t kbeg = 0;
   if (kchunk > 0) {
-    const int64_t kz = (int64_t)blockIdx.z * kchunk;
-    A += kz;
-    B += kz;
-    K = K - kz < kchunk ? K - kz : kchunk;
+    kbeg = (int64_t)blockIdx.z * kchunk;
+    K = K - kbeg < kchunk ? K - kbeg : kchunk;
     ep.out = reinterpret_cast<float*>(ep.out) + (int64_t)blockIdx.z * zstride;
   }
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  // 1024-byte aligned stages: A0 B0 A1 B1
+  // 1024-byte aligned stages (swizzle atoms): A0 B0 A1 B1 ...
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sa[2] = {base, base + 2 * kStageBytes};
-  uint8_t* sb[2] = {base + kStageBytes, base + 3 * kStageBytes};
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
   __shared__ uint32_t tmem_base;
-  __shared__ int failed;
+  __shared__ int failed, n_loads, n_mma;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t m0 = (int64_t)blockIdx.y * kTileM, n0 = (int64_t)blockIdx.x * kTileN;
+  const int nk = (int)((K + kTileK - 1) / kTileK);
   if (t == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
     failed = 0;
+    n_loads = 0;
+    n_mma = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -216,62 +248,102 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16_tn(const __nv_bfloat16* 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = instr_desc_bf16(kTileM, kTileN);
-  const int nk = (int)((K + kTileK - 1) / kTileK);
-  int issued = 0;  // commits issued (thread 0's count; the same for all threads)
-  for (int kb = 0; kb < nk; ++kb) {
-    const int s = kb & 1;
-    if (kb >= 2) {
-      // the MMAs that read this stage (block kb - 2) must have completed
-      if (!mbar_wait(&bar[s], (uint32_t)(((kb - 2) >> 1) & 1))) atomicExch(&failed, 1);
-    }
-    __syncthreads();
-    if (failed) break;  // uniform after the barrier
-    load_block(sa[s], A, M, K, lda, m0, (int64_t)kb * kTileK);
-    load_block(sb[s], B, N, K, ldb, n0, (int64_t)kb * kTileK);
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (t == 0) {
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(sa[s]), b0 = smem_u32(sb[s]);
-#pragma unroll
-      for (int j = 0; j < kTileK / 16; ++j) {
-        // 16 elements of K = two core matrices = 2 * LBO bytes
-        tc_mma(tmem, smem_desc(a0 + j * 2 * kLBO, kLBO, kSBO), smem_desc(b0 + j * 2 * kLBO, kLBO, kSBO),
-               idesc, (kb > 0 || j > 0) ? 1u : 0u);
+  volatile int* vfailed = &failed;
+  if (warp == 0 && lane == 0) {
+    // producer
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % nst;
+      if (kb >= nst && !mbar_wait(&empty[s], (uint32_t)(((kb / nst) - 1) & 1))) {
+        *vfailed = 1;
+        break;
       }
-      tc_commit(&bar[s]);
+      if (*vfailed) break;
+      uint8_t* sa = base + (size_t)s * 2 * kStageBytes;
+      mbar_expect_tx(&full[s], 2 * kStageBytes);
+      const int32_t kx = (int32_t)(kbeg + (int64_t)kb * kTileK);
+      tma_load_2d(sa, &tmA, kx, (int32_t)m0, &full[s]);
+      tma_load_2d(sa + kStageBytes, &tmB, kx, (int32_t)n0, &full[s]);
+      ++issued;
     }
-    ++issued;
+    n_loads = issued;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = instr_desc_bf16(kTileM, kTileN);
+    int used = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % nst;
+      if (!mbar_wait(&full[s], (uint32_t)((kb / nst) & 1))) {
+        *vfailed = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(base + (size_t)s * 2 * kStageBytes), b0 = a0 + kStageBytes;
+#pragma unroll
+      for (int j = 0; j < kTileK / 16; ++j)
+        tc_mma(tmem, smem_desc_sw128(a0 + 32 * j), smem_desc_sw128(b0 + 32 * j), idesc,
+               (kb > 0 || j > 0) ? 1u : 0u);
+      tc_commit(&empty[s]);
+      ++used;
+    }
+    tc_commit(&done);  // tracks every MMA this thread issued
+    n_mma = used;
   }
-  // wait for the last commit (it tracks every MMA issued before it)
-  if (issued > 0) {
-    const int kl = issued - 1;
-    if (!mbar_wait(&bar[kl & 1], (uint32_t)((kl >> 1) & 1))) atomicExch(&failed, 1);
+  __syncthreads();
+  // the accumulator is complete once "done" fires; a failed run still waits
+  // for the MMAs and loads it has in flight before the memory is released
+  if (t == 0) {
+    if (!mbar_wait(&done, 0u)) failed = 1;
+    for (int kb = n_mma; kb < n_loads; ++kb)
+      if (!mbar_wait(&full[kb % nst], (uint32_t)((kb / nst) & 1))) failed = 1;
   }
   __syncthreads();
   tc_fence_after();
-  if (!failed && issued == nk && nk > 0) {
-    const int64_t r = m0 + warp * 32 + lane;
+  if (!failed && n_mma == nk && nk > 0) {
+    // the accumulator goes through shared memory (the stages are free now):
+    // thread (warp w, lane l) holds row 32 w + l; rows are stored 129 floats
+    // apart so the column-wise writes hit distinct banks, then each thread
+    // takes one column and walks the rows, so a warp stores 32 consecutive
+    // columns of a row per step (coalesced)
+    float* stage = reinterpret_cast<float*>(base);
+    constexpr int kLd = kTileN + 1;
+    fence_proxy_async_smem();  // the stages were last touched by the async proxy
+    const int rl = warp * 32 + lane;
     for (int c0 = 0; c0 < kTileN; c0 += 16) {
       float v[16];
       tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (r >= M) continue;
-      const int64_t cb = n0 + c0;
-      if (ep.kind == EPI_F32 || ep.kind == EPI_F32_BIAS) {
-        float* o = reinterpret_cast<float*>(ep.out) + r * ep.ldc;
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (cb + i < N) o[cb + i] = v[i] + (ep.kind == EPI_F32_BIAS ? ep.bias[cb + i] : 0.0f);
-      } else {
-        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out) + r * ep.ldc;
+      for (int i = 0; i < 16; ++i) stage[rl * kLd + c0 + i] = v[i];
+    }
+    __syncthreads();
+    const int64_t c = n0 + t;
+    if (c < N) {
+      const float bc = (ep.kind == EPI_F32_BIAS || ep.kind == EPI_BF16_BIAS_RELU) ? ep.bias[c] : 0.0f;
+      const int rmax = (int)(M - m0 < kTileM ? M - m0 : kTileM);
+      // kRows rows at a time: their (mask) loads are issued before the stores
+      constexpr int kRows = 32;
+      for (int r0 = 0; r0 < rmax; r0 += kRows) {
+        float x[kRows];
+        bool keep[kRows];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          if (cb + i >= N) continue;
-          float x = v[i];
-          if (ep.kind == EPI_BF16_BIAS_RELU) x = fmaxf(x + ep.bias[cb + i], 0.0f);
-          else if (__bfloat162float(ep.mask[r * ep.ldm + cb + i]) <= 0.0f) x = 0.0f;
-          o[cb + i] = __float2bfloat16(x);
+        for (int i = 0; i < kRows; ++i) {
+          x[i] = r0 + i < rmax ? stage[(r0 + i) * kLd + t] + bc : 0.0f;
+          keep[i] = true;
+          if (ep.kind == EPI_BF16_RELU_MASK && r0 + i < rmax)
+            keep[i] = __bfloat162float(ep.mask[(m0 + r0 + i) * ep.ldm + c]) > 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) {
+          if (r0 + i >= rmax) break;
+          const int64_t gr = m0 + r0 + i;
+          if (ep.kind == EPI_F32 || ep.kind == EPI_F32_BIAS) {
+            reinterpret_cast<float*>(ep.out)[gr * ep.ldc + c] = x[i];
+          } else {
+            const float y = ep.kind == EPI_BF16_BIAS_RELU ? fmaxf(x[i], 0.0f) : (keep[i] ? x[i] : 0.0f);
+            reinterpret_cast<__nv_bfloat16*>(ep.out)[gr * ep.ldc + c] = __float2bfloat16(y);
+          }
         }
       }
     }
@@ -307,9 +379,15 @@ __global__ void k_splitk_reduce(const float* __restrict__ part, int splits, int6
   }
 }
 
-// Dynamic shared memory of k_gemm_bf16_tn (two stages of A and B, plus the
-// 1024-byte alignment slack).
-constexpr int kGemmSmem = 4 * kStageBytes + 1024;
+// Dynamic shared memory of k_gemm_bf16_tn with nst stages: the ring of A and
+// B stages or the epilogue's 128 x 129 FP32 staging tile, whichever is
+// larger, plus the 1024-byte alignment slack.
+constexpr int gemm_smem(int nst) {
+  return (2 * nst * kStageBytes > kTileM * (kTileN + 1) * 4 ? 2 * nst * kStageBytes
+                                                            : kTileM * (kTileN + 1) * 4) +
+         1024;
+}
+constexpr int kGemmSmem = gemm_smem(kStages);
 
 }  // namespace tc
 }  // namespace pdcs

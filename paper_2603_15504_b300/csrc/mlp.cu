@@ -313,15 +313,26 @@ struct Mlp {
     const int64_t tn = (N + pdcs::tc::kTileN - 1) / pdcs::tc::kTileN;
     const int64_t tm = (M + pdcs::tc::kTileM - 1) / pdcs::tc::kTileM;
     const int64_t nkb = (K + pdcs::tc::kTileK - 1) / pdcs::tc::kTileK;
+    CUtensorMap ta, tb;
+    if (!pdcs::tc::make_kmajor_map(&ta, A, M, K, lda) || !pdcs::tc::make_kmajor_map(&tb, Bm, N, K, ldb))
+      throw MlpFail{PDCS_ERR_CUDA, "cuTensorMapEncodeTiled refused a GEMM operand"};
     int64_t splits = 1;
     if (tn * tm < 148 && nkb >= 16) splits = std::min<int64_t>(nkb / 8, (2 * 148 + tn * tm - 1) / (tn * tm));
+    // stages: as many as a CTA has K blocks, up to the maximum; grids of two
+    // or more CTAs per SM take at most two, so three CTAs fit on an SM
+    auto stages = [&](int64_t nk_cta, int64_t ctas) {
+      const int64_t cap = ctas >= 2 * 148 ? 2 : pdcs::tc::kStages;
+      return (int)std::max<int64_t>(1, std::min<int64_t>(nk_cta, cap));
+    };
     if (splits <= 1) {
+      const int nst = stages(nkb, tn * tm);
       pdcs::tc::k_gemm_bf16_tn<<<dim3((unsigned)tn, (unsigned)tm), pdcs::tc::kThreads,
-                                 pdcs::tc::kGemmSmem, st>>>(A, Bm, M, N, K, lda, ldb, ep, err, 0, 0);
+                                 pdcs::tc::gemm_smem(nst), st>>>(ta, tb, M, N, K, ep, err, 0, 0, nst);
       return;
     }
     const int64_t kchunk = (nkb + splits - 1) / splits * pdcs::tc::kTileK;
     splits = (K + kchunk - 1) / kchunk;
+    const int nst = stages(kchunk / pdcs::tc::kTileK, tn * tm * splits);
     const int64_t zstride = M * N;
     if (splits * zstride > splitws_len) {
       splitws_len = splits * zstride;
@@ -329,8 +340,8 @@ struct Mlp {
     }
     EpiArgs part{pdcs::tc::EPI_F32, splitws, N, nullptr, nullptr, 0};
     pdcs::tc::k_gemm_bf16_tn<<<dim3((unsigned)tn, (unsigned)tm, (unsigned)splits), pdcs::tc::kThreads,
-                               pdcs::tc::kGemmSmem, st>>>(A, Bm, M, N, K, lda, ldb, part, err, kchunk,
-                                                          zstride);
+                               pdcs::tc::gemm_smem(nst), st>>>(ta, tb, M, N, K, part, err, kchunk, zstride,
+                                                               nst);
     pdcs::tc::k_splitk_reduce<<<grid_for(M * N), 256, 0, st>>>(splitws, (int)splits, M, N, zstride, ep);
   }
 
