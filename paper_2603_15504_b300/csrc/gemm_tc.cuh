@@ -292,6 +292,32 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16_tn(const __grid_constant
     n_mma = used;
   }
   __syncthreads();
+  // ReLU-mask epilogue: while the last MMAs run, thread (warp w, lane l)
+  // turns the mask of its row 32 w + l into 128 keep bits
+  const int rl = warp * 32 + lane;
+  uint32_t keep[4] = {0u, 0u, 0u, 0u};
+  if (ep.kind == EPI_BF16_RELU_MASK && m0 + rl < M) {
+    const __nv_bfloat16* mp = ep.mask + (m0 + rl) * ep.ldm + n0;
+    if (n0 + kTileN <= N && ((uintptr_t)mp & 15u) == 0) {
+      uint4 q[kTileN / 8];
+#pragma unroll
+      for (int j = 0; j < kTileN / 8; ++j) q[j] = __ldg(reinterpret_cast<const uint4*>(mp) + j);
+#pragma unroll
+      for (int j = 0; j < kTileN / 8; ++j) {
+        const uint32_t w[4] = {q[j].x, q[j].y, q[j].z, q[j].w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const uint16_t b = (uint16_t)(w[e >> 1] >> (16 * (e & 1)));
+          if (__bfloat162float(__ushort_as_bfloat16(b)) > 0.0f) keep[(8 * j + e) >> 5] |= 1u << ((8 * j + e) & 31);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < 4; ++w)
+        for (int j = 0; j < 32 && n0 + 32 * w + j < N; ++j)
+          if (__bfloat162float(mp[32 * w + j]) > 0.0f) keep[w] |= 1u << j;
+    }
+  }
   // the accumulator is complete once "done" fires; a failed run still waits
   // for the MMAs and loads it has in flight before the memory is released
   if (t == 0) {
@@ -310,38 +336,35 @@ __global__ void __launch_bounds__(kThreads) k_gemm_bf16_tn(const __grid_constant
     float* stage = reinterpret_cast<float*>(base);
     constexpr int kLd = kTileN + 1;
     fence_proxy_async_smem();  // the stages were last touched by the async proxy
-    const int rl = warp * 32 + lane;
+    const bool masked = ep.kind == EPI_BF16_RELU_MASK;
+#pragma unroll
     for (int c0 = 0; c0 < kTileN; c0 += 16) {
       float v[16];
       tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) stage[rl * kLd + c0 + i] = v[i];
+      for (int i = 0; i < 16; ++i) {
+        const int cc = c0 + i;
+        stage[rl * kLd + cc] = (masked && !((keep[cc >> 5] >> (cc & 31)) & 1u)) ? 0.0f : v[i];
+      }
     }
     __syncthreads();
     const int64_t c = n0 + t;
     if (c < N) {
       const float bc = (ep.kind == EPI_F32_BIAS || ep.kind == EPI_BF16_BIAS_RELU) ? ep.bias[c] : 0.0f;
       const int rmax = (int)(M - m0 < kTileM ? M - m0 : kTileM);
-      // kRows rows at a time: their (mask) loads are issued before the stores
-      constexpr int kRows = 32;
-      for (int r0 = 0; r0 < rmax; r0 += kRows) {
-        float x[kRows];
-        bool keep[kRows];
+      // eight rows at a time: their shared-memory loads before the stores
+      for (int r0 = 0; r0 < rmax; r0 += 8) {
+        float x[8];
 #pragma unroll
-        for (int i = 0; i < kRows; ++i) {
-          x[i] = r0 + i < rmax ? stage[(r0 + i) * kLd + t] + bc : 0.0f;
-          keep[i] = true;
-          if (ep.kind == EPI_BF16_RELU_MASK && r0 + i < rmax)
-            keep[i] = __bfloat162float(ep.mask[(m0 + r0 + i) * ep.ldm + c]) > 0.0f;
-        }
+        for (int i = 0; i < 8; ++i) x[i] = r0 + i < rmax ? stage[(r0 + i) * kLd + t] + bc : 0.0f;
 #pragma unroll
-        for (int i = 0; i < kRows; ++i) {
+        for (int i = 0; i < 8; ++i) {
           if (r0 + i >= rmax) break;
           const int64_t gr = m0 + r0 + i;
           if (ep.kind == EPI_F32 || ep.kind == EPI_F32_BIAS) {
             reinterpret_cast<float*>(ep.out)[gr * ep.ldc + c] = x[i];
           } else {
-            const float y = ep.kind == EPI_BF16_BIAS_RELU ? fmaxf(x[i], 0.0f) : (keep[i] ? x[i] : 0.0f);
+            const float y = ep.kind == EPI_BF16_BIAS_RELU ? fmaxf(x[i], 0.0f) : x[i];
             reinterpret_cast<__nv_bfloat16*>(ep.out)[gr * ep.ldc + c] = __float2bfloat16(y);
           }
         }
