@@ -63,22 +63,25 @@ constexpr int kExpGrid = 113;
 PDCS_HD float exp_grid_r(int i) { return sinhf(-14.0f + 0.25f * (float)i); }
 
 // phi(r) for the coarse scan, in FP32, with the ray scaled by e^{-max(r,0)}.
+// Of e^{-max(r,0)} and e^{r - max(r,0)} one is e^0 = 1, so one exponential
+// is evaluated (the same values as evaluating both).
 PDCS_HD float exp_phi_f(float r, float p0, float p1, float p2, float e0, float e1, float e2) {
-  const float R = fmaxf(r, 0.0f);
-  const float g = PDCS_FEXP(-R);
-  const float a0 = e0 * r * g, a1 = e1 * g, a2 = e2 * PDCS_FEXP(r - R);
+  const float x = PDCS_FEXP(-fabsf(r));
+  const float g = r > 0.0f ? x : 1.0f, h = r > 0.0f ? 1.0f : x;
+  const float a0 = e0 * r * g, a1 = e1 * g, a2 = e2 * h;
   const float num = p0 * a0 + p1 * a1 + p2 * a2;
   const float den = sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
   return num / den;
 }
 
 // g(r) and g'(r), both multiplied by e^{-2 max(r,0)} (the same factor, so the
-// Newton step g/g' and the sign of g are unchanged).
+// Newton step g/g' and the sign of g are unchanged).  One of e^{r - R} and
+// e^{-R} is e^0 = 1, so one exponential is evaluated.
 template <typename F>
 PDCS_HD void exp_g(F r, F P0, F P1, F P2, F S0, F S1, F S2, F& g, F& dg) {
-  const F R = r > F(0) ? r : F(0);
-  const F E1 = exp(r - R);  // e^{r} e^{-R}
-  const F eR = exp(-R);     // e^{-R}
+  const F x = exp(-fabs(r));
+  const F E1 = r > F(0) ? F(1) : x;  // e^{r} e^{-R}, R = max(r, 0)
+  const F eR = r > F(0) ? x : F(1);  // e^{-R}
   const F E2 = E1 * E1;     // e^{2r} e^{-2R}
   const F q = r * r - r + S1 / S0;
   g = (P0 * S1 - P1 * S0 * r) * eR * eR + P2 * S0 * E1 * eR * q + S2 * E2 * (P0 * (F(1) - r) - P1);
@@ -110,8 +113,9 @@ PDCS_HD F exp_newton(F r, F lo, F hi, F P0, F P1, F P2, F S0, F S1, F S2, int it
 // Nearest point of the ray through diag(e)(r, 1, e^r) to p; returns the squared
 // distance (+inf when <p, a> <= 0, i.e. the ray is not visible from p).
 PDCS_HD double exp_ray_point(double r, const double p[3], const double e[3], double c[3]) {
-  const double R = fmax(r, 0.0), g = exp(-R);
-  const double a0 = e[0] * r * g, a1 = e[1] * g, a2 = e[2] * exp(r - R);
+  const double x = exp(-fabs(r));
+  const double g = r > 0.0 ? x : 1.0, h = r > 0.0 ? 1.0 : x;  // e^{-R}, e^{r - R}
+  const double a0 = e[0] * r * g, a1 = e[1] * g, a2 = e[2] * h;
   const double pa = p[0] * a0 + p[1] * a1 + p[2] * a2;
   const double aa = a0 * a0 + a1 * a1 + a2 * a2;
   if (!(pa > 0.0) || !(aa > 0.0)) return INFINITY;
@@ -144,8 +148,11 @@ PDCS_HD bool exp_dual_member_fast(double u, double v, double w) {
   return exp_dual_member(u, v, w);
 }
 
-// Projection of p onto diag(e) K_exp (ie = 1 / e, elementwise).
-PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], const double ie[3], double q[3]) {
+// Projection of p onto diag(e) K_exp (ie = 1 / e, elementwise).  grid: the
+// kExpGrid scan abscissae exp_grid_r(i) precomputed (e.g. in shared memory),
+// or NULL to evaluate them here.
+PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], const double ie[3], double q[3],
+                             const float* grid = nullptr) {
   if (exp_member_fast(p[0] * ie[0], p[1] * ie[1], p[2] * ie[2])) {
     q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
     return;
@@ -167,9 +174,10 @@ PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], const double 
     const float fe0 = (float)e[0], fe1 = (float)e[1], fe2 = (float)e[2];
     float b1 = -3.0e38f, b2 = -3.0e38f;
     int i1 = -1, i2 = -1;
-    float prev2 = -3.0e38f, prev = exp_phi_f(exp_grid_r(0), fp0, fp1, fp2, fe0, fe1, fe2);
+    auto gr = [&](int i) { return grid ? grid[i] : exp_grid_r(i); };
+    float prev2 = -3.0e38f, prev = exp_phi_f(gr(0), fp0, fp1, fp2, fe0, fe1, fe2);
     for (int i = 0; i < kExpGrid; ++i) {
-      const float nxt = i + 1 < kExpGrid ? exp_phi_f(exp_grid_r(i + 1), fp0, fp1, fp2, fe0, fe1, fe2)
+      const float nxt = i + 1 < kExpGrid ? exp_phi_f(gr(i + 1), fp0, fp1, fp2, fe0, fe1, fe2)
                                          : -3.0e38f;
       const float cur = prev;
       if (cur >= prev2 && cur >= nxt) {
@@ -186,12 +194,12 @@ PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], const double 
     for (int pass = 0; pass < 2; ++pass) {
       const int bi = pass == 0 ? i1 : i2;
       if (bi < 0) continue;
-      const float rbf = exp_grid_r(bi);
+      const float rbf = gr(bi);
       const double rb = (double)rbf;
       // neighbourhood of the grid maximum: phi rises then falls in it, so
       // g > 0 at its left end and g < 0 at its right end
-      const double lo_n = bi > 0 ? (double)exp_grid_r(bi - 1) : rb;
-      const double hi_n = bi < kExpGrid - 1 ? (double)exp_grid_r(bi + 1) : rb;
+      const double lo_n = bi > 0 ? (double)gr(bi - 1) : rb;
+      const double hi_n = bi < kExpGrid - 1 ? (double)gr(bi + 1) : rb;
       double c[3];
       if (!(hi_n > lo_n)) {
         const double dd = exp_ray_point(rb, p, e, c);
@@ -224,11 +232,11 @@ PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], const double 
 // Projection onto diag(e) K' where K' = K_exp (dual == false) or K_exp^* (dual ==
 // true, via Moreau: P_{E K*}(v) = v + P_{E^{-1} K}(-v)); ie = 1 / e.
 PDCS_HD void proj_exp_family(const double v[3], const double e[3], const double ie[3], bool dual,
-                             double out[3]) {
-  if (!dual) { proj_exp_scaled(v, e, ie, out); return; }
+                             double out[3], const float* grid = nullptr) {
+  if (!dual) { proj_exp_scaled(v, e, ie, out, grid); return; }
   const double nv[3] = {-v[0], -v[1], -v[2]};
   double q[3];
-  proj_exp_scaled(nv, ie, e, q);
+  proj_exp_scaled(nv, ie, e, q, grid);
   out[0] = v[0] + q[0]; out[1] = v[1] + q[1]; out[2] = v[2] + q[2];
 }
 

@@ -246,13 +246,16 @@ __global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
   const bool on = gate_on(blockIdx.y == 0 ? gate0 : gate1);
   if (!gate_on(gate0) && (gridDim.y == 1 || !gate_on(gate1))) return;  // whole launch idle
   ktimer_begin(tm);
+  __shared__ float grid[kExpGrid];  // the scan abscissae, once per CTA
+  for (int i = threadIdx.x; i < kExpGrid; i += blockDim.x) grid[i] = exp_grid_r(i);
+  __syncthreads();
   if (on) PDCS_GRID_LOOP(b, count) {
     const int64_t s = starts[b];
     const double in[3] = {(double)v[s], (double)v[s + 1], (double)v[s + 2]};
     double e[3], ie[3];
     cone_scale_pair(d, s, inv, e, ie);
     double out[3];
-    proj_exp_family(in, e, ie, (isd[b] != 0) != (dual != 0), out);
+    proj_exp_family(in, e, ie, (isd[b] != 0) != (dual != 0), out, grid);
     v[s] = (B)out[0];
     v[s + 1] = (B)out[1];
     v[s + 2] = (B)out[2];

@@ -103,24 +103,21 @@ struct SpmvPlan {
   unsigned int* counters = nullptr;
 };
 
-// Bin rows into SpMV tasks (see spmv.cuh): short rows one per thread, medium
-// rows one lane group per row, long rows split into kChunk-nonzero chunks.
+// Bin rows into SpMV tasks (see spmv.cuh): long rows (> 4096 nonzeros) split
+// into kChunk-nonzero chunks; every other run of consecutive rows becomes a
+// task whose kind follows its longest row: one thread per row when no row has
+// more than 4 nonzeros, else one lane group per row (small_g lanes up to 512
+// nonzeros, a warp beyond).  Rows of different lengths share tasks, so
+// interleaved short and medium rows (the three rows of an exponential cone)
+// do not fragment the plan into one-row tasks.
 static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream_t st, int small_g) {
   const int64_t m = (int64_t)rp.size() - 1;
   std::vector<SpmvTask> tasks;
   int64_t npart = 0;
   int ncnt = 0;
-  auto cls = [&](int64_t r) {
-    const int64_t len = rp[r + 1] - rp[r];
-    if (len <= 4) return 0;
-    if (len <= 512) return 1;
-    if (len <= 4096) return 2;
-    return 3;
-  };
   int64_t r = 0;
   while (r < m) {
-    const int c = cls(r);
-    if (c == 3) {
+    if (rp[r + 1] - rp[r] > 4096) {
       const int64_t s = rp[r], e = rp[r + 1];
       const int64_t nch = (e - s + kChunk - 1) / kChunk;
       for (int64_t k = 0; k < nch; ++k) {
@@ -140,19 +137,28 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
       ++r;
       continue;
     }
-    // kind 1: one row per lane group at least (the nonzero cap applies beyond that)
-    const int64_t groups = c == 1 ? kSpmvThreads / small_g : 1;
-    const int64_t max_rows = c == 0 ? 256 : (c == 1 ? 4 * groups : 32);
-    const int64_t max_nnz = c == 2 ? 16384 : 8192;
-    int64_t e = r, nnz = 0;
-    while (e < m && cls(e) == c && e - r < max_rows &&
-           (nnz == 0 || e - r < groups || nnz + rp[e + 1] - rp[e] <= max_nnz)) {
-      nnz += rp[e + 1] - rp[e];
+    // extend while the task stays within the limits of the kind it would
+    // have: 256 rows (one thread each); 4 rows per lane group and 8,192
+    // nonzeros (small groups); 32 rows and 16,384 nonzeros (warps) -- the
+    // nonzero caps apply only beyond one row per group
+    int64_t e = r, nnz = 0, maxlen = 0;
+    while (e < m) {
+      const int64_t len = rp[e + 1] - rp[e];
+      if (len > 4096) break;
+      const int64_t ml = std::max(maxlen, len), cnt = e - r + 1;
+      int64_t lim_rows, lim_nnz, groups;
+      if (ml <= 4) { lim_rows = 256; lim_nnz = INT64_MAX; groups = 1; }
+      else if (ml <= 512) { groups = kSpmvThreads / small_g; lim_rows = 4 * groups; lim_nnz = 8192; }
+      else { groups = kSpmvThreads / 32; lim_rows = 32; lim_nnz = 16384; }
+      if (cnt > lim_rows) break;
+      if (cnt > groups && nnz + len > lim_nnz) break;
+      nnz += len;
+      maxlen = ml;
       ++e;
     }
     SpmvTask t{};
-    t.kind = c == 0 ? 0 : 1;
-    t.g = c == 1 ? small_g : 32;
+    t.kind = maxlen <= 4 ? 0 : 1;
+    t.g = maxlen <= 512 ? small_g : 32;
     t.a = r;
     t.b = e;
     tasks.push_back(t);

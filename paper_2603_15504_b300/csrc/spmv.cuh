@@ -1,14 +1,16 @@
 // CSR sparse matrix-vector product y = A x for the two products of every PDHG
 // step, G xhat and G^T yhat (PDCS note, eq. PDHG).
 //
-// Rows are binned on the host into tasks, one CTA per task:
-//   kind 0  up to 256 short rows (<= 4 nonzeros), one thread per row;
-//   kind 1  medium rows, one group of G lanes per row, lanes striding over the
-//           row so loads are coalesced: G = 32 for rows of 513..4096 nonzeros,
+// Rows are binned on the host into tasks, one CTA per task (runs of
+// consecutive rows; the kind follows the longest row of the run):
+//   kind 0  up to 256 rows of <= 4 nonzeros, one thread per row;
+//   kind 1  one group of G lanes per row, lanes striding over the row so
+//           loads are coalesced: G = 32 when a row has 513..4096 nonzeros,
 //           else the smallest group whose loads still fill 32-byte sectors
 //           (G = 4 for FP64, 8 for FP32), which keeps the FP64 shuffle-add tree
 //           per row short (FP64 instructions are the scarce resource here);
-//           a task holds at least one row per group, so no group idles;
+//           a task holds at least one row per group, so no group idles, and
+//           short rows ride along with longer neighbours;
 //   kind 2  one chunk of <= kChunk nonzeros of a long row; the chunk sums are
 //           written to a partial buffer and the last chunk CTA of the row (an
 //           atomic ticket, no waiting) adds them in chunk order, so the result
