@@ -111,7 +111,7 @@ PDCS_DEV void b_proj_exp(B* v, const int64_t* __restrict__ starts, const uint8_t
     const int64_t s = starts[first + j];
     const double in[3] = {(double)v[s], (double)v[s + 1], (double)v[s + 2]};
     double e[3], ie[3];
-    cone_scale_pair(d, s, inv, e, ie);
+    cone_scale_pair(d, nullptr, s, inv, e, ie);
     double out[3];
     proj_exp_family(in, e, ie, (isd[first + j] != 0) != (dual != 0), out);
     v[s] = (B)out[0];

@@ -41,6 +41,50 @@ namespace pdcs {
 #endif
 #define PDCS_HD __host__ __device__ __forceinline__
 
+// 1/d by Newton-Raphson refinement (r <- r + r (1 - d r), twice) of an FP32
+// seed: the seed (FP32 approximate reciprocal of d truncated to FP32) has a
+// relative error below 2^-21, so the first step leaves below 2^-42 and the
+// second rounding level.  On the device the seed and the range test run on
+// the integer and FP32 pipes; only the four FMAs use the FP64 pipe, whose
+// throughput is scarce.  Falls back to division outside |d| in
+// [2^-100, 2^100].
+PDCS_HD double rcp_nr(double d) {
+#ifdef __CUDA_ARCH__
+  const int e = (__double2hiint(d) >> 20) & 0x7ff;
+  if (e < 1023 - 100 || e > 1023 + 100) return 1.0 / d;
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f32_trunc(d)));
+  double r = f64_of_f32(rf);
+#else
+  const double ad = fabs(d);
+  if (!(ad > 0x1p-100 && ad < 0x1p100)) return 1.0 / d;
+  double r = (double)(1.0f / (float)d);
+#endif
+  double e1 = fma(-d, r, 1.0);
+  r = fma(r, e1, r);
+  e1 = fma(-d, r, 1.0);
+  return fma(r, e1, r);
+}
+
+// FP64 <-> FP32 for the FP32 screens and scans of the exponential cone: on the
+// device through the integer pipes (f32_trunc truncates the mantissa and
+// flushes subnormals, f64_of_f32 widens exactly), keeping the conversions out
+// of the FP64 pipe these kernels are bound by; plain casts on the host.
+PDCS_HD float exp_to_f32(double v) {
+#ifdef __CUDA_ARCH__
+  return f32_trunc(v);
+#else
+  return (float)v;
+#endif
+}
+PDCS_HD double exp_to_f64(float v) {
+#ifdef __CUDA_ARCH__
+  return f64_of_f32(v);
+#else
+  return (double)v;
+#endif
+}
+
 // ------------------------------------------------------------------ K_exp
 PDCS_HD bool exp_member(double x, double y, double z) {
   if (y > 0.0) {
@@ -76,28 +120,33 @@ PDCS_HD float exp_phi_f(float r, float p0, float p1, float p2, float e0, float e
 
 // g(r) and g'(r), both multiplied by e^{-2 max(r,0)} (the same factor, so the
 // Newton step g/g' and the sign of g are unchanged).  One of e^{r - R} and
-// e^{-R} is e^0 = 1, so one exponential is evaluated.
+// e^{-R} is e^0 = 1, so one exponential is evaluated; s10 = S1 / S0.
 template <typename F>
-PDCS_HD void exp_g(F r, F P0, F P1, F P2, F S0, F S1, F S2, F& g, F& dg) {
+PDCS_HD void exp_g(F r, F P0, F P1, F P2, F S0, F S1, F S2, F s10, F& g, F& dg) {
   const F x = exp(-fabs(r));
   const F E1 = r > F(0) ? F(1) : x;  // e^{r} e^{-R}, R = max(r, 0)
   const F eR = r > F(0) ? x : F(1);  // e^{-R}
   const F E2 = E1 * E1;     // e^{2r} e^{-2R}
-  const F q = r * r - r + S1 / S0;
+  const F q = r * r - r + s10;
   g = (P0 * S1 - P1 * S0 * r) * eR * eR + P2 * S0 * E1 * eR * q + S2 * E2 * (P0 * (F(1) - r) - P1);
-  dg = -P1 * S0 * eR * eR + P2 * S0 * E1 * eR * (r * r + r - F(1) + S1 / S0) +
+  dg = -P1 * S0 * eR * eR + P2 * S0 * E1 * eR * (r * r + r - F(1) + s10) +
        S2 * E2 * (P0 * (F(1) - F(2) * r) - F(2) * P1);
 }
 
-// Safeguarded Newton on g inside [lo, hi] with g(lo) > 0 >= g(hi).
+// a / b for the Newton steps: FP32 division, or in FP64 a times the
+// Newton-Raphson reciprocal (a few FMAs instead of a division sequence).
+PDCS_HD float exp_quot(float a, float b) { return a / b; }
+PDCS_HD double exp_quot(double a, double b) { return a * rcp_nr(b); }
+
+// Safeguarded Newton on g inside [lo, hi] with g(lo) > 0 >= g(hi); s10 = S1 / S0.
 template <typename F>
-PDCS_HD F exp_newton(F r, F lo, F hi, F P0, F P1, F P2, F S0, F S1, F S2, int iters, F tol) {
+PDCS_HD F exp_newton(F r, F lo, F hi, F P0, F P1, F P2, F S0, F S1, F S2, F s10, int iters, F tol) {
   for (int it = 0; it < iters; ++it) {
     F g, dg;
-    exp_g<F>(r, P0, P1, P2, S0, S1, S2, g, dg);
+    exp_g<F>(r, P0, P1, P2, S0, S1, S2, s10, g, dg);
     if (g > F(0)) lo = r; else hi = r;
     if (g == F(0)) break;
-    const F step = -g / dg;
+    const F step = -exp_quot(g, dg);
     F rn = r + step;
     // converged: the correction is below tolerance (it may not even move r)
     if (fabs(step) <= tol * (F(1) + fabs(r))) {
@@ -119,7 +168,7 @@ PDCS_HD double exp_ray_point(double r, const double p[3], const double e[3], dou
   const double pa = p[0] * a0 + p[1] * a1 + p[2] * a2;
   const double aa = a0 * a0 + a1 * a1 + a2 * a2;
   if (!(pa > 0.0) || !(aa > 0.0)) return INFINITY;
-  const double s = pa / aa;
+  const double s = pa * rcp_nr(aa);
   c[0] = s * a0; c[1] = s * a1; c[2] = s * a2;
   return (p[0] - c[0]) * (p[0] - c[0]) + (p[1] - c[1]) * (p[1] - c[1]) + (p[2] - c[2]) * (p[2] - c[2]);
 }
@@ -130,7 +179,7 @@ PDCS_HD double exp_ray_point(double r, const double p[3], const double e[3], dou
 // which cost logarithms in the scarce FP64 pipe).
 PDCS_HD bool exp_member_fast(double x, double y, double z) {
   if (y > 0.0 && z > 0.0) {
-    const float xf = (float)x, yf = (float)y, zf = (float)z;
+    const float xf = exp_to_f32(x), yf = exp_to_f32(y), zf = exp_to_f32(z);
     const float l = yf * logf(zf / yf);
     const float t = l - xf;
     if (fabsf(t) > 1e-4f * (fabsf(xf) + fabsf(l)) + 1e-30f && isfinite(t)) return t >= 0.0f;
@@ -140,7 +189,7 @@ PDCS_HD bool exp_member_fast(double x, double y, double z) {
 
 PDCS_HD bool exp_dual_member_fast(double u, double v, double w) {
   if (u < 0.0 && w > 0.0) {
-    const float uf = (float)u, vf = (float)v, wf = (float)w;
+    const float uf = exp_to_f32(u), vf = exp_to_f32(v), wf = exp_to_f32(w);
     const float a = logf(-uf), b = vf / uf, c = logf(wf);
     const float t = 1.0f + c - a - b;
     if (fabsf(t) > 1e-4f * (fabsf(a) + fabsf(b) + 1.0f + fabsf(c)) && isfinite(t)) return t >= 0.0f;
@@ -170,36 +219,49 @@ PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], const double 
     // Coarse scan: the two largest local maxima of phi on the grid.  The
     // visible part of the surface (phi > 0) can be narrower than the grid
     // spacing, so refinement never requires a positive grid value.
-    const float fp0 = (float)p[0], fp1 = (float)p[1], fp2 = (float)p[2];
-    const float fe0 = (float)e[0], fe1 = (float)e[1], fe2 = (float)e[2];
+    const float fp0 = exp_to_f32(p[0]), fp1 = exp_to_f32(p[1]), fp2 = exp_to_f32(p[2]);
+    const float fe0 = exp_to_f32(e[0]), fe1 = exp_to_f32(e[1]), fe2 = exp_to_f32(e[2]);
     float b1 = -3.0e38f, b2 = -3.0e38f;
     int i1 = -1, i2 = -1;
     auto gr = [&](int i) { return grid ? grid[i] : exp_grid_r(i); };
     float prev2 = -3.0e38f, prev = exp_phi_f(gr(0), fp0, fp1, fp2, fe0, fe1, fe2);
-    for (int i = 0; i < kExpGrid; ++i) {
-      const float nxt = i + 1 < kExpGrid ? exp_phi_f(gr(i + 1), fp0, fp1, fp2, fe0, fe1, fe2)
-                                         : -3.0e38f;
-      const float cur = prev;
-      if (cur >= prev2 && cur >= nxt) {
-        if (cur > b1) { b2 = b1; i2 = i1; b1 = cur; i1 = i; }
-        else if (cur > b2) { b2 = cur; i2 = i; }
+    // the grid values are independent: evaluate them kScan at a time, then
+    // walk them in order (the same values and comparisons as one at a time)
+    constexpr int kScan = 4;
+    for (int i0 = 0; i0 < kExpGrid; i0 += kScan) {
+      float f[kScan];
+#pragma unroll
+      for (int j = 0; j < kScan; ++j)
+        f[j] = i0 + j + 1 < kExpGrid ? exp_phi_f(gr(i0 + j + 1), fp0, fp1, fp2, fe0, fe1, fe2)
+                                     : -3.0e38f;
+#pragma unroll
+      for (int j = 0; j < kScan; ++j) {
+        const int i = i0 + j;
+        if (i >= kExpGrid) break;
+        const float cur = prev, nxt = f[j];
+        if (cur >= prev2 && cur >= nxt) {
+          if (cur > b1) { b2 = b1; i2 = i1; b1 = cur; i1 = i; }
+          else if (cur > b2) { b2 = cur; i2 = i; }
+        }
+        prev2 = cur;
+        prev = nxt;
       }
-      prev2 = cur;
-      prev = nxt;
     }
     const double P0 = e[0] * p[0], P1 = e[1] * p[1], P2 = e[2] * p[2];
     const double S0 = e[0] * e[0], S1 = e[1] * e[1], S2 = e[2] * e[2];
-    const float P0f = (float)P0, P1f = (float)P1, P2f = (float)P2;
-    const float S0f = (float)S0, S1f = (float)S1, S2f = (float)S2;
+    const float P0f = exp_to_f32(P0), P1f = exp_to_f32(P1), P2f = exp_to_f32(P2);
+    const float S0f = exp_to_f32(S0), S1f = exp_to_f32(S1), S2f = exp_to_f32(S2);
+    const double s10 = S1 * rcp_nr(S0);
+    const float s10f = S1f / S0f;
     for (int pass = 0; pass < 2; ++pass) {
       const int bi = pass == 0 ? i1 : i2;
       if (bi < 0) continue;
       const float rbf = gr(bi);
-      const double rb = (double)rbf;
+      const float lof_n = bi > 0 ? gr(bi - 1) : rbf, hif_n = bi < kExpGrid - 1 ? gr(bi + 1) : rbf;
+      const double rb = exp_to_f64(rbf);
       // neighbourhood of the grid maximum: phi rises then falls in it, so
       // g > 0 at its left end and g < 0 at its right end
-      const double lo_n = bi > 0 ? (double)gr(bi - 1) : rb;
-      const double hi_n = bi < kExpGrid - 1 ? (double)gr(bi + 1) : rb;
+      const double lo_n = exp_to_f64(lof_n), hi_n = exp_to_f64(hif_n);
       double c[3];
       if (!(hi_n > lo_n)) {
         const double dd = exp_ray_point(rb, p, e, c);
@@ -208,19 +270,19 @@ PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], const double 
       }
       // FP32: the side of the maximum, then Newton to FP32 accuracy
       float gf, dgf;
-      exp_g<float>(rbf, P0f, P1f, P2f, S0f, S1f, S2f, gf, dgf);
-      const float lof = gf > 0.0f ? rbf : (float)lo_n, hif = gf > 0.0f ? (float)hi_n : rbf;
+      exp_g<float>(rbf, P0f, P1f, P2f, S0f, S1f, S2f, s10f, gf, dgf);
+      const float lof = gf > 0.0f ? rbf : lof_n, hif = gf > 0.0f ? hif_n : rbf;
       double r = rb;
       if (hif > lof) {
         const float rf = exp_newton<float>(0.5f * (lof + hif), lof, hif, P0f, P1f, P2f, S0f, S1f,
-                                           S2f, 40, 1e-6f);
-        r = (double)rf;
+                                           S2f, s10f, 40, 1e-6f);
+        r = exp_to_f64(rf);
       }
       if (!(r > lo_n && r < hi_n)) r = 0.5 * (lo_n + hi_n);
       // FP64 polish in the whole neighbourhood: Newton converges
       // quadratically, so after a step below 1e-6 (1 + |r|) the root is
       // accurate far beyond what the candidate comparison needs
-      r = exp_newton<double>(r, lo_n, hi_n, P0, P1, P2, S0, S1, S2, 12, 1e-6);
+      r = exp_newton<double>(r, lo_n, hi_n, P0, P1, P2, S0, S1, S2, s10, 12, 1e-6);
       double dd = exp_ray_point(r, p, e, c);
       if (!(dd < INFINITY)) dd = exp_ray_point(rb, p, e, c);
       if (dd < bd) { best[0] = c[0]; best[1] = c[1]; best[2] = c[2]; bd = dd; }
@@ -241,31 +303,6 @@ PDCS_HD void proj_exp_family(const double v[3], const double e[3], const double 
 }
 
 // ------------------------------------------------------------------ K_soc
-// 1/d by Newton-Raphson refinement (r <- r + r (1 - d r), twice) of an FP32
-// seed: the seed (FP32 approximate reciprocal of d truncated to FP32) has a
-// relative error below 2^-21, so the first step leaves below 2^-42 and the
-// second rounding level.  On the device the seed and the range test run on
-// the integer and FP32 pipes; only the four FMAs use the FP64 pipe, whose
-// throughput is scarce.  Falls back to division outside |d| in
-// [2^-100, 2^100].
-PDCS_HD double rcp_nr(double d) {
-#ifdef __CUDA_ARCH__
-  const int e = (__double2hiint(d) >> 20) & 0x7ff;
-  if (e < 1023 - 100 || e > 1023 + 100) return 1.0 / d;
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f32_trunc(d)));
-  double r = f64_of_f32(rf);
-#else
-  const double ad = fabs(d);
-  if (!(ad > 0x1p-100 && ad < 0x1p100)) return 1.0 / d;
-  double r = (double)(1.0f / (float)d);
-#endif
-  double e1 = fma(-d, r, 1.0);
-  r = fma(r, e1, r);
-  e1 = fma(-d, r, 1.0);
-  return fma(r, e1, r);
-}
-
 // Per-element terms of the secular function and its first two derivatives:
 // f += (a r^2, a r^3, a r^4) with r = 1/(b + 2x) (branch v0 > 0, x = mu) or
 // (a r^2, a b r^3, a b^2 r^4) with r = 1/(1 + b x) (branch v0 < 0, x = nu).

@@ -212,13 +212,14 @@ PDCS_DEV double cone_scale(const double* d, int64_t i, int inv) {
   return inv ? 1.0 / d[i] : d[i];
 }
 
-// e = d or 1/d (inv) or 1 (d == NULL) for the 3-block at s, and ie = 1 / e
-// (one division per element).
-PDCS_DEV void cone_scale_pair(const double* d, int64_t s, int inv, double (&e)[3], double (&ie)[3]) {
+// e = d or 1/d (inv) or 1 (d == NULL) for the 3-block at s, and ie = 1 / e;
+// dinv, when given, holds the reciprocals 1 / d (else one division per element).
+PDCS_DEV void cone_scale_pair(const double* d, const double* dinv, int64_t s, int inv,
+                              double (&e)[3], double (&ie)[3]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     if (d == nullptr) { e[k] = ie[k] = 1.0; continue; }
-    const double di = d[s + k], r = 1.0 / di;
+    const double di = d[s + k], r = dinv ? dinv[s + k] : 1.0 / di;
     e[k] = inv ? r : di;
     ie[k] = inv ? di : r;
   }
@@ -235,7 +236,8 @@ PDCS_DEV bool gate_on(const int* g) { return g == nullptr || *g != 0; }
 template <typename B>
 __global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
                            const uint8_t* __restrict__ isd, int64_t count,
-                           const double* __restrict__ d, int inv, int dual, int flip1,
+                           const double* __restrict__ d, const double* __restrict__ dinv, int inv,
+                           int dual, int flip1,
                            const int* __restrict__ gate0, const int* __restrict__ gate1,
                            KTimer* tm) {
   B* v = blockIdx.y == 0 ? v0 : v1;
@@ -253,7 +255,7 @@ __global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
     const int64_t s = starts[b];
     const double in[3] = {(double)v[s], (double)v[s + 1], (double)v[s + 2]};
     double e[3], ie[3];
-    cone_scale_pair(d, s, inv, e, ie);
+    cone_scale_pair(d, dinv, s, inv, e, ie);
     double out[3];
     proj_exp_family(in, e, ie, (isd[b] != 0) != (dual != 0), out, grid);
     v[s] = (B)out[0];

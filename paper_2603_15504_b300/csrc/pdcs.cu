@@ -200,6 +200,7 @@ struct ConeTable {
   int64_t* exp_s = nullptr;
   uint8_t* exp_isd = nullptr;
   int64_t nexp = 0;
+  double* dinv = nullptr;     // 1 / d over the whole side (exp blocks read it)
   // grid-wide kernel resources (shared by both tables)
   double* gpart = nullptr;
   GridSync gsync = {nullptr, nullptr};
@@ -207,6 +208,13 @@ struct ConeTable {
   KTimer* timers = nullptr;  // profiling slots (NULL: off)
   bool any() const { return nexp > 0 || nsoc[0] > 0 || nsoc[1] > 0 || nsoc[2] > 0 || nbig > 0; }
 };
+
+// r[i] = 1 / d[i] for i < n.
+__global__ void k_reciprocal(const double* __restrict__ d, int64_t n, double* __restrict__ r) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = 1.0 / d[i];
+}
 
 // b[i] = d[i]^2, bi[i] = 1 / d[i]^2 for i < n.
 __global__ void k_square_scales(const double* __restrict__ d, int64_t n, double* __restrict__ b,
@@ -233,7 +241,8 @@ static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d,
   const int fl = flip1 ? 1 : 0;
   if (t.nexp > 0) {
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((t.nexp + 127) / 128, 148 * 8)), nvec);
-    k_cone_exp<B><<<grid, 128, 0, st>>>(v0, v1, t.exp_s, t.exp_isd, t.nexp, d, inv, dual, fl, g0, g1,
+    k_cone_exp<B><<<grid, 128, 0, st>>>(v0, v1, t.exp_s, t.exp_isd, t.nexp, d,
+                                         d ? t.dinv : nullptr, inv, dual, fl, g0, g1,
                                          tm ? tm + TM_EXP : nullptr);
   }
   KTimer* tsc = tm ? tm + TM_SOC_CTA : nullptr;
@@ -573,8 +582,8 @@ struct Solver : SolverBase {
     ck = ar.alloc<uint8_t>(n);
     copy_in(rk, hrk.data(), m, st);
     copy_in(ck, hck.data(), n, st);
-    fill_table(rows, rsoc, rbig, rexp, rexpd, d1);
-    fill_table(cols, csoc, cbig, cexp, cexpd, d2);
+    fill_table(rows, rsoc, rbig, rexp, rexpd, d1, m);
+    fill_table(cols, csoc, cbig, cexp, cexpd, d2, n);
     const int small_g = sizeof(T) == 8 ? 4 : 8;
     planG = build_plan(hrp, ar, st, small_g);
     planGT = build_plan(hrpT, ar, st, small_g);
@@ -634,7 +643,7 @@ struct Solver : SolverBase {
   void fill_table(ConeTable& t, const std::vector<std::vector<std::pair<int64_t, int32_t>>>& soc,
                   const std::vector<std::pair<int64_t, int64_t>>& big,
                   const std::vector<int64_t>& ex, const std::vector<uint8_t>& exd,
-                  const double* dscale) {
+                  const double* dscale, int64_t dlen) {
     t.nbig = (int)big.size();
     if (t.nbig > 0) {
       std::vector<int64_t> bs, bd, bo;
@@ -697,6 +706,13 @@ struct Solver : SolverBase {
       CK(cudaStreamSynchronize(st));
     }
     t.nexp = (int64_t)ex.size();
+    if (t.nexp > 0 && dlen > 0) {
+      // the exponential-cone kernels take e = d or 1/d per element: the
+      // reciprocals once here instead of three FP64 divisions per projection
+      t.dinv = ar.alloc<double>(dlen);
+      k_reciprocal<<<ew_grid(dlen), 256, 0, st>>>(dscale, dlen, t.dinv);
+      CK(cudaGetLastError());
+    }
     if (t.nexp > 0) {
       t.exp_s = ar.alloc<int64_t>(t.nexp);
       t.exp_isd = ar.alloc<uint8_t>(t.nexp);
