@@ -41,10 +41,10 @@ CHECK_FREQ = 64
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
 # (precision, source digest of spmv.cuh at capture time); see profiles/.
 NCU_TRAFFIC = {
-    # profiles/k_spmv_portfolio_n100k_fp64.md: 257.6 MB per launch (mean of
+    # profiles/k_spmv_portfolio_n100k_fp64.md: 257.5 MB per launch (mean of
     # G xhat and G^T yhat) at n = 100,000, scaled by the algorithmic bytes
     # (x 2.005) to the n = 200,000 workload
-    ("fp64", "46df4901e6f5ad18"): 516.5e6,
+    ("fp64", "419527a7d587b9d0"): 516.3e6,
 }
 
 

@@ -272,6 +272,29 @@ PDCS_HD void proj_exp_scaled(const double p[3], const double e[3], const double 
       float gf, dgf;
       exp_g<float>(rbf, P0f, P1f, P2f, S0f, S1f, S2f, s10f, gf, dgf);
       const float lof = gf > 0.0f ? rbf : lof_n, hif = gf > 0.0f ? hif_n : rbf;
+      // a local maximum of phi needs g to change sign across that half of the
+      // neighbourhood; grid "maxima" on flat stretches of phi (ties in the
+      // FP32 scan) have no sign change and no root, and only the grid point
+      // itself is kept as a candidate.  FP32 screens; where it sees no sign
+      // change, FP64 values at both points decide.
+      const float oend = gf > 0.0f ? hif_n : lof_n;
+      bool root = oend != rbf;
+      if (root) {
+        float go, dgo;
+        exp_g<float>(oend, P0f, P1f, P2f, S0f, S1f, S2f, s10f, go, dgo);
+        root = gf > 0.0f ? !(go > 0.0f) : (go > 0.0f);
+        if (!root) {
+          double g0, dg0, g1, dg1;
+          exp_g<double>(rb, P0, P1, P2, S0, S1, S2, s10, g0, dg0);
+          exp_g<double>(exp_to_f64(oend), P0, P1, P2, S0, S1, S2, s10, g1, dg1);
+          root = g0 > 0.0 ? !(g1 > 0.0) : (g1 > 0.0);
+        }
+      }
+      if (!root) {
+        const double dd = exp_ray_point(rb, p, e, c);
+        if (dd < bd) { best[0] = c[0]; best[1] = c[1]; best[2] = c[2]; bd = dd; }
+        continue;
+      }
       double r = rb;
       if (hif > lof) {
         const float rf = exp_newton<float>(0.5f * (lof + hif), lof, hif, P0f, P1f, P2f, S0f, S1f,
