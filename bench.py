@@ -39,12 +39,12 @@ METRIC = "time to 1e-6 rel. KKT & PDHG iters/s; batched and warm-start vs plain 
 UNIT = "PDHG iterations/s"
 CHECK_FREQ = 64
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
-# (precision, source digest of spmv.cuh at capture time); see profiles/.
+# (workload, precision, source digest of spmv.cuh at capture time); see profiles/.
 NCU_TRAFFIC = {
     # profiles/k_spmv_portfolio_n100k_fp64.md: 257.5 MB per launch (mean of
     # G xhat and G^T yhat) at n = 100,000, scaled by the algorithmic bytes
     # (x 2.005) to the n = 200,000 workload
-    ("fp64", "419527a7d587b9d0"): 516.3e6,
+    ("portfolio", "fp64", "419527a7d587b9d0"): 516.3e6,
 }
 
 
@@ -278,7 +278,7 @@ def run_ours(args):
     sp_bytes = prof["g_bytes"] * prof["g_launches"] + prof["gt_bytes"] * prof["gt_launches"]
     launches = prof["g_launches"] + prof["gt_launches"]
     achieved = sp_bytes / sp_time / 1e9 if sp_time > 0 else None
-    traffic = NCU_TRAFFIC.get((args.precision, _spmv_digest()))
+    traffic = NCU_TRAFFIC.get((args.workload, args.precision, _spmv_digest()))
     roofline = {"bound": "hbm", "kernel": "k_spmv (G xhat and G^T yhat)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None,
