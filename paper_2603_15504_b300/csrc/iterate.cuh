@@ -234,7 +234,7 @@ PDCS_DEV bool gate_on(const int* g) { return g == nullptr || *g != 0; }
 // projected onto the other family member (1 - dual) under the inverse scales
 // (1 - inv), as for a dual iterate and a primal residual in one launch.
 template <typename B>
-__global__ void k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
+__global__ void __launch_bounds__(128, 6) k_cone_exp(B* v0, B* v1, const int64_t* __restrict__ starts,
                            const uint8_t* __restrict__ isd, int64_t count,
                            const double* __restrict__ d, const double* __restrict__ dinv, int inv,
                            int dual, int flip1,
