@@ -125,9 +125,40 @@ PDCS_DEV void dual_elem(const Prob<T>& p, double sigma, const T* __restrict__ y,
   yh[i] = (T)v;
 }
 
-// Dual step; when res is non-NULL it also stores u = G xhat - h on the cone
-// rows (the primal residual's argument, as res_prep_row), so the cone
-// projections of yhat and of u can run as one launch.
+// The dual step of row i as the epilogue of the product G xhat (the product
+// hands each row's value to this functor): stores (G xhat)_i, the dual update
+// of dual_elem, and, when res is non-NULL, u = G xhat - h on the cone rows
+// (the primal residual's argument, as res_prep_row), so the cone projections
+// of yhat and of u can run as one launch.  sigma = eta omega of the attempt.
+template <typename T>
+struct DualOut {
+  Prob<T> p;
+  const Ctl* ctl;
+  const T* y;
+  const T* gx;
+  T* gxh;
+  T* yh;
+  double* res;
+  struct Pre {
+    double y, gx, h, sigma;
+    uint8_t rk;
+  };
+  PDCS_DEV Pre pre(int64_t i) const {
+    return Pre{(double)__ldg(y + i), (double)__ldg(gx + i), (double)__ldg(p.h + i),
+               ctl->eta * ctl->omega, __ldg(p.rk + i)};
+  }
+  PDCS_DEV void operator()(int64_t i, double v, const Pre& q) const {
+    const T g = (T)v;
+    gxh[i] = g;
+    double w = q.y + q.sigma * (q.h - 2.0 * (double)g + q.gx);
+    if (q.rk == RK_NONNEG) w = fmax(w, 0.0);
+    yh[i] = (T)w;
+    if (res != nullptr && q.rk >= RK_SOC) res[i] = (double)g - q.h;
+  }
+};
+
+// Dual step as a kernel of its own (products with short rows, where the
+// product's epilogue would cost it occupancy); res as in DualOut.
 template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_dual(Prob<T> p, const Ctl* __restrict__ ctl,
                                                      const T* __restrict__ y,
@@ -525,30 +556,6 @@ PDCS_DEV void ctl_halpern_finalize(Ctl& c, double eta, double beta, double* trac
   }
 }
 
-// z^{t,k+1} = (k+1)/(k+2) ((1+beta) zhat - beta z) + z^{t,0}/(k+2) (Algorithm
-// 1), applied to (x, y) and, by linearity, to the maintained products G x and
-// G^T y; the average accumulators add eta * z^{t,k+1} in FP64.
-template <typename T>
-__global__ void __launch_bounds__(kEwThreads) k_halpern(
-    Prob<T> p, Ctl* __restrict__ ctl, T* __restrict__ x, T* __restrict__ y, T* __restrict__ gx,
-    T* __restrict__ gty, const T* __restrict__ xh, const T* __restrict__ yh,
-    const T* __restrict__ gxh, const T* __restrict__ gtyh, const T* __restrict__ x0,
-    const T* __restrict__ y0, const T* __restrict__ gx0, const T* __restrict__ gty0,
-    double* __restrict__ xs, double* __restrict__ ys, double* __restrict__ trace) {
-  if (!ctl->g_accept) return;
-  ktimer_begin(tslot(p.tm, TM_HALPERN));
-  const double kk = (double)ctl->k;
-  const double beta = ctl->beta, eta = ctl->eta_acc;
-  const double a = (kk + 1.0) / (kk + 2.0), b = 1.0 / (kk + 2.0);
-  PDCS_GRID_LOOP(j, p.n) halpern_elem(a, b, beta, eta, x, gty, xh, gtyh, x0, gty0, xs, j);
-  PDCS_GRID_LOOP(i, p.m) halpern_elem(a, b, beta, eta, y, gx, yh, gxh, y0, gx0, ys, i);
-  ktimer_end(tslot(p.tm, TM_HALPERN));
-  if (!last_block_done(&ctl->cnt[CNT_HALPERN])) return;
-  if (threadIdx.x != 0) return;
-  ctl->cnt[CNT_HALPERN] = 0u;
-  ctl_halpern_finalize(*ctl, eta, beta, trace);
-}
-
 // Body terminator of the attempt loop: continue while the period needs more
 // accepted iterations (bounded by guard_cap bodies per graph launch).
 // (use_cond = 0: launched eagerly from the host, which reads g_attempt itself.)
@@ -568,9 +575,42 @@ PDCS_DEV int ctl_period_begin(Ctl& c) {
   return go;
 }
 
-__global__ void k_loop_ctl(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
-  const int go = ctl_loop_ctl(*ctl);
+// The loop decision and, inside a graph, the WHILE node's condition.
+PDCS_DEV void loop_ctl(Ctl& c, cudaGraphConditionalHandle h, int use_cond) {
+  const int go = ctl_loop_ctl(c);
   if (use_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// z^{t,k+1} = (k+1)/(k+2) ((1+beta) zhat - beta z) + z^{t,0}/(k+2) (Algorithm
+// 1), applied to (x, y) and, by linearity, to the maintained products G x and
+// G^T y; the average accumulators add eta * z^{t,k+1} in FP64.  The kernel
+// ends the attempt body: after the step (or at once for a rejected attempt)
+// one thread takes the loop decision.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_halpern(
+    Prob<T> p, Ctl* __restrict__ ctl, T* __restrict__ x, T* __restrict__ y, T* __restrict__ gx,
+    T* __restrict__ gty, const T* __restrict__ xh, const T* __restrict__ yh,
+    const T* __restrict__ gxh, const T* __restrict__ gtyh, const T* __restrict__ x0,
+    const T* __restrict__ y0, const T* __restrict__ gx0, const T* __restrict__ gty0,
+    double* __restrict__ xs, double* __restrict__ ys, double* __restrict__ trace,
+    cudaGraphConditionalHandle h, int use_cond) {
+  if (!ctl->g_accept) {
+    // rejected attempt: only the loop decision
+    if (blockIdx.x == 0 && threadIdx.x == 0) loop_ctl(*ctl, h, use_cond);
+    return;
+  }
+  ktimer_begin(tslot(p.tm, TM_HALPERN));
+  const double kk = (double)ctl->k;
+  const double beta = ctl->beta, eta = ctl->eta_acc;
+  const double a = (kk + 1.0) / (kk + 2.0), b = 1.0 / (kk + 2.0);
+  PDCS_GRID_LOOP(j, p.n) halpern_elem(a, b, beta, eta, x, gty, xh, gtyh, x0, gty0, xs, j);
+  PDCS_GRID_LOOP(i, p.m) halpern_elem(a, b, beta, eta, y, gx, yh, gxh, y0, gx0, ys, i);
+  ktimer_end(tslot(p.tm, TM_HALPERN));
+  if (!last_block_done(&ctl->cnt[CNT_HALPERN])) return;
+  if (threadIdx.x != 0) return;
+  ctl->cnt[CNT_HALPERN] = 0u;
+  ctl_halpern_finalize(*ctl, eta, beta, trace);
+  loop_ctl(*ctl, h, use_cond);
 }
 
 __global__ void k_period_begin(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {

@@ -177,11 +177,19 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
   return p;
 }
 
+template <typename T, typename Out>
+static void launch_spmv_out(const SpmvPlan& p, const int64_t* rp, const int32_t* ci, const T* vv,
+                            const T* x, const Out& out, const int* gate, cudaStream_t st,
+                            KTimer* tm = nullptr) {
+  if (p.ntasks == 0) return;
+  k_spmv<T, Out><<<p.ntasks, kSpmvThreads, 0, st>>>(p.tasks, rp, ci, vv, x, out, p.partial,
+                                                    p.counters, gate, tm);
+}
+
 template <typename T>
 static void launch_spmv(const SpmvPlan& p, const int64_t* rp, const int32_t* ci, const T* vv,
                         const T* x, T* y, const int* gate, cudaStream_t st, KTimer* tm = nullptr) {
-  if (p.ntasks == 0) return;
-  k_spmv<T><<<p.ntasks, kSpmvThreads, 0, st>>>(p.tasks, rp, ci, vv, x, y, p.partial, p.counters, gate, tm);
+  launch_spmv_out<T>(p, rp, ci, vv, x, StoreOut<T>{y}, gate, st, tm);
 }
 
 // ------------------------------------------------------------- cone tables
@@ -359,6 +367,10 @@ struct Solver : SolverBase {
   cudaGraph_t graph = nullptr;
   int64_t trace_rows = 0;
   int use_cond = 1;  // 0 in eager mode (kernels launched from the host, no graphs)
+  // the dual step runs as the epilogue of G xhat when the rows are long
+  // (16 nonzeros or more on average): there it costs the product nothing,
+  // while on short rows the epilogue's registers cost the product occupancy
+  bool dual_in_product = false;
   int64_t nk_a = 0, nk_b = 0, nk_top = 0;  // kernel nodes: attempt body, probe body, top level
   int64_t eager_a = 0, eager_b = 0;        // attempt / probe bodies run by the eager loop
   int64_t graph_launches = 0;
@@ -507,6 +519,7 @@ struct Solver : SolverBase {
       transpose(hrpT, drpT, dciT, dvT, n, m, hrp, drp, dci, dv);
     }
     nnz = hrp[m];
+    dual_in_product = nnz >= 16 * m;
     // ---- scaling (Ruiz + Pock-Chambolle), Sec. 2.6
     d1 = ar.alloc<double>(m);
     d2 = ar.alloc<double>(n);
@@ -888,12 +901,20 @@ struct Solver : SolverBase {
     const int gn = ew_grid(n), gm = ew_grid(m), gmx = ew_grid(std::max(m, n));
     k_primal<T><<<gn, kEwThreads, 0, s>>>(p, ctl, x, gty, xh);
     project<T>(cols, xh, xh, 1, d2, 1, 0, &ctl->g_attempt, nullptr, s);
-    launch_spmv<T>(planG, rp, ci, vv, xh, gxh, &ctl->g_attempt, s, timers ? timers + TM_SPMV_G : nullptr);
     // FP64: the dual iterate (onto diag(1/d1) K*) and the primal residual's
     // argument G xhat - h (onto diag(d1) K) are projected in one launch; the
     // residual is then also formed for rejected attempts, where it is unused
     const bool fuse = std::is_same<T, double>::value;
-    k_dual<T><<<gm, kEwThreads, 0, s>>>(p, ctl, y, gxh, gx, yh, fuse ? tm[0] : nullptr);
+    double* res = fuse ? tm[0] : nullptr;
+    KTimer* tg = timers ? timers + TM_SPMV_G : nullptr;
+    if (dual_in_product) {
+      // long rows: the dual step rides on the product's epilogue
+      launch_spmv_out<T>(planG, rp, ci, vv, xh, DualOut<T>{p, ctl, y, gx, gxh, yh, res},
+                         &ctl->g_attempt, s, tg);
+    } else {
+      launch_spmv<T>(planG, rp, ci, vv, xh, gxh, &ctl->g_attempt, s, tg);
+      k_dual<T><<<gm, kEwThreads, 0, s>>>(p, ctl, y, gxh, gx, yh, res);
+    }
     if (fuse)
       project<T>(rows, yh, reinterpret_cast<T*>(tm[0]), 2, d1, 1, 1, &ctl->g_attempt,
                  &ctl->g_attempt, s, true);
@@ -912,8 +933,8 @@ struct Solver : SolverBase {
     }
     project<double>(cols, tn[0], tn[0], 1, d2, 0, 1, &ctl->g_accept, nullptr, s);
     k_point_stats<T, false><<<gmx, kEwThreads, 0, s>>>(p, ctl, &ctl->g_accept, 0, ph, nullptr, nullptr, t0, part);
-    k_halpern<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, y, gx, gty, xh, yh, gxh, gtyh, x0, y0, gx0, gty0, xs, ys, trace);
-    k_loop_ctl<<<1, 1, 0, s>>>(ctl, hA, use_cond);
+    k_halpern<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, y, gx, gty, xh, yh, gxh, gtyh, x0, y0, gx0,
+                                            gty0, xs, ys, trace, hA, use_cond);
   }
 
   void rec_check_stats(cudaStream_t s) {

@@ -62,6 +62,18 @@ struct Acc<float> {
   PDCS_DEV double get() const { return (double)s - (double)comp; }
 };
 
+// Where a row's value goes: by default y[row]; a caller may pass a functor
+// with the same interface that also applies an elementwise update to the
+// row.  pre(row) issues the row's other loads before the product's, so their
+// latency overlaps it; the call then finishes the row.
+template <typename T>
+struct StoreOut {
+  T* y;
+  struct Pre {};
+  PDCS_DEV Pre pre(int64_t) const { return Pre{}; }
+  PDCS_DEV void operator()(int64_t row, double v, const Pre&) const { y[row] = (T)v; }
+};
+
 // Group sum over G consecutive lanes (G a power of two <= 32).
 template <int G>
 PDCS_DEV double group_sum(double v) {
@@ -70,16 +82,18 @@ PDCS_DEV double group_sum(double v) {
   return v;
 }
 
-template <typename T, int G>
+template <typename T, int G, typename Out>
 PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
                               const int32_t* __restrict__ ci, const T* __restrict__ vv,
-                              const T* __restrict__ x, T* __restrict__ y) {
+                              const T* __restrict__ x, const Out& out) {
   const int gid = threadIdx.x / G, lane = threadIdx.x % G, ng = kSpmvThreads / G;
   // every group runs the same number of trips so the shuffles stay converged
   const int64_t trips = (t.b - t.a + ng - 1) / ng;
   for (int64_t q = 0; q < trips; ++q) {
     const int64_t row = t.a + gid + q * ng;
     Acc<T> acc;
+    typename Out::Pre pr{};
+    if (lane == 0 && row < t.b) pr = out.pre(row);
     if (row < t.b) {
       const int64_t s = rp[row], e = rp[row + 1];
       constexpr int U = kSpmvUnroll;
@@ -99,51 +113,53 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
       for (; k < e; k += G) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
     }
     const double r = group_sum<G>(acc.get());
-    if (lane == 0 && row < t.b) y[row] = (T)r;
+    if (lane == 0 && row < t.b) out(row, r, pr);
   }
 }
 
-template <typename T>
+template <typename T, typename Out>
 PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
                         const int32_t* __restrict__ ci, const T* __restrict__ vv,
-                        const T* __restrict__ x, T* __restrict__ y, double* __restrict__ partial,
+                        const T* __restrict__ x, const Out& out, double* __restrict__ partial,
                         unsigned int* __restrict__ counters);
 
-// y = A x over the task list.  When `gate` is non-NULL and *gate == 0 the kernel
-// does nothing (used to skip products inside a captured graph).  partial /
-// counters are the scratch of kind-2 tasks (counters are left at zero).  tm,
-// when non-NULL, accumulates the launch's duration.
-template <typename T>
+// y = A x over the task list, each row's value handed to `out` (StoreOut:
+// y[row]).  When `gate` is non-NULL and *gate == 0 the kernel does nothing
+// (used to skip products inside a captured graph).  partial / counters are the
+// scratch of kind-2 tasks (counters are left at zero).  tm, when non-NULL,
+// accumulates the launch's duration.
+template <typename T, typename Out>
 __global__ void __launch_bounds__(kSpmvThreads)
 k_spmv(const SpmvTask* __restrict__ tasks, const int64_t* __restrict__ rp,
        const int32_t* __restrict__ ci, const T* __restrict__ vv, const T* __restrict__ x,
-       T* __restrict__ y, double* __restrict__ partial, unsigned int* __restrict__ counters,
+       Out out, double* __restrict__ partial, unsigned int* __restrict__ counters,
        const int* __restrict__ gate, KTimer* tm) {
   if (gate != nullptr && *gate == 0) return;
   ktimer_begin(tm);
-  spmv_task<T>(tasks[blockIdx.x], rp, ci, vv, x, y, partial, counters);
+  spmv_task<T, Out>(tasks[blockIdx.x], rp, ci, vv, x, out, partial, counters);
   ktimer_end(tm);
 }
 
-template <typename T>
+template <typename T, typename Out>
 PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
                         const int32_t* __restrict__ ci, const T* __restrict__ vv,
-                        const T* __restrict__ x, T* __restrict__ y, double* __restrict__ partial,
+                        const T* __restrict__ x, const Out& out, double* __restrict__ partial,
                         unsigned int* __restrict__ counters) {
   if (t.kind == 0) {
     const int64_t row = t.a + threadIdx.x;
     if (row < t.b) {
+      const typename Out::Pre pr = out.pre(row);
       const int64_t s = rp[row], e = rp[row + 1];
       Acc<T> acc;
       for (int64_t k = s; k < e; ++k) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
-      y[row] = (T)acc.get();
+      out(row, acc.get(), pr);
     }
     return;
   }
   if (t.kind == 1) {
-    if (t.g == 4) spmv_group_rows<T, 4>(t, rp, ci, vv, x, y);
-    else if (t.g == 8) spmv_group_rows<T, 8>(t, rp, ci, vv, x, y);
-    else spmv_group_rows<T, 32>(t, rp, ci, vv, x, y);
+    if (t.g == 4) spmv_group_rows<T, 4>(t, rp, ci, vv, x, out);
+    else if (t.g == 8) spmv_group_rows<T, 8>(t, rp, ci, vv, x, out);
+    else spmv_group_rows<T, 32>(t, rp, ci, vv, x, out);
     return;
   }
   // kind 2: chunk of a long row
@@ -167,7 +183,7 @@ PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
   double r[1] = {acc.get()};
   block_sum<1>(r, sh);
   if (t.nchunks == 1) {
-    if (threadIdx.x == 0) y[t.a] = (T)r[0];
+    if (threadIdx.x == 0) out(t.a, r[0], out.pre(t.a));
     return;
   }
   if (threadIdx.x == 0) partial[t.pbase + t.b] = r[0];
@@ -185,7 +201,7 @@ PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
       for (int j = threadIdx.x; j < t.nchunks; j += 32) s += __ldcg(partial + t.pbase + j);
       s = warp_sum(s);
       if (threadIdx.x == 0) {
-        y[t.a] = (T)s;
+        out(t.a, s, out.pre(t.a));
         counters[t.counter] = 0u;
       }
     }
