@@ -41,10 +41,10 @@ CHECK_FREQ = 64
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
 # (workload, precision, source digest of spmv.cuh at capture time); see profiles/.
 NCU_TRAFFIC = {
-    # profiles/k_spmv_portfolio_n100k_fp64.md: 257.5 MB per launch (mean of
-    # G xhat and G^T yhat) at n = 100,000, scaled by the algorithmic bytes
-    # (x 2.005) to the n = 200,000 workload
-    ("portfolio", "fp64", "419527a7d587b9d0"): 516.3e6,
+    # profiles/k_spmv_portfolio_n100k_fp64.md: 258.7 MB per launch (mean of
+    # G xhat with the fused dual step and G^T yhat) at n = 100,000, scaled by
+    # the algorithmic bytes (x 2.005) to the n = 200,000 workload
+    ("portfolio", "fp64", "a4527262d271f341"): 518.6e6,
 }
 
 

@@ -216,7 +216,9 @@ int pdcs_get_trace(pdcs_handle* handle, double* out, int64_t cap, int64_t* count
  * is timed from the start of its first CTA to the end of its last CTA with the
  * GPU's global nanosecond timer.  bytes_* are the algorithmic bytes of one
  * launch: values and column indices once, row pointers once, the gathered
- * vector and the result vector once each. */
+ * vector and the result vector once each; when the dual step runs in the
+ * epilogue of G xhat (problems averaging 16 or more nonzeros per row), g_bytes
+ * adds its per-row reads and writes. */
 typedef struct {
   int64_t g_launches;    /* G xhat products (one per attempt) */
   double g_seconds;

@@ -371,6 +371,7 @@ struct Solver : SolverBase {
   // (16 nonzeros or more on average): there it costs the product nothing,
   // while on short rows the epilogue's registers cost the product occupancy
   bool dual_in_product = false;
+  int64_t cone_rows = 0;  // rows whose cone is SOC or exponential
   int64_t nk_a = 0, nk_b = 0, nk_top = 0;  // kernel nodes: attempt body, probe body, top level
   int64_t eager_a = 0, eager_b = 0;        // attempt / probe bodies run by the eager loop
   int64_t graph_launches = 0;
@@ -594,6 +595,8 @@ struct Solver : SolverBase {
     rk = ar.alloc<uint8_t>(m);
     ck = ar.alloc<uint8_t>(n);
     copy_in(rk, hrk.data(), m, st);
+    cone_rows = 0;
+    for (int64_t i = 0; i < m; ++i) cone_rows += hrk[i] >= RK_SOC;
     copy_in(ck, hck.data(), n, st);
     fill_table(rows, rsoc, rbig, rexp, rexpd, d1, m);
     fill_table(cols, csoc, cbig, cexp, cexpd, d2, n);
@@ -848,6 +851,10 @@ struct Solver : SolverBase {
     std::memset(pr, 0, sizeof(*pr));
     const double vb = (double)sizeof(T);
     pr->g_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(m + 1) + vb * (double)(n + m);
+    // the dual step in the product's epilogue: y, G x, h and the row kind
+    // read, yhat written per row, G xhat - h on the cone rows (FP64)
+    if (dual_in_product)
+      pr->g_bytes += (double)m * (4.0 * vb + 1.0) + (std::is_same<T, double>::value ? 8.0 * (double)cone_rows : 0.0);
     pr->gt_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(n + 1) + vb * (double)(n + m);
     pr->nnz_flops = 2.0 * (double)nnz;
     pr->graph_launches = graph_launches;
