@@ -54,11 +54,13 @@ DIMS = [300, 136, 136, 200]  # ragged sizes: partial 128-tiles and 64-wide K blo
 DIMS_SPLIT = [2000, 136, 136, 4000]
 
 
-@pytest.mark.parametrize("dims", [DIMS, DIMS_SPLIT])
-def test_forward_matches_the_reference(dims):
+@pytest.mark.parametrize("dims,batch", [(DIMS, 40), (DIMS_SPLIT, 40), (DIMS, 200)])
+def test_forward_matches_the_reference(dims, batch):
+    """batch 200: two 128-row tiles of the activations (a TMA box past the
+    last row, zero-filled)."""
     P = _P()
-    net, params, rng = _net(P, dims, 40)
-    X = rng.standard_normal((40, dims[0]))
+    net, params, rng = _net(P, dims, batch)
+    X = rng.standard_normal((batch, dims[0]))
     with net:
         Y = net.predict(X)
     R = _ref_forward_bf16(params, X)
