@@ -410,6 +410,8 @@ PDCS_HD double soc_initial_guess(double s0, double s1, double v0, double e0) {
   return x;
 }
 
+constexpr double kSocStepTol = 1e-6;
+
 // CTA-wide projection of one block held in registers: each thread owns EPT
 // elements (index = threadIdx.x + k * NT); element 0 is the head.  `sh` is
 // scratch: 8 doubles of broadcast slots, then a block-reduction area of
@@ -469,7 +471,11 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
   const double c0 = (v0 * sc) * (v0 * sc) * e02;
   const bool pos = v0 > 0.0;
   double lo = 0.0, hi = pos ? 0.5 * e02 : 1.0 / e02;
+  const double top = hi;
   double x = soc_initial_guess(s[0], s[1], v0, e0);
+  // Halley steps until one is below kSocStepTol of x's distance to the ends
+  // of (0, top): cubic convergence leaves an error of order kSocStepTol^3 of
+  // that distance after it, below what the FP64 sums resolve
   for (int it = 0; it < 200; ++it) {
     double f[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -483,14 +489,16 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
     block_sum<3>(f, red);
     if (tid == 0) {  // scalar step once per CTA, broadcast
       int stop = 0;
+      const double dist = fmin(x, top - x);
       const double step = soc_halley_step(pos, f, c0, e02, x, lo, hi);
       if (step == 0.0) {
         stop = 1;
       } else {
         double xn = x + step;
-        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        const bool inside = xn > lo && xn < hi;
+        if (!inside) xn = 0.5 * (lo + hi);
         x = xn;
-        if (hi - lo <= 1e-15 * hi) stop = 1;
+        if ((inside && fabs(step) <= kSocStepTol * dist) || hi - lo <= 1e-15 * hi) stop = 1;
       }
       sh[2] = x; sh[3] = lo; sh[4] = hi; sh[5] = (double)stop;
     }
