@@ -486,7 +486,21 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
         soc_secular_terms(pos, a, b, x, f);
       }
     }
-    block_sum<3>(f, red);
+    // block sums of the three terms and the scalar step with two barriers:
+    // warp 0 adds the staged values, thread 0 steps and publishes x, the
+    // bracket and the stop flag (the next iteration's staging happens after
+    // every thread has read them)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) red[k * NT + tid] = f[k];
+    __syncthreads();
+    if (tid < 32) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double a = 0.0;
+        for (int t = tid; t < NT; t += 32) a += red[k * NT + t];
+        f[k] = warp_sum(a);
+      }
+    }
     if (tid == 0) {  // scalar step once per CTA, broadcast
       int stop = 0;
       const double dist = fmin(x, top - x);
@@ -504,9 +518,7 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
     }
     __syncthreads();
     x = sh[2]; lo = sh[3]; hi = sh[4];
-    const bool stop = sh[5] != 0.0;
-    __syncthreads();
-    if (stop) break;
+    if (sh[5] != 0.0) break;
   }
   const double mu2 = pos ? 2.0 * x : 1.0 / x;  // 2 mu
 #pragma unroll
