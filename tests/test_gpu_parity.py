@@ -216,6 +216,19 @@ def test_fp32_bulk_mode_reaches_tolerance_on_tiny_conic():
     assert abs(g["pobj"] - opt) <= 1e-4 * (1 + abs(opt))
 
 
+def test_fp32_bulk_mode_long_rows_dual_in_product():
+    """A portfolio with 16+ nonzeros per row (the dual step runs in the
+    epilogue of G xhat) in FP32 bulk: it reaches 1e-4 and its objective
+    agrees with the FP64 solve's."""
+    prob = workloads.portfolio(n=2000, k=40, n_limits=10, limit_density=0.01, seed=13)
+    assert len(prob["val"]) >= 16 * prob["m"]
+    P = _gpu()
+    g32 = P.solve(prob, max_iter=200000, precision="fp32", rel_tol=1e-4, time_limit=120.0)
+    g64 = P.solve(prob, max_iter=200000, rel_tol=1e-6, time_limit=120.0)
+    assert g32["exit_code"] == 0 and g64["exit_code"] == 0
+    assert abs(g32["pobj"] - g64["pobj"]) <= 1e-3 * (1 + abs(g64["pobj"]))
+
+
 def test_problem_without_constraints():
     """m = 0: min c^T x over a box."""
     P = _gpu()
