@@ -121,12 +121,14 @@ PDCS_DEV void b_proj_exp(B* v, const int64_t* __restrict__ starts, const uint8_t
 }
 
 // The cone blocks of one instance's rows / columns (the product cone's zero /
-// nonnegative / box parts are projected by the element functions).
+// nonnegative / box parts are projected by the element functions).  The
+// barrier between the two lists is taken only when both are present (the
+// instance fields are the same for every thread of the CTA).
 template <typename T, typename B>
 PDCS_DEV void b_project_rows(const BatchArgs<T>& a, const BInst& I, B* v, const double* d, int inv,
                              int dual, double* sh) {
   b_proj_exp(v, a.exp_rs, a.exp_risd, I.exp_r0, I.exp_rn, d, inv, dual);
-  __syncthreads();
+  if (I.exp_rn > 0 && I.soc_rn > 0) __syncthreads();
   b_proj_soc(v, a.soc_rs, a.soc_rd, I.soc_r0, I.soc_rn, d, inv, sh);
 }
 
@@ -134,7 +136,7 @@ template <typename T, typename B>
 PDCS_DEV void b_project_cols(const BatchArgs<T>& a, const BInst& I, B* v, const double* d, int inv,
                              int dual, double* sh) {
   b_proj_exp(v, a.exp_cs, a.exp_cisd, I.exp_c0, I.exp_cn, d, inv, dual);
-  __syncthreads();
+  if (I.exp_cn > 0 && I.soc_cn > 0) __syncthreads();
   b_proj_soc(v, a.soc_cs, a.soc_cd, I.soc_c0, I.soc_cn, d, inv, sh);
 }
 
@@ -148,15 +150,20 @@ PDCS_DEV void b_point_stats(const BatchArgs<T>& a, const BInst& I, Ctl& sc, int 
   PDCS_BLOCK_LOOP(i, I.r0, I.r0 + I.m) res_prep_row(p, pt, tr, i);
   PDCS_BLOCK_LOOP(j, I.c0, I.c0 + I.n) res_prep_col(p, pt, tr, j);
   __syncthreads();
+  const bool ccones = I.exp_cn + I.soc_cn > 0;  // uniform: the instance's column cones
   b_project_rows(a, I, tr.tm, p.d1, 0, 0, sh);
   __syncthreads();
-  b_project_cols(a, I, tr.tn, p.d2, 0, 1, sh);
-  __syncthreads();
+  if (ccones) {
+    b_project_cols(a, I, tr.tn, p.d2, 0, 1, sh);
+    __syncthreads();
+  }
   if (FULL) {
     b_project_rows(a, I, tr.um, (const double*)nullptr, 0, 0, sh);
     __syncthreads();
-    b_project_cols(a, I, tr.un, (const double*)nullptr, 0, 1, sh);
-    __syncthreads();
+    if (ccones) {
+      b_project_cols(a, I, tr.un, (const double*)nullptr, 0, 1, sh);
+      __syncthreads();
+    }
   }
   double s[kStatSums], mx[kStatMax];
 #pragma unroll
@@ -180,8 +187,10 @@ PDCS_DEV void b_attempt(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* 
   const double tau = sc.eta / sc.omega, sigma = sc.eta * sc.omega;
   PDCS_BLOCK_LOOP(j, c0, c1) primal_elem(p, tau, a.x, a.gty, a.xh, j);
   __syncthreads();
-  b_project_cols(a, I, a.xh, p.d2, 1, 0, sh);
-  __syncthreads();
+  if (I.exp_cn + I.soc_cn > 0) {  // column cones: their projection, then a barrier
+    b_project_cols(a, I, a.xh, p.d2, 1, 0, sh);
+    __syncthreads();
+  }
   b_spmv(a.rp, a.ci, a.vv, a.xh, a.gxh, r0, I.m, I.tile);
   __syncthreads();
   PDCS_BLOCK_LOOP(i, r0, r1) dual_elem(p, sigma, a.y, a.gxh, a.gx, a.yh, i);
@@ -242,8 +251,10 @@ PDCS_DEV void b_check(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh
       PDCS_BLOCK_LOOP(j, c0, c1) probe_prep_col(p, pt, tt, a.px[c], j);
       PDCS_BLOCK_LOOP(i, r0, r1) probe_prep_row(p, pt, ts, a.py[c], i);
       __syncthreads();
-      b_project_cols(a, I, a.px[c], p.d2, 1, 0, sh);
-      __syncthreads();
+      if (I.exp_cn + I.soc_cn > 0) {
+        b_project_cols(a, I, a.px[c], p.d2, 1, 0, sh);
+        __syncthreads();
+      }
       b_project_rows(a, I, a.py[c], p.d1, 1, 1, sh);
       __syncthreads();
     }
