@@ -93,3 +93,54 @@ def unscaled_errors(sp_, xt, yt):
     return dict(abs_p=abs_p, abs_d=abs_d, abs_gap=abs_gap, rel_p=rel_p, rel_d=rel_d,
                 rel_gap=rel_gap, max_rel=max(rel_p, rel_d, rel_gap), pobj=pobj, dobj=dobj,
                 x=x, y=y, Gx=Gx)
+
+
+def _proj_recession_box(v, lo, hi):
+    """Projection onto the recession cone of the box [lo, hi]: {0} where both
+    bounds are finite, R_+ (R_-) where only lo (hi) is finite, R otherwise."""
+    out = v.copy()
+    lf, uf = np.isfinite(lo), np.isfinite(hi)
+    out[lf & uf] = 0.0
+    m = lf & ~uf
+    out[m] = np.maximum(v[m], 0.0)
+    m = ~lf & uf
+    out[m] = np.minimum(v[m], 0.0)
+    return out
+
+
+def infeasibility_ratios(sp_, dxt, dyt):
+    """Ratios of the infeasibility tests of Sec. 3.2.3 (reading c19) for the
+    direction (dxt, dyt) in the solver's scaled variables (the change of the
+    restart candidate between two checks), evaluated on the unscaled
+    SOC-reformulated problem after x = D2 dxt, y = D1 dyt.
+
+    Primal infeasibility (a Farkas ray y): the dual error of eq.
+    PDCS_terminate_tolerance_abs for the homogeneous problem (c = 0, so
+    lambda = -G^T y), together with the distance of y from the dual row cone,
+    over the dual objective y^T h + l^T lambda_1^+ - u^T lambda_1^- (finite
+    bounds); +inf unless that objective is positive.
+    Dual infeasibility (a ray x): the relative primal error of eq.
+    PDCS_terminate_tolerance_rel for the homogeneous problem (h = 0), together
+    with the distance of x from the recession cone of [l, u] x K_p, over
+    -c^T x; +inf unless -c^T x is positive.
+    Returns (primal_ratio, dual_ratio)."""
+    base = sp_.base
+    nb = base.nb
+    x = sp_.d2 * dxt
+    y = sp_.d1 * dyt
+    inf = lambda v: float(np.max(np.abs(v))) if v.size else 0.0
+    lam = -(base.G.T @ y)
+    lam1 = lam[:nb]
+    ed1 = lam1 - proj_lambda(lam1, lambda_kind(base.lo, base.hi))
+    ed2 = lam[nb:] - proj_cone_product(lam[nb:], base.col_cones, np.ones(base.n - nb), dual=True)
+    ey = y - proj_cone_product(y, base.row_cones, np.ones(base.m), dual=True)
+    dobj = dual_objective(base.h, y, base.lo, base.hi, lam1)
+    num_p = max(inf(ed1), inf(ed2), inf(ey))
+    gx = base.G @ x
+    pg = proj_cone_product(gx, base.row_cones, np.ones(base.m), dual=False)
+    rel_p = inf(gx - pg) / (1.0 + max(inf(gx), inf(pg)))
+    ex1 = x[:nb] - _proj_recession_box(x[:nb], base.lo, base.hi)
+    ex2 = x[nb:] - proj_cone_product(x[nb:], base.col_cones, np.ones(base.n - nb), dual=False)
+    num_d = max(rel_p, inf(ex1), inf(ex2))
+    mpobj = -float(base.c @ x)
+    return (num_p / dobj if dobj > 0 else np.inf), (num_d / mpobj if mpobj > 0 else np.inf)

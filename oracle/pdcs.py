@@ -34,16 +34,136 @@ Readings where the paper is silent or inconsistent (listed in the design notes):
   c15 the candidate is tested for termination and returned.
   ref the reference gap of a restart period is the candidate's gap at the check
       that started the period; N uses the last accepted step size.
+  c19 infeasibility (Sec. 3.2.3 eps_*_infeasible_* options) is tested at every
+      check after the optimality test, on the change of the restart candidate
+      since the previous check (the direction in which the iterates of an
+      infeasible problem diverge), with the paper's ratios taken on the
+      homogeneous problem: err_abs,d (c = 0, plus the dual-cone violation of
+      the y change) over the dual objective, and err_rel,p (h = 0, plus the
+      violation of the recession cone of X by the x change) over -c^T x
+      (kkt.infeasibility_ratios).  Taken on the candidate itself the ratio
+      err_abs,d / (dual objective) is 0 for every y when all bounds are
+      finite, so it would call feasible problems infeasible.  High accuracy:
+      the ratio test alone (exit 3 / 5); low accuracy: also a rising trend,
+      the candidates' dual objective (resp. -c^T x) strictly increasing over
+      the last INFEAS_TREND_CHECKS checks (exit 2 / 4).
+  c21 use_adaptive_step_size_weight = False: every attempt is accepted with
+      the fixed step eta = 1 / sqrt(||G||_1 ||G||_inf) (induced norms: largest
+      column / row absolute sum), an upper bound on 1 / ||G||_2, so that
+      tau sigma ||G||_2^2 <= 1.
+  c22 restart criteria: at multiples of check_freq (the duality-gap restart
+      frequency) with use_duality_gap_restart the criterion is rho^N; at
+      multiples of kkt_restart_freq with use_kkt_restart (and not a gap check)
+      it is KKT_omega, as in the fallback of reading c10; at other checks
+      (termination only) restart condition 3 alone can fire.  A gap that was
+      not computed (a KKT-criterion check) counts like a negative one for c10.
 """
 import time
 
 import numpy as np
 
 from .cones import proj_box, proj_cone_product
-from .kkt import scaled_errors, unscaled_errors, kkt_omega
+from .kkt import scaled_errors, unscaled_errors, kkt_omega, infeasibility_ratios
 from .problem import ScaledProblem, apply_block_T
 
 EXIT_OPTIMAL, EXIT_MAX_ITER, EXIT_TIME_LIMIT, EXIT_NUMERICAL = 0, 1, 6, 8
+EXIT_PRIMAL_INFEAS_LOW, EXIT_PRIMAL_INFEAS_HIGH = 2, 3
+EXIT_DUAL_INFEAS_LOW, EXIT_DUAL_INFEAS_HIGH = 4, 5
+INFEAS_TREND_CHECKS = 3          # reading c19
+
+# Restart thresholds of Sec. 2.3 and the primal-weight constants of Sec. 2.5.
+BETA_SUFFICIENT, BETA_NECESSARY, BETA_ARTIFICIAL = 0.4, 0.8, 0.223
+PW_THETA, PW_GUARD, PW_MAX, PW_MIN = 0.5, 1e-10, 1e5, 1e-5
+
+
+# -- controller scalars (each is pinned by hand-derived values in the tests) --
+def step_bound(dx2, dy2, inter, omega):
+    """eta_bar of Function 1: (1/2) ||(dx, dy)||_omega^2 / |dy^T G dx| with
+    ||z||_omega^2 = omega ||dx||^2 + ||dy||^2 / omega (eq. adaptive_step_size);
+    +inf when the product vanishes (reading c4)."""
+    inter = abs(inter)
+    num = 0.5 * (omega * dx2 + dy2 / omega)
+    return num / inter if inter > 0 else np.inf
+
+
+def next_step_size(eta, eta_bar, kbar):
+    """eta' of Function 1; kbar already counts the current attempt (reading c3)."""
+    return min((1.0 - (kbar + 1) ** -0.3) * eta_bar, (1.0 + (kbar + 1) ** -0.6) * eta)
+
+
+def reflection(max_err):
+    """Reflection parameter, eq. adaptive_reflection: Proj_[0,1](-0.1 log10(maxErr) + 0.2)."""
+    if max_err <= 0:
+        return 1.0
+    return float(min(1.0, max(0.0, -0.1 * np.log10(max_err) + 0.2)))
+
+
+def halpern_step(k, beta, zhat, z, z0):
+    """Reflected Halpern step of Algorithm 1:
+    (k+1)/(k+2) ((1+beta) zhat - beta z) + z0 / (k+2)."""
+    a = (k + 1.0) / (k + 2.0)
+    return a * ((1.0 + beta) * zhat - beta * z) + z0 / (k + 2.0)
+
+
+def initialize_primal_weight(c_norm, h_norm):
+    """InitializePrimalWeight of Sec. 2.5 from ||c||_2 and ||h||_2."""
+    return c_norm / h_norm if (c_norm > PW_GUARD and h_norm > PW_GUARD) else 1.0
+
+
+def primal_weight_update(dx, dy, omega, omega0):
+    """PrimalWeightUpdate of Sec. 2.5 (theta = 0.5) with the reset to omega0
+    outside [1e-5, 1e5]; dx, dy = ||x^{t,0} - x^{t-1,0}||, ||y^{t,0} - y^{t-1,0}||."""
+    if dx > PW_GUARD and dy > PW_GUARD:
+        omega = float(np.exp(PW_THETA * np.log(dy / dx) + (1.0 - PW_THETA) * np.log(omega)))
+    if omega > PW_MAX or omega < PW_MIN:
+        omega = omega0
+    return omega
+
+
+def restart_conditions(val, ref, prev, k, kbar):
+    """The three restart conditions of Sec. 2.3 for the candidate's measure val
+    against the anchor's ref (None in the first period, reading c8) and the
+    previous candidate's prev (None if none yet in this period); k = inner
+    iterations, kbar = all attempts.  Returns (sufficient, necessary, long)."""
+    cond3 = k >= BETA_ARTIFICIAL * kbar
+    if ref is None:
+        return False, False, cond3
+    cond1 = val <= BETA_SUFFICIENT * ref
+    cond2 = (prev is not None) and val <= BETA_NECESSARY * ref and val > prev
+    return cond1, cond2, cond3
+
+
+def fixed_step_size(G):
+    """Step of the non-adaptive mode (reading c21): 1 / sqrt(||G||_1 ||G||_inf)."""
+    if G.nnz == 0:
+        return 1.0
+    A = abs(G)
+    n1 = float(np.max(np.asarray(A.sum(axis=0)).ravel()))
+    ninf = float(np.max(np.asarray(A.sum(axis=1)).ravel()))
+    return 1.0 / np.sqrt(n1 * ninf)
+
+
+def _rising(seq, count):
+    s = seq[-(count + 1):]
+    return len(s) == count + 1 and all(b > a for a, b in zip(s, s[1:]))
+
+
+def infeasibility_exit(ratios, dobj_hist, mpobj_hist, opts):
+    """Sec. 3.2.3 infeasibility tests (reading c19): ratios = (primal, dual)
+    ratio of the candidate's change since the previous check
+    (kkt.infeasibility_ratios); dobj_hist / mpobj_hist hold the dual
+    objective / -c^T x of the candidates of every check so far, this one
+    included.  Returns an exit code of Table 1 (2 to 5) or None."""
+    pr, dr = ratios
+    if pr < opts.eps_primal_infeasible_high_acc:
+        return EXIT_PRIMAL_INFEAS_HIGH
+    if dr < opts.eps_dual_infeasible_high_acc:
+        return EXIT_DUAL_INFEAS_HIGH
+    if pr < opts.eps_primal_infeasible_low_acc and _rising(dobj_hist, INFEAS_TREND_CHECKS):
+        return EXIT_PRIMAL_INFEAS_LOW
+    if dr < opts.eps_dual_infeasible_low_acc and _rising(mpobj_hist, INFEAS_TREND_CHECKS):
+        return EXIT_DUAL_INFEAS_LOW
+    return None
 
 
 class Options:
@@ -60,8 +180,16 @@ class Options:
         self.pc_alpha = 1.0
         self.method = "average"
         self.use_adaptive_restart = True
-        self.check_freq = 64
+        self.check_freq = 64                 # duality-gap restart / termination period
         self.bisect_rel_tol = 1e-6
+        self.use_adaptive_step_size_weight = True
+        self.use_duality_gap_restart = True
+        self.use_kkt_restart = False
+        self.kkt_restart_freq = 2000
+        self.eps_primal_infeasible_low_acc = 1e-12
+        self.eps_dual_infeasible_low_acc = 1e-12
+        self.eps_primal_infeasible_high_acc = 1e-16
+        self.eps_dual_infeasible_high_acc = 1e-16
         for k, v in kw.items():
             if not hasattr(self, k):
                 raise KeyError(k)
@@ -77,12 +205,11 @@ class Oracle:
         self.sp = ScaledProblem(prob, o.use_preconditioner, o.ruiz_iters, o.pc_alpha)
         sp_ = self.sp
         # Sec. 2.5 InitializePrimalWeight on the rescaled data.
-        nc = np.linalg.norm(sp_.c)
-        nh = np.linalg.norm(sp_.h)
-        self.omega0 = nc / nh if (nc > 1e-10 and nh > 1e-10) else 1.0
+        self.omega0 = initialize_primal_weight(np.linalg.norm(sp_.c), np.linalg.norm(sp_.h))
         # Algorithm 1 Require: eta_hat = 1 / ||G||_inf (reading c2: max |entry|).
         gmax = np.max(np.abs(sp_.G.data)) if sp_.G.nnz else 1.0
         self.eta0 = 1.0 / gmax
+        self.eta_fixed = fixed_step_size(sp_.G)                    # reading c21
 
     # -- projections onto X = [lhat, uhat] x D2^{-1} K_p and Y = (D1 K_r)^* ----
     def proj_X(self, v):
@@ -106,15 +233,18 @@ class Oracle:
     # -- Function 1 ----------------------------------------------------------
     def adaptive_step(self, x, y, omega, eta, kbar):
         sp_ = self.sp
+        if not self.opts.use_adaptive_step_size_weight:              # reading c21
+            kbar += 1
+            eta = self.eta_fixed
+            xh, yh = self.one_pdhg(x, y, eta / omega, eta * omega)
+            return xh, yh, eta, eta, kbar
         while True:
             kbar += 1                                                # reading c3
             xh, yh = self.one_pdhg(x, y, eta / omega, eta * omega)
             dx = xh - x
             dy = yh - y
-            inter = abs(float(dy @ (sp_.G @ dx)))
-            num = 0.5 * (omega * float(dx @ dx) + float(dy @ dy) / omega)
-            eta_bar = num / inter if inter > 0 else np.inf           # reading c4
-            eta_p = min((1.0 - (kbar + 1) ** -0.3) * eta_bar, (1.0 + (kbar + 1) ** -0.6) * eta)
+            eta_bar = step_bound(float(dx @ dx), float(dy @ dy), float(dy @ (sp_.G @ dx)), omega)
+            eta_p = next_step_size(eta, eta_bar, kbar)
             if eta < eta_bar:
                 return xh, yh, eta, eta_p, kbar
             eta = eta_p
@@ -122,9 +252,7 @@ class Oracle:
     # -- eq. adaptive_reflection ----------------------------------------------
     @staticmethod
     def reflection(max_err):
-        if max_err <= 0:
-            return 1.0
-        return float(min(1.0, max(0.0, -0.1 * np.log10(max_err) + 0.2)))
+        return reflection(max_err)
 
     # -- Definition 2.1 / Algorithm 3 ------------------------------------------
     def normalized_gap(self, x, y, r, tau, sigma):
@@ -186,7 +314,7 @@ class Oracle:
         y = np.zeros(sp_.m) if y0 is None else apply_block_T(np.asarray(y0, float), sp_.row_T) / sp_.d1
         xa, ya = x.copy(), y.copy()            # anchor z^{t,0}
         omega = self.omega0
-        eta_hat = self.eta0
+        eta_hat = self.eta0 if o.use_adaptive_step_size_weight else self.eta_fixed
         kbar = 0
         it = 0                                  # accepted iterations, all periods
         t_period = 0
@@ -200,6 +328,9 @@ class Oracle:
         xc, yc = x.copy(), y.copy()
         exit_code = None
         eta = eta_hat
+        dobj_hist, mpobj_hist = [], []          # candidates' objectives (reading c19)
+        any_check = False
+        last_cand = None                        # candidate of the previous check
 
         def capture():
             return dict(x=x.copy(), y=y.copy(), x0=xa.copy(), y0=ya.copy(), xs=xs.copy(),
@@ -217,10 +348,9 @@ class Oracle:
         while True:
             xh, yh, eta, eta_hat, kbar = self.adaptive_step(x, y, omega, eta_hat, kbar)
             errh = scaled_errors(sp_, xh, yh)
-            beta = self.reflection(errh["max_err"])
-            a = (k + 1.0) / (k + 2.0)
-            x = a * ((1.0 + beta) * xh - beta * x) + xa / (k + 2.0)
-            y = a * ((1.0 + beta) * yh - beta * y) + ya / (k + 2.0)
+            beta = reflection(errh["max_err"])
+            x = halpern_step(k, beta, xh, x, xa)
+            y = halpern_step(k, beta, yh, y, ya)
             wsum += eta
             xs += eta * x
             ys += eta * y
@@ -228,26 +358,35 @@ class Oracle:
             it += 1
             rec = dict(iter=it, kbar=kbar, period=t_period, eta=eta, eta_hat=eta_hat, beta=beta,
                        omega=omega, max_err=errh["max_err"], check=0, cand_avg=-1,
-                       restart=0, rho_c=np.nan)
-            if it % o.check_freq == 0:
+                       restart=0, rho_c=np.nan, fallback=0)
+            gap_check = o.use_duality_gap_restart and it % o.check_freq == 0
+            kkt_check = o.use_kkt_restart and it % o.kkt_restart_freq == 0
+            if it % o.check_freq == 0 or kkt_check:
                 rec["check"] = 1
+                any_check = True
                 tau, sigma = eta / omega, eta * omega
                 xbar, ybar = xs / wsum, ys / wsum
-                r_h = self.n_norm(x - xa, y - ya, tau, sigma)
-                rho_h = self.normalized_gap(x, y, r_h, tau, sigma)
+                avg = o.method == "average"
                 err_h = scaled_errors(sp_, x, y)
-                if o.method == "average":
-                    r_a = self.n_norm(xbar - xa, ybar - ya, tau, sigma)
-                    rho_a = self.normalized_gap(xbar, ybar, r_a, tau, sigma)
-                    err_a = scaled_errors(sp_, xbar, ybar)
+                err_a = scaled_errors(sp_, xbar, ybar) if avg else None
+                if gap_check:
+                    r_h = self.n_norm(x - xa, y - ya, tau, sigma)
+                    rho_h = self.normalized_gap(x, y, r_h, tau, sigma)
+                    if avg:
+                        r_a = self.n_norm(xbar - xa, ybar - ya, tau, sigma)
+                        rho_a = self.normalized_gap(xbar, ybar, r_a, tau, sigma)
+                    else:
+                        rho_a = np.inf
                 else:
-                    rho_a, err_a = np.inf, None
-                used = [rho_h] + ([rho_a] if o.method == "average" else [])
+                    rho_h = np.nan                                   # reading c22
+                    rho_a = np.nan if avg else np.inf
+                used = [rho_h] + ([rho_a] if avg else [])
                 if rho_ref is not None:
                     used.append(rho_ref[0])
                 if prev is not None:
                     used.append(prev[0])
-                fallback = any(v < 0 for v in used)                  # reading c10
+                fallback = any(not (v >= 0) for v in used)           # readings c10, c22
+                rec["fallback"] = int(fallback)
                 if fallback:
                     m_h = kkt_omega(err_h, omega)
                     m_a = kkt_omega(err_a, omega) if err_a is not None else np.inf
@@ -264,32 +403,34 @@ class Oracle:
                 ue = unscaled_errors(sp_, xc, yc)
                 done = ue["max_rel"] <= o.rel_tol and (not o.require_abs or max(
                     ue["abs_p"], ue["abs_d"], ue["abs_gap"]) <= o.abs_tol)
+                dobj_hist.append(ue["dobj"])
+                mpobj_hist.append(-ue["pobj"])
                 if done:
                     exit_code = EXIT_OPTIMAL
                 elif not np.isfinite(ue["max_rel"]):
                     exit_code = EXIT_NUMERICAL
+                elif last_cand is not None:
+                    ratios = infeasibility_ratios(sp_, xc - last_cand[0], yc - last_cand[1])
+                    rec["infeas"] = ratios
+                    exit_code = infeasibility_exit(ratios, dobj_hist, mpobj_hist, o)
+                last_cand = (xc.copy(), yc.copy())
                 if exit_code is None:
                     do_restart = False
                     if o.use_adaptive_restart:
-                        cond3 = k >= 0.223 * kbar
-                        if rho_ref is None:
-                            do_restart = cond3                        # reading c8
-                        else:
+                        ref = pv = None                               # reading c8
+                        if rho_ref is not None:
                             ref = kkt_omega(rho_ref[1], omega) if fallback else rho_ref[0]
-                            pv = None
-                            if prev is not None:
-                                pv = kkt_omega(prev[1], omega) if fallback else prev[0]
-                            cond1 = val_c <= 0.4 * ref
-                            cond2 = (pv is not None) and val_c <= 0.8 * ref and val_c > pv
-                            do_restart = cond1 or cond2 or cond3
+                        if prev is not None:
+                            pv = kkt_omega(prev[1], omega) if fallback else prev[0]
+                        cond1, cond2, cond3 = restart_conditions(val_c, ref, pv, k, kbar)
+                        if not (gap_check or kkt_check):
+                            cond1 = cond2 = False                     # reading c22
+                        do_restart = cond1 or cond2 or cond3
                     if do_restart:
                         rec["restart"] = 1
                         dx = np.linalg.norm(xc - xa)
                         dy = np.linalg.norm(yc - ya)
-                        if dx > 1e-10 and dy > 1e-10:
-                            omega = float(np.exp(0.5 * np.log(dy / dx) + 0.5 * np.log(omega)))
-                        if omega > 1e5 or omega < 1e-5:
-                            omega = self.omega0
+                        omega = primal_weight_update(dx, dy, omega, self.omega0)
                         rho_ref = (rho_c, err_c)
                         prev = None
                         xa, ya = xc.copy(), yc.copy()
@@ -316,9 +457,10 @@ class Oracle:
             if time.perf_counter() - t_start > o.time_limit:
                 exit_code = EXIT_TIME_LIMIT
                 break
-        if exit_code != EXIT_OPTIMAL:
+        if exit_code not in (EXIT_OPTIMAL, EXIT_PRIMAL_INFEAS_LOW, EXIT_PRIMAL_INFEAS_HIGH,
+                             EXIT_DUAL_INFEAS_LOW, EXIT_DUAL_INFEAS_HIGH):
             # Return the most recent candidate; before the first check, z itself.
-            if it < o.check_freq:
+            if not any_check:
                 xc, yc = x.copy(), y.copy()
         ue = unscaled_errors(sp_, xc, yc)
         xo = apply_block_T(ue["x"], sp_.col_T)

@@ -304,3 +304,29 @@ def test_trace_records_restart_at_first_check_and_monotone_counters():
     assert all(t["check"] == (1 if t["iter"] % 32 == 0 else 0) for t in tr)
     assert all(b["kbar"] >= a["kbar"] + 1 for a, b in zip(tr, tr[1:]))
     assert all(0.0 <= t["beta"] <= 1.0 for t in tr)
+
+
+# ------------------------------------------- option modes (readings c21, c22)
+@pytest.mark.parametrize("opts", [
+    dict(use_adaptive_step_size_weight=False),
+    dict(use_kkt_restart=True, kkt_restart_freq=48),
+    dict(use_duality_gap_restart=False, use_kkt_restart=True, kkt_restart_freq=64),
+    dict(use_duality_gap_restart=False),
+])
+def test_option_modes_reach_planted_optimum(opts):
+    p = workloads.tiny_conic(seed=11, m_nonneg=16, soc_rows=(4, 5), nb=24, soc_cols=(4, 3),
+                             density=0.2)
+    tr = []
+    res = _solve(p, max_iter=60000, trace=tr, **opts)
+    assert res["exit_code"] == 0
+    opt = p["meta"]["opt"]
+    assert abs(res["pobj"] - opt) <= 1e-5 * (1 + abs(opt))
+    checks = [r for r in tr if r["check"]]
+    if not opts.get("use_adaptive_step_size_weight", True):
+        assert res["attempts"] == res["iters"]          # every attempt accepted
+        assert len({r["eta"] for r in tr}) == 1
+    if opts.get("use_kkt_restart") and not opts.get("use_duality_gap_restart", True):
+        assert checks and all(r["fallback"] == 1 for r in checks)   # KKT_omega throughout
+    if opts.get("use_kkt_restart") and opts.get("use_duality_gap_restart", True):
+        kkt_only = [r for r in checks if r["iter"] % 64 != 0]
+        assert kkt_only and all(r["fallback"] == 1 for r in kkt_only)
