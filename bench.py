@@ -39,13 +39,9 @@ METRIC = "time to 1e-6 rel. KKT & PDHG iters/s; batched and warm-start vs plain 
 UNIT = "PDHG iterations/s"
 CHECK_FREQ = 64
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
-# (workload, precision, source digest of spmv.cuh at capture time); see profiles/.
-NCU_TRAFFIC = {
-    # profiles/k_spmv_portfolio_n100k_fp64.md: 258.7 MB per launch (mean of
-    # G xhat with the fused dual step and G^T yhat) at n = 100,000, scaled by
-    # the algorithmic bytes (x 2.005) to the n = 200,000 workload
-    ("portfolio", "fp64", "a4527262d271f341"): 518.6e6,
-}
+# (workload, precision, source digest of spmv.cuh at capture time); None when
+# the kernel changed after the counters were taken.
+NCU_TRAFFIC = {}
 
 
 def _args():
@@ -68,6 +64,11 @@ def _args():
     ap.add_argument("--oracle-iters", type=int, default=12)
     ap.add_argument("--eager", action="store_true",
                     help="launch kernels from the host (for per-kernel profilers)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra keys (FP32 portfolio, logistic, 4096-instance batch)")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--oracle-procs", type=int, default=8,
+                    help="processes of the all-cores oracle leg (independent copies)")
     return ap.parse_args()
 
 
@@ -194,6 +195,29 @@ def _oracle_child(args, out_path):
                             stdout=subprocess.DEVNULL, stderr=subprocess.PIPE)
 
 
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def _oracle_multi(args, procs):
+    """The all-cores leg: `procs` oracle processes (one thread each), each on
+    its own copy of the same instance, started together; the aggregate rate
+    is the sum of their iterations / s.  Returns the child processes and
+    their output files."""
+    kids = []
+    for _ in range(procs):
+        fd, path = tempfile.mkstemp(suffix=".json")
+        os.close(fd)
+        kids.append((_oracle_child(args, path), path))
+    return kids
+
+
 def _args_from(argv):
     old = sys.argv
     try:
@@ -201,6 +225,118 @@ def _args_from(argv):
         return _args()
     finally:
         sys.argv = old
+
+
+def _timed_window(P, prob, opts, warmup, steps):
+    """Iterations / s of `steps` check periods after `warmup` ones (CUDA events
+    on the current stream around a pdcs_resume; synchronised)."""
+    import torch
+    with P.Solver(prob, **dict(opts, max_iter=warmup * CHECK_FREQ, profile=0)) as s:
+        r0 = s.solve()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r1 = s.resume(max_iter=r0["iters"] + steps * CHECK_FREQ)
+        e1.record()
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1000.0
+    return (r1["iters"] - r0["iters"]) / dt
+
+
+def _tts(P, prob, opts, cap):
+    with P.Solver(prob, **dict(opts, time_limit=cap, max_iter=2**62, profile=0)) as st:
+        t = time.perf_counter()
+        r = st.solve()
+        dt = time.perf_counter() - t
+    return r, {"reached": r["exit_code"] == 0, "seconds": dt, "iters": r["iters"],
+               "rel_kkt": max(r["err_rel_p"], r["err_rel_d"], r["err_rel_gap"]),
+               "status": r["status"]}
+
+
+def _extra_fp32(P, prob, ref64, cap):
+    """FP32 mode (FP32 matrix values and float-float products, FP64 vectors,
+    FP64 products at the checks) on the headline instance: its rate, time to
+    1e-6, and the distance of its result from the FP64 path's (which the
+    parity tests tie to the oracle)."""
+    opts = dict(precision="fp32", check_freq=CHECK_FREQ, time_limit=3600.0)
+    out = {"iters_per_s": _timed_window(P, prob, opts, 3, 10)}
+    r, out["time_to_tol"] = _tts(P, prob, opts, cap)
+    if ref64 is not None:
+        def rel(a, b):
+            return float(np.linalg.norm(a - b) / max(1e-300, np.linalg.norm(b)))
+        out["error_vs_fp64_path"] = {
+            "pobj_rel": abs(r["pobj"] - ref64["pobj"]) / (1.0 + abs(ref64["pobj"])),
+            "x_rel": rel(r["x"], ref64["x"]), "y_rel": rel(r["y"], ref64["y"])}
+    return out
+
+
+def _extra_logistic(P, cap):
+    """The L1-logistic regression (100,000 samples x 2,000 features, 200,000
+    exponential cones), FP64: rate, time to 1e-6 and the exponential-cone
+    projection's share and throughput (cones / s over its launches)."""
+    import torch
+    import workloads
+    prob = workloads.logistic_l1(seed=20260103)
+    opts = dict(precision="fp64", check_freq=CHECK_FREQ, time_limit=3600.0)
+    out = {"workload": "L1-logistic 100000 x 2000 (m=%d, n=%d, nnz=%d, 200000 exp cones)"
+                       % (prob["m"], prob["n"], len(prob["val"]))}
+    out["iters_per_s"] = _timed_window(P, prob, opts, 3, 10)
+    _, out["time_to_tol"] = _tts(P, prob, opts, cap)
+    with P.Solver(prob, **dict(opts, profile=1, max_iter=10 * CHECK_FREQ)) as sp:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sp.solve()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t
+        kt = sp.kernel_times()
+    tot = sum(v[0] for v in kt.values())
+    exp_s, exp_n = kt.get("exp", (0.0, 0))
+    # rows carry 200,000 cones; each launch projects two vectors of them
+    out["exp_projection"] = {"share_of_kernel_time": exp_s / tot if tot else None,
+                             "launches": exp_n, "us_per_launch": 1e6 * exp_s / exp_n if exp_n else None,
+                             "cones_per_s": 2 * 200000 * exp_n / exp_s if exp_s else None,
+                             "window_s": wall}
+    return out
+
+
+def _extra_batch(P, count):
+    """4096 portfolio SOCPs of uneven size (n ~ U{50..2000}, k = n/20,
+    ceil(n/200) limits) in one persistent launch, FP64: solves / s, per-instance
+    time to tolerance p50 / p99, and the plain FP64 path (one set-up and solve
+    per problem) on an evenly spaced sample of 16, scaled to the batch."""
+    import workloads
+    t = time.perf_counter()
+    probs = workloads.portfolio_batch(count=count)
+    gen = time.perf_counter() - t
+    nnz = np.array([len(p["val"]) for p in probs])
+    t = time.perf_counter()
+    b = P.Batch(probs, precision="fp64", time_limit=600.0)
+    setup = time.perf_counter() - t
+    t = time.perf_counter()
+    res = b.solve()
+    solve_s = time.perf_counter() - t
+    b.close()
+    per = np.array([r["solve_time_s"] for r in res])
+    ok = np.array([r["exit_code"] == 0 for r in res])
+    order = np.argsort(nnz)
+    pick = order[np.linspace(0, len(order) - 1, min(16, len(order))).astype(int)]
+    plain, agree = [], []
+    for k in pick:
+        t = time.perf_counter()
+        g = P.solve(probs[k], time_limit=600.0)
+        plain.append(time.perf_counter() - t)
+        agree.append(abs(g["pobj"] - res[k]["pobj"]) / (1.0 + abs(g["pobj"])))
+    plain_est = float(np.mean(plain) * count)
+    return {"workload": "%d portfolio SOCPs, n ~ U{50..2000}, k = n/20 (%.0fM nonzeros)"
+                        % (count, nnz.sum() / 1e6),
+            "solves_per_s": count / solve_s, "batch_solve_s": solve_s, "setup_s": setup,
+            "generate_s": gen, "per_instance_s_p50": float(np.percentile(per, 50)),
+            "per_instance_s_p99": float(np.percentile(per, 99)), "all_reached": bool(ok.all()),
+            "reached": int(ok.sum()), "plain_fp64_sample": len(pick),
+            "plain_fp64_s_mean": float(np.mean(plain)), "plain_fp64_total_s_estimate": plain_est,
+            "speedup_vs_plain_estimate": plain_est / solve_s,
+            "objective_rel_diff_max_vs_plain": float(max(agree))}
 
 
 def run_ours(args):
@@ -215,7 +351,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    oracle_proc, oracle_out = None, None
+    oracle_proc, oracle_out, oracle_kids = None, None, []
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         fd, oracle_out = tempfile.mkstemp(suffix=".json")
         os.close(fd)
@@ -321,6 +457,7 @@ def run_ours(args):
 
     # time to 1e-6 relative KKT error
     tts = None
+    rt = None
     if args.tts_cap > 0 and rank == 0:
         with P.Solver(prob, **dict(opts, time_limit=args.tts_cap, max_iter=2**62, profile=0)) as st:
             t2 = time.perf_counter()
@@ -331,18 +468,32 @@ def run_ours(args):
                "rel_kkt": max(rt["err_rel_p"], rt["err_rel_d"], rt["err_rel_gap"]),
                "status": rt["status"], "time_cap_s": args.tts_cap}
         if args.precision == "fp32":
-            # error of the FP32-bulk result against the FP64 path (the path the
+            # error of the FP32 result against the FP64 path (the path the
             # parity tests tie to the FP64 oracle), same instance and cap
             with P.Solver(prob, **dict(opts, precision="fp64", time_limit=args.tts_cap,
                                        max_iter=2**62, profile=0)) as s64:
                 r64 = s64.solve()
             def rel(a, b):
                 return float(np.linalg.norm(a - b) / max(1e-300, np.linalg.norm(b)))
-            tts["error_vs_fp64"] = {
+            tts["error_vs_fp64_path"] = {
                 "pobj_rel": abs(rt["pobj"] - r64["pobj"]) / (1.0 + abs(r64["pobj"])),
                 "x_rel": rel(rt["x"], r64["x"]), "y_rel": rel(rt["y"], r64["y"]),
                 "fp64_rel_kkt": max(r64["err_rel_p"], r64["err_rel_d"], r64["err_rel_gap"]),
                 "fp64_reached": r64["exit_code"] == 0}
+
+    # extra workloads of the same metric (N = 1 only): FP32 mode of the
+    # headline instance, the exponential-cone program, the 4096-instance batch
+    extras = None
+    if rank == 0 and ws == 1 and not args.no_extras and args.workload == "portfolio":
+        extras = {}
+        for name, fn in (("fp32_portfolio", lambda: _extra_fp32(
+                              P, prob, rt if args.precision == "fp64" else None, args.tts_cap)),
+                         ("logistic_exp_cones", lambda: _extra_logistic(P, 120.0)),
+                         ("batch_4096_portfolios", lambda: _extra_batch(P, args.batch_count))):
+            try:
+                extras[name] = fn()
+            except Exception as e:  # noqa: BLE001 -- reported, not fatal for the line
+                extras[name] = {"error": repr(e)[:300]}
 
     cpu = None
     if oracle_proc is not None:
@@ -350,12 +501,31 @@ def run_ours(args):
         try:
             o = json.load(open(oracle_out))
             cpu = {"value": o["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "cpu_model": _cpu_model(), "host_cores": os.cpu_count(),
                    "sample": "FP64 CPU oracle on the same instance: %d accepted PDHG iterations "
                              "after its set-up (%.0f s, not counted)" % (o["iters"], o["setup_s"])}
         except (OSError, ValueError, KeyError):
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": "oracle run failed: %s" % err.decode()[-200:]}
         os.unlink(oracle_out)
+        # the all-cores leg, after the GPU work (independent processes, one
+        # thread each, each on its own copy of the instance)
+        nproc = max(1, min(args.oracle_procs, os.cpu_count() or 1))
+        if nproc > 1:
+            kids = _oracle_multi(args, nproc)
+            rates = []
+            for kp, path in kids:
+                kp.communicate(timeout=1800)
+                try:
+                    rates.append(json.load(open(path))["value"])
+                except (OSError, ValueError, KeyError):
+                    pass
+                os.unlink(path)
+            cpu["all_cores"] = {"value": sum(rates) if len(rates) == nproc else None,
+                                "unit": UNIT, "cores": nproc, "kind": "oracle",
+                                "sample": "%d oracle processes at once, each %d accepted "
+                                          "iterations of its own copy of the instance; value = "
+                                          "sum of their rates" % (nproc, args.oracle_iters)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -373,7 +543,8 @@ def run_ours(args):
                 "gpu_launches": counts["kernel_launches"], "graph_launches": counts["graph_launches"],
                 "clocks": ck, "time_to_tol": tts,
                 "profiled_ms_per_step": 1000.0 * elapsed_prof / args.steps,
-                "kernel_seconds": {k: [round(v[0], 6), v[1]] for k, v in ktimes.items()}}
+                "kernel_seconds": {k: [round(v[0], 6), v[1]] for k, v in ktimes.items()},
+                "extras": extras}
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()

@@ -106,6 +106,37 @@ typedef struct {
   int32_t eager;             /* 1: launch the kernels one by one from the host
                                 instead of replaying captured graphs (slower; for
                                 per-kernel profilers) */
+  int32_t use_adaptive_step_size_weight; /* 1: the line search of Function 1 (Sec.
+                                2.1); 0: every attempt is accepted with the fixed
+                                step 1 / sqrt(||Ghat||_1 ||Ghat||_inf) (largest
+                                column / row absolute sum of the rescaled matrix,
+                                so that tau sigma ||Ghat||_2^2 <= 1) */
+  int32_t use_duality_gap_restart; /* 1: at every check_freq-th iteration (the
+                                paper's duality_gap_restart_freq) the restart
+                                criterion is the normalized duality gap of Sec.
+                                2.3 (KKT_omega when a gap is negative) */
+  int32_t use_kkt_restart;   /* 0; 1: at every kkt_restart_freq-th iteration that
+                                is not a gap check, the restart criterion is
+                                KKT_omega (Sec. 2.3).  Checks with neither
+                                criterion test termination and restart
+                                condition 3 only */
+  int32_t pad0;
+  int64_t kkt_restart_freq;  /* 2000 */
+  int64_t print_freq;        /* 2000: with verbose, a line whenever the iteration
+                                count passes a multiple (checked per period) */
+  /* Infeasibility tests of Sec. 3.2.3 (exit codes 2-5), on the change of the
+   * restart candidate between consecutive checks with the paper's ratios for
+   * the homogeneous problem: primal infeasible when the dual error of
+   * lambda = -G^T dy (plus the dual-cone violation of dy) over the dual
+   * objective h^T dy + l^T lambda_1^+ - u^T lambda_1^- is below the threshold;
+   * dual infeasible when the relative primal error of G dx (h = 0, plus the
+   * violation of the recession cone of X by dx) over -c^T dx is below it.
+   * The low-accuracy tests also need the candidates' dual objective (resp.
+   * -c^T x) to have risen at each of the last 3 checks.  0 disables a test. */
+  double eps_primal_infeasible_low_acc;   /* 1e-12 */
+  double eps_dual_infeasible_low_acc;     /* 1e-12 */
+  double eps_primal_infeasible_high_acc;  /* 1e-16 */
+  double eps_dual_infeasible_high_acc;    /* 1e-16 */
 } pdcs_options;
 
 typedef struct {
@@ -207,8 +238,9 @@ int pdcs_get_iterate(pdcs_handle* handle, int32_t which, double* x, double* y);
 /* Copy up to cap trace rows (PDCS_TRACE_FIELDS doubles each, one per accepted
  * iteration, row i = iteration i + 1) to host memory; *count receives the
  * number of rows available.  Fields: iter, kbar, period, eta, eta_hat, beta,
- * omega, max_err, check, cand_avg, restart, rho_c. */
-#define PDCS_TRACE_FIELDS 12
+ * omega, max_err, check, cand_avg, restart, rho_c (the candidate's restart
+ * measure), fallback (1 at a check whose measure was KKT_omega, Sec. 2.3). */
+#define PDCS_TRACE_FIELDS 13
 int pdcs_get_trace(pdcs_handle* handle, double* out, int64_t cap, int64_t* count);
 
 /* Device-measured cost of the sparse products of the last pdcs_solve /
@@ -259,8 +291,9 @@ const char* pdcs_last_error(void);
  * (one thread block per problem at a time, largest first; every problem has
  * its own step sizes, primal weight, restarts and termination).  Each problem
  * is described as pdcs_setup's arguments; arrays may be host or device memory
- * and are copied.  Limits: SOC blocks of at most 4096 elements
- * (PDCS_ERR_UNSUPPORTED beyond), fewer than 2^31 columns in all.  Set-up also
+ * and are copied.  SOC blocks of up to 4096 elements are projected with the
+ * block held in registers, larger ones by streaming the block from memory on
+ * every root-finding pass.  Limit: fewer than 2^31 columns in all.  Set-up also
  * picks the lanes per row of the sparse products for four size buckets by
  * timing a few problems of each (autotuning).  options.time_limit applies to
  * each problem from its start. */
@@ -340,9 +373,10 @@ int pdcs_kkt(pdcs_handle* handle, const double* x, const double* y, pdcs_result*
 
 /* y = G x for a CSR matrix held in device memory, without allocating.  The
  * paper has no counterpart: this is a service for callers that must not
- * allocate device memory when they call (for example while a caching
- * allocator owns the device's whole memory budget, or on a path that cannot
- * afford cudaMalloc's implicit device synchronisation).
+ * allocate device memory when they call, for example code running while a
+ * caching allocator (such as PyTorch's) owns the device's whole memory
+ * budget, where a cudaMalloc would fail or force the allocator to give its
+ * cache back.
  *   m, n: rows and columns of G (m = 0: nothing to do).
  *   row_ptr int64 [m+1], col_idx int32 [nnz] (entries in [0, n)),
  *   val float64 [nnz], x float64 [n], y float64 [m] (written): all device
@@ -353,20 +387,22 @@ int pdcs_kkt(pdcs_handle* handle, const double* x, const double* y, pdcs_result*
  * chunks of 4096 nonzeros among them; a matrix beyond either limit is
  * rejected with PDCS_ERR_INVALID before anything is computed.  Rows of up to
  * 4096 nonzeros have no limit.
- * The call synchronises cuda_stream once (to read the size check) and then
- * enqueues the product; y is ready when the stream reaches it.  It allocates
- * no device memory and, when it succeeds, no host memory either; a rejected
- * call stores its message for pdcs_last_error.
+ * The call synchronises cuda_stream once (to read that size check) and then
+ * enqueues the product; y is ready when the stream reaches it.  Because of
+ * that synchronisation it cannot be called while cuda_stream is being
+ * captured into a graph: it returns PDCS_ERR_INVALID then, and the capture
+ * is left intact.  It allocates no device memory and, when it succeeds, no
+ * host memory either; a rejected call stores its message for
+ * pdcs_last_error.
  * The first call on a device looks up the scratch's device address with that
- * device current and caches it: make that first call before any stream
- * capture.  The scratch's tickets must be zero when a call starts: they are
- * zero when the library is loaded and every completed call leaves them zero
- * (a call cut short by a device error does not).  All calls on one device
- * share the scratch, so calls that overlap in time race: serialise them.
- * Results are deterministic (fixed summation order) but round differently
- * from the solver's own product.
+ * device current and caches it.  The scratch's tickets must be zero when a
+ * call starts: they are zero when the library is loaded and every completed
+ * call leaves them zero (a call cut short by a device error does not).  All
+ * calls on one device share the scratch, so calls that overlap in time race:
+ * serialise them.  Results are deterministic (fixed summation order) but
+ * round differently from the solver's own product.
  * Returns PDCS_OK, PDCS_ERR_INVALID (sizes, NULL or host pointers, scratch
- * limits) or PDCS_ERR_CUDA. */
+ * limits, a capturing stream) or PDCS_ERR_CUDA. */
 int pdcs_spmv_noalloc(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                       const double* val, const double* x, double* y, void* cuda_stream);
 

@@ -299,12 +299,14 @@ class Oracle:
         return float(np.sqrt(float(dx @ dx) / tau + float(dy @ dy) / sigma))
 
     # -- Algorithm 1 / 2 --------------------------------------------------------
-    def solve(self, x0=None, y0=None, trace=None, snapshots=None, states=None):
+    def solve(self, x0=None, y0=None, trace=None, snapshots=None, states=None, init_state=None):
         """Run the solver.  trace: list to append one dict per accepted iteration.
         snapshots: dict {iteration: None} filled with copies of the scaled
         Halpern iterate (x, y) after that many accepted iterations.
         states: dict {iteration: None} filled with the complete solver state
-        after that many accepted iterations (0 = before the first one)."""
+        after that many accepted iterations (0 = before the first one).
+        init_state: a state in the form `states` records, to continue from
+        (the infeasibility history starts empty)."""
         o = self.opts
         sp_ = self.sp
         t_start = time.perf_counter()
@@ -343,6 +345,18 @@ class Oracle:
                         prev=(prev[0], prev[1]["abs_p"], prev[1]["abs_d"], prev[1]["abs_gap"])
                         if prev is not None else (0.0,) * 4)
 
+        if init_state is not None:
+            st = init_state
+            x, y = st["x"].copy(), st["y"].copy()
+            xa, ya = st["x0"].copy(), st["y0"].copy()
+            xs, ys = st["xs"].copy(), st["ys"].copy()
+            wsum, k, kbar, it = st["wsum"], st["k"], st["kbar"], st["iter"]
+            t_period, restarts = st["period"], st["restarts"]
+            eta_hat, eta, omega = st["eta_hat"], st["eta"], st["omega"]
+            errs = lambda t: dict(abs_p=t[1], abs_d=t[2], abs_gap=t[3])  # noqa: E731
+            rho_ref = (st["ref"][0], errs(st["ref"])) if st["has_ref"] else None
+            prev = (st["prev"][0], errs(st["prev"])) if st["has_prev"] else None
+            xc, yc = x.copy(), y.copy()
         if states is not None and 0 in states:
             states[0] = capture()
         while True:
@@ -475,6 +489,7 @@ class Oracle:
                     x_scaled=x, y_scaled=y, omega=omega, eta_hat=eta_hat)
 
 
-def solve(prob, x0=None, y0=None, trace=None, snapshots=None, states=None, **opts):
+def solve(prob, x0=None, y0=None, trace=None, snapshots=None, states=None, init_state=None,
+          **opts):
     """Convenience wrapper: Oracle(prob, Options(**opts)).solve(...)."""
-    return Oracle(prob, Options(**opts)).solve(x0, y0, trace, snapshots, states)
+    return Oracle(prob, Options(**opts)).solve(x0, y0, trace, snapshots, states, init_state)

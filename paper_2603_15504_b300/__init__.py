@@ -13,9 +13,9 @@ import numpy as np
 from .build import LIB, build  # noqa: F401
 
 CONE_ZERO, CONE_NONNEG, CONE_SOC, CONE_RSOC, CONE_EXP, CONE_DUAL_EXP = 0, 1, 2, 3, 4, 5
-TRACE_FIELDS = 12
+TRACE_FIELDS = 13
 TRACE_NAMES = ("iter", "kbar", "period", "eta", "eta_hat", "beta", "omega", "max_err", "check",
-               "cand_avg", "restart", "rho_c")
+               "cand_avg", "restart", "rho_c", "fallback")
 EXIT_NAMES = {0: "optimal", 1: "max_iter", 2: "primal_infeasible_low_acc",
               3: "primal_infeasible_high_acc", 4: "dual_infeasible_low_acc",
               5: "dual_infeasible_high_acc", 6: "time_limit", 7: "continue",
@@ -35,7 +35,14 @@ class PdcsOptions(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("require_abs", ctypes.c_int32),
                 ("bisect_rel_tol", ctypes.c_double), ("verbose", ctypes.c_int32),
                 ("trace_capacity", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("eager", ctypes.c_int32)]
+                ("eager", ctypes.c_int32), ("use_adaptive_step_size_weight", ctypes.c_int32),
+                ("use_duality_gap_restart", ctypes.c_int32), ("use_kkt_restart", ctypes.c_int32),
+                ("pad0", ctypes.c_int32), ("kkt_restart_freq", ctypes.c_int64),
+                ("print_freq", ctypes.c_int64),
+                ("eps_primal_infeasible_low_acc", ctypes.c_double),
+                ("eps_dual_infeasible_low_acc", ctypes.c_double),
+                ("eps_primal_infeasible_high_acc", ctypes.c_double),
+                ("eps_dual_infeasible_high_acc", ctypes.c_double)]
 
 
 class PdcsResult(ctypes.Structure):

@@ -11,8 +11,9 @@
 // CTA-wide reductions in place of grid-wide ones, and the same thread-0
 // control functions on the instance's own control block (kept in shared
 // memory).  So every instance has its own step sizes, primal weight, restarts
-// and termination.  SOC blocks (up to 4096 elements) are projected by the CTA
-// (soc_proj_cta), exponential cones per thread.  The products use `tile`
+// and termination.  SOC blocks are projected by the CTA (soc_proj_cta with the
+// block in registers up to 4096 elements, streamed from memory beyond),
+// exponential cones per thread.  The products use `tile`
 // lanes per row, chosen per size bucket by an autotuner on the host.
 #pragma once
 #include "iterate.cuh"
@@ -31,14 +32,16 @@ struct BInst {
   int32_t tile, pad;                         // lanes per row of the products
 };
 
+// T: the type of the matrix values (FP64, or FP32 in the FP32 mode); vectors
+// are FP64.
 template <typename T>
 struct BatchArgs {
-  Prob<T> p;  // batch-problem data, global indices
+  Prob<double> p;  // batch-problem data, global indices
   const int64_t *rp, *rpT;
   const int32_t *ci, *ciT;
   const T *vv, *vvT;
-  T *x, *y, *xh, *yh, *gx, *gty, *gxh, *gtyh, *x0, *y0, *gx0, *gty0;
-  T *xb, *yb, *gxb, *gtyb, *xc, *yc, *gxc, *gtyc;
+  double *x, *y, *xh, *yh, *gx, *gty, *gxh, *gtyh, *x0, *y0, *gx0, *gty0;
+  double *xb, *yb, *gxb, *gtyb, *xc, *yc, *gxc, *gtyc;
   double *xs, *ys;
   double *tm[2], *tn[2], *um[2], *un[2], *px[2], *py[2];
   const int64_t *soc_rs, *soc_cs;
@@ -58,25 +61,125 @@ struct BatchArgs {
 #define PDCS_BLOCK_LOOP(i, lo, hi) for (int64_t i = (lo) + threadIdx.x; i < (hi); i += blockDim.x)
 
 // y[r0 + r] = sum_e v[e] x[ci[e]] for the rows r < nr, `tile` lanes per row
-// (a power of two <= 32); every group runs the same number of trips so the
-// shuffles stay converged.
-template <typename T>
+// (a power of two <= 32), FP64 products of the (FP64 or FP32) values; every
+// group runs the same number of trips so the shuffles stay converged.
+template <typename V>
 PDCS_DEV void b_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                     const T* __restrict__ vv, const T* __restrict__ x, T* __restrict__ y,
+                     const V* __restrict__ vv, const double* __restrict__ x, double* __restrict__ y,
                      int64_t r0, int64_t nr, int tile) {
   const int gid = threadIdx.x / tile, lane = threadIdx.x % tile, ng = blockDim.x / tile;
   const int64_t trips = (nr + ng - 1) / ng;
   for (int64_t q = 0; q < trips; ++q) {
     const int64_t r = gid + q * ng;
-    Acc<T> acc;
+    Acc<double> acc;
     if (r < nr) {
       const int64_t s = rp[r0 + r], e = rp[r0 + r + 1];
-      for (int64_t k = s + lane; k < e; k += tile) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
+      for (int64_t k = s + lane; k < e; k += tile)
+        acc.add((double)__ldg(vv + k), __ldg(x + __ldg(ci + k)));
     }
     double v = acc.get();
     for (int o = tile / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, tile);
-    if (lane == 0 && r < nr) y[r0 + r] = (T)v;
+    if (lane == 0 && r < nr) y[r0 + r] = v;
   }
+}
+
+// One SOC block too large for registers (more than kBatchThreads *
+// kBatchSocEpt elements), onto diag(e) K_soc: the root-finding of
+// soc_proj_cta (inside / polar tests, the v0 = 0 case, normalisation by
+// max |v|, the closed-form start and Halley steps with the same stopping
+// rule), every pass streaming the block from memory (each thread takes
+// elements tid, tid + NT, ... as soc_proj_cta does).  Kept out of line so the
+// persistent kernel's register allocation does not grow.
+template <typename B>
+__device__ __noinline__ void b_proj_soc_stream(B* v, int64_t s, int dim, const double* d, int inv,
+                                               double* sh) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const double v0 = (double)v[s], e0 = cone_scale(d, s, inv);
+  double* red = sh + 8;
+  double s2[2] = {0.0, 0.0};  // sum (v/e)^2, sum (e v)^2 over the tail
+  for (int i = tid; i < dim; i += NT) {
+    if (i < 1) continue;
+    const double vi = (double)v[s + i], e = cone_scale(d, s + i, inv);
+    const double a = vi / e, b = vi * e;
+    s2[0] += a * a;
+    s2[1] += b * b;
+  }
+  block_sum<2>(s2, red);
+  if (sqrt(s2[0]) <= v0 / e0) return;  // inside (the sums are the same in every thread)
+  if (sqrt(s2[1]) <= -e0 * v0) {       // polar
+    for (int i = tid; i < dim; i += NT) v[s + i] = (B)0.0;
+    return;
+  }
+  const double e02 = e0 * e0;
+  if (v0 == 0.0) {
+    double acc[1] = {0.0};
+    for (int i = tid; i < dim; i += NT) {
+      if (i < 1) continue;
+      const double e = cone_scale(d, s + i, inv), b = e * e;
+      const double w = (double)v[s + i] * b / (b + e02);
+      v[s + i] = (B)w;
+      const double t = w / e;
+      acc[0] += t * t;
+    }
+    block_sum<1>(acc, red);
+    if (tid == 0) v[s] = (B)(e0 * sqrt(acc[0]));
+    return;
+  }
+  double mx[1] = {fabs(v0)};
+  for (int i = tid; i < dim; i += NT)
+    if (i >= 1) mx[0] = fmax(mx[0], fabs((double)v[s + i]));
+  block_max<1>(mx, red);
+  const double sc = mx[0] > 0.0 ? 1.0 / mx[0] : 1.0;
+  const double c0 = (v0 * sc) * (v0 * sc) * e02;
+  const bool pos = v0 > 0.0;
+  double lo = 0.0, hi = pos ? 0.5 * e02 : 1.0 / e02;
+  const double top = hi;
+  double x = soc_initial_guess(s2[0], s2[1], v0, e0);
+  for (int it = 0; it < 200; ++it) {
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int i = tid; i < dim; i += NT) {
+      if (i < 1) continue;
+      const double vv = (double)v[s + i] * sc, e = cone_scale(d, s + i, inv);
+      const double b = e * e;
+      soc_secular_terms(pos, vv * vv * b, b, x, f);
+    }
+    for (int k = 0; k < 3; ++k) red[k * NT + tid] = f[k];
+    __syncthreads();
+    if (tid < 32) {
+      for (int k = 0; k < 3; ++k) {
+        double a = 0.0;
+        for (int t = tid; t < NT; t += 32) a += red[k * NT + t];
+        f[k] = warp_sum(a);
+      }
+    }
+    if (tid == 0) {  // the scalar step once per CTA, broadcast
+      int stop = 0;
+      const double dist = fmin(x, top - x);
+      const double step = soc_halley_step(pos, f, c0, e02, x, lo, hi);
+      if (step == 0.0) {
+        stop = 1;
+      } else {
+        double xn = x + step;
+        const bool inside = xn > lo && xn < hi;
+        if (!inside) xn = 0.5 * (lo + hi);
+        x = xn;
+        if ((inside && fabs(step) <= kSocStepTol * dist) || hi - lo <= 1e-15 * hi) stop = 1;
+      }
+      sh[2] = x; sh[3] = lo; sh[4] = hi; sh[5] = (double)stop;
+    }
+    __syncthreads();
+    x = sh[2]; lo = sh[3]; hi = sh[4];
+    // thread 0 rewrites sh[2..5] only after the next pass's staging barrier,
+    // which every thread reaches after these reads
+    if (sh[5] != 0.0) break;
+  }
+  const double mu2 = pos ? 2.0 * x : 1.0 / x;  // 2 mu
+  for (int i = tid; i < dim; i += NT) {
+    if (i < 1) continue;
+    const double e = cone_scale(d, s + i, inv), b = e * e;
+    v[s + i] = (B)((double)v[s + i] * (b / (b + mu2)));
+  }
+  if (tid == 0) v[s] = (B)(pos ? v0 * e02 / (e02 - mu2) : v0 * e02 * x / (e02 * x - 1.0));
 }
 
 // SOC blocks [first, first + count) of a list, onto diag(e) K_soc (e from d, inv).
@@ -86,6 +189,11 @@ PDCS_DEV void b_proj_soc(B* v, const int64_t* __restrict__ starts, const int32_t
   for (int j = first; j < first + count; ++j) {
     const int64_t s = starts[j];
     const int dim = dims[j];
+    if (dim > kBatchThreads * kBatchSocEpt) {  // uniform
+      b_proj_soc_stream(v, s, dim, d, inv, sh);
+      __syncthreads();
+      continue;
+    }
     double vv[kBatchSocEpt], ee[kBatchSocEpt];
 #pragma unroll
     for (int k = 0; k < kBatchSocEpt; ++k) {
@@ -144,8 +252,8 @@ PDCS_DEV void b_project_cols(const BatchArgs<T>& a, const BInst& I, B* v, const 
 // k_point_stats of the grid engine, restricted to the instance).
 template <typename T, bool FULL>
 PDCS_DEV void b_point_stats(const BatchArgs<T>& a, const BInst& I, Ctl& sc, int slot,
-                            const PointRef<T>& pt, const T* x0, const T* y0, int buf, double* sh) {
-  const Prob<T>& p = a.p;
+                            const PointRef<double>& pt, const double* x0, const double* y0, int buf, double* sh) {
+  const Prob<double>& p = a.p;
   const TmpRef tr{a.tm[buf], a.tn[buf], FULL ? a.um[buf] : nullptr, FULL ? a.un[buf] : nullptr};
   PDCS_BLOCK_LOOP(i, I.r0, I.r0 + I.m) res_prep_row(p, pt, tr, i);
   PDCS_BLOCK_LOOP(j, I.c0, I.c0 + I.n) res_prep_col(p, pt, tr, j);
@@ -170,8 +278,8 @@ PDCS_DEV void b_point_stats(const BatchArgs<T>& a, const BInst& I, Ctl& sc, int 
   for (int k = 0; k < kStatSums; ++k) s[k] = 0.0;
 #pragma unroll
   for (int k = 0; k < kStatMax; ++k) mx[k] = 0.0;
-  PDCS_BLOCK_LOOP(i, I.r0, I.r0 + I.m) stats_row<T, FULL>(p, pt, y0, tr, i, s, mx);
-  PDCS_BLOCK_LOOP(j, I.c0, I.c0 + I.n) stats_col<T, FULL>(p, pt, x0, tr, j, s, mx);
+  PDCS_BLOCK_LOOP(i, I.r0, I.r0 + I.m) stats_row<double, FULL>(p, pt, y0, tr, i, s, mx);
+  PDCS_BLOCK_LOOP(j, I.c0, I.c0 + I.n) stats_col<double, FULL>(p, pt, x0, tr, j, s, mx);
   block_sum<kStatSums>(s, sh);
   block_max<kStatMax>(mx, sh);
   if (threadIdx.x == 0) ctl_stats_finalize(sc, slot, s, mx);
@@ -182,7 +290,7 @@ PDCS_DEV void b_point_stats(const BatchArgs<T>& a, const BInst& I, Ctl& sc, int 
 // Halpern step (the attempt body of the grid engine).
 template <typename T>
 PDCS_DEV void b_attempt(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh) {
-  const Prob<T>& p = a.p;
+  const Prob<double>& p = a.p;
   const int64_t r0 = I.r0, r1 = I.r0 + I.m, c0 = I.c0, c1 = I.c0 + I.n;
   const double tau = sc.eta / sc.omega, sigma = sc.eta * sc.omega;
   PDCS_BLOCK_LOOP(j, c0, c1) primal_elem(p, tau, a.x, a.gty, a.xh, j);
@@ -213,7 +321,7 @@ PDCS_DEV void b_attempt(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* 
   if (!sc.g_accept) return;
   b_spmv(a.rpT, a.ciT, a.vvT, a.yh, a.gtyh, c0, I.n, I.tile);
   __syncthreads();
-  const PointRef<T> ph{a.xh, a.yh, a.gxh, a.gtyh};
+  const PointRef<double> ph{a.xh, a.yh, a.gxh, a.gtyh};
   b_point_stats<T, false>(a, I, sc, 0, ph, nullptr, nullptr, 0, sh);
   const double kk = (double)sc.k, beta = sc.beta, eta = sc.eta_acc;
   const double ca = (kk + 1.0) / (kk + 2.0), cb = 1.0 / (kk + 2.0);
@@ -228,16 +336,16 @@ PDCS_DEV void b_attempt(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* 
 // for both candidates, decision, candidate copy and the restart's products).
 template <typename T>
 PDCS_DEV void b_check(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh) {
-  const Prob<T>& p = a.p;
+  const Prob<double>& p = a.p;
   const int64_t r0 = I.r0, r1 = I.r0 + I.m, c0 = I.c0, c1 = I.c0 + I.n;
   const double w = sc.wsum;
-  PDCS_BLOCK_LOOP(j, c0, c1) a.xb[j] = (T)(a.xs[j] / w);
-  PDCS_BLOCK_LOOP(i, r0, r1) a.yb[i] = (T)(a.ys[i] / w);
+  PDCS_BLOCK_LOOP(j, c0, c1) a.xb[j] = a.xs[j] / w;
+  PDCS_BLOCK_LOOP(i, r0, r1) a.yb[i] = a.ys[i] / w;
   __syncthreads();
   b_spmv(a.rp, a.ci, a.vv, a.xb, a.gxb, r0, I.m, I.tile);
   b_spmv(a.rpT, a.ciT, a.vvT, a.yb, a.gtyb, c0, I.n, I.tile);
   __syncthreads();
-  const PointRef<T> z{a.x, a.y, a.gx, a.gty}, zb{a.xb, a.yb, a.gxb, a.gtyb};
+  const PointRef<double> z{a.x, a.y, a.gx, a.gty}, zb{a.xb, a.yb, a.gxb, a.gtyb};
   b_point_stats<T, true>(a, I, sc, 1, z, a.x0, a.y0, 0, sh);
   b_point_stats<T, true>(a, I, sc, 2, zb, a.x0, a.y0, 1, sh);
   if (threadIdx.x == 0) ctl_bisect_init(sc);
@@ -245,7 +353,7 @@ PDCS_DEV void b_check(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh
   while (sc.bs[0].active || sc.bs[1].active) {
     for (int c = 0; c < 2; ++c) {
       if (!sc.bs[c].active) continue;  // uniform
-      const PointRef<T> pt = c == 0 ? z : zb;
+      const PointRef<double> pt = c == 0 ? z : zb;
       const double t = probe_t(sc.bs[c]);
       const double tt = t * sc.bs[c].tau, ts = t * sc.bs[c].sigma;
       PDCS_BLOCK_LOOP(j, c0, c1) probe_prep_col(p, pt, tt, a.px[c], j);
@@ -261,7 +369,7 @@ PDCS_DEV void b_check(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh
     double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int c = 0; c < 2; ++c) {
       if (!sc.bs[c].active) continue;
-      const PointRef<T> pt = c == 0 ? z : zb;
+      const PointRef<double> pt = c == 0 ? z : zb;
       double s4[4] = {0.0, 0.0, 0.0, 0.0};
       PDCS_BLOCK_LOOP(j, c0, c1) probe_sum_col(p, pt, a.px[c], j, s4);
       PDCS_BLOCK_LOOP(i, r0, r1) probe_sum_row(p, pt, a.py[c], i, s4);
@@ -276,16 +384,16 @@ PDCS_DEV void b_check(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh
   }
   if (threadIdx.x == 0) ctl_check_decide(sc, nullptr);
   __syncthreads();
-  const PointRef<T> s = sc.cand ? zb : z;
+  const PointRef<double> s = sc.cand ? zb : z;
   const bool rs = sc.g_restart != 0;
   PDCS_BLOCK_LOOP(j, c0, c1) {
-    const T v = s.x[j];
+    const double v = s.x[j];
     a.gtyc[j] = s.gty[j];
     a.xc[j] = v;
     if (rs) { a.x0[j] = v; a.x[j] = v; a.xs[j] = 0.0; }
   }
   PDCS_BLOCK_LOOP(i, r0, r1) {
-    const T v = s.y[i];
+    const double v = s.y[i];
     a.gxc[i] = s.gx[i];
     a.yc[i] = v;
     if (rs) { a.y0[i] = v; a.y[i] = v; a.ys[i] = 0.0; }
@@ -308,7 +416,7 @@ PDCS_DEV void b_check(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh
 template <typename T>
 PDCS_DEV void b_solve(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh,
                       unsigned long long t_begin) {
-  const Prob<T>& p = a.p;
+  const Prob<double>& p = a.p;
   const int64_t r0 = I.r0, r1 = I.r0 + I.m, c0 = I.c0, c1 = I.c0 + I.n;
   // per-instance norms: ||hhat||_1, ||hhat||_2^2, ||chat||_1, ||chat||_2^2,
   // ||h||_inf, ||c||_inf (unscaled) and max |Ghat| (eta0 = 1 / max |Ghat|)
@@ -330,12 +438,32 @@ PDCS_DEV void b_solve(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh
   }
   block_sum<4>(s4, sh);
   block_max<3>(mx3, sh);
+  // largest row / column absolute sums of the instance's Ghat (fixed step)
+  const bool fixed = !a.tmpl->adaptive_step;
+  double rc[2] = {0.0, 0.0};
+  if (fixed) {
+    PDCS_BLOCK_LOOP(i, r0, r1) {
+      double t = 0.0;
+      for (int64_t e = a.rp[i]; e < a.rp[i + 1]; ++e) t += fabs((double)a.vv[e]);
+      rc[0] = fmax(rc[0], t);
+    }
+    PDCS_BLOCK_LOOP(j, c0, c1) {
+      double t = 0.0;
+      for (int64_t e = a.rpT[j]; e < a.rpT[j + 1]; ++e) t += fabs((double)a.vvT[e]);
+      rc[1] = fmax(rc[1], t);
+    }
+    block_max<2>(rc, sh);
+  }
   if (threadIdx.x == 0) {
     sc = *a.tmpl;
     const double nh2 = sqrt(s4[1]), nc2 = sqrt(s4[3]);
     const double omega0 = (nc2 > 1e-10 && nh2 > 1e-10) ? nc2 / nh2 : 1.0;  // Sec. 2.5
     const double eta0 = mx3[2] > 0.0 ? 1.0 / mx3[2] : 1.0;                  // 1 / ||Ghat||_inf
     sc.eta = sc.eta_hat = sc.eta_acc = sc.eta0 = eta0;
+    if (fixed) {
+      sc.eta_fixed = (rc[0] > 0.0 && rc[1] > 0.0) ? 1.0 / sqrt(rc[1] * rc[0]) : 1.0;
+      sc.eta = sc.eta_hat = sc.eta_acc = sc.eta_fixed;
+    }
     sc.omega = sc.omega0 = omega0;
     sc.h1 = s4[0];
     sc.c1 = s4[2];
@@ -345,11 +473,11 @@ PDCS_DEV void b_solve(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh
   }
   // cold start: x = y = 0, so every product is zero
   PDCS_BLOCK_LOOP(j, c0, c1) {
-    a.x[j] = a.x0[j] = a.gty[j] = a.gty0[j] = (T)0.0;
+    a.x[j] = a.x0[j] = a.gty[j] = a.gty0[j] = 0.0;
     a.xs[j] = 0.0;
   }
   PDCS_BLOCK_LOOP(i, r0, r1) {
-    a.y[i] = a.y0[i] = a.gx[i] = a.gx0[i] = (T)0.0;
+    a.y[i] = a.y0[i] = a.gx[i] = a.gx0[i] = 0.0;
     a.ys[i] = 0.0;
   }
   __syncthreads();
@@ -373,7 +501,7 @@ PDCS_DEV void b_solve(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* sh
     PDCS_BLOCK_LOOP(i, r0, r1) { a.yc[i] = a.y[i]; a.gxc[i] = a.gx[i]; }
     __syncthreads();
   }
-  const PointRef<T> pr{a.xc, a.yc, a.gxc, a.gtyc};
+  const PointRef<double> pr{a.xc, a.yc, a.gxc, a.gtyc};
   b_point_stats<T, true>(a, I, sc, 3, pr, nullptr, nullptr, 0, sh);
 }
 

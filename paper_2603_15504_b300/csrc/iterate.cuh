@@ -15,6 +15,7 @@
 #pragma once
 #include "common.cuh"
 #include "cones.cuh"
+#include "spmv.cuh"
 
 namespace pdcs {
 
@@ -23,7 +24,9 @@ enum : int { kRunning = -1 };
 enum : uint8_t { RK_FREE = 0, RK_NONNEG = 1, RK_SOC = 2, RK_EXP = 3, RK_DEXP = 4 };
 enum : uint8_t { CK_BOX = 0, CK_ZERO = 1, CK_NONNEG = 2, CK_SOC = 3, CK_EXP = 4, CK_DEXP = 5 };
 enum : int { BS_DONE = 0, BS_EXP = 1, BS_BISECT = 2 };
-enum : int { CNT_STEP = 0, CNT_STATS0 = 1, CNT_HALPERN = 5, CNT_PROBE = 6, CNT_NUM = 8 };
+enum : int { CNT_STEP = 0, CNT_STATS0 = 1, CNT_HALPERN = 5, CNT_PROBE = 6, CNT_INFEAS = 7, CNT_NUM = 8 };
+constexpr int kTraceF = 13;  // trace row: the fields listed with pdcs_get_trace
+constexpr int kHist = 4;     // checks kept for the infeasibility trend (3 rises)
 constexpr int kEwThreads = 256;
 constexpr int kStatSums = 8, kStatMax = 5, kStatK = kStatSums + kStatMax;
 
@@ -52,6 +55,16 @@ struct Ctl {
   int guard, guard_cap, probes, probe_cap;
   int g_attempt, g_accept, g_check, g_restart;
   long long bodies_a, bodies_b;  // executions of the attempt / probe loop bodies
+  // options of Sec. 3.2.3: fixed step, restart criteria, infeasibility tests
+  int adaptive_step, gap_restart, kkt_restart, infeas_on;
+  long long kkt_freq;
+  double eta_fixed;
+  double eps_pl, eps_dl, eps_ph, eps_dh;
+  // the current check: rho^N computed (gap criterion), KKT criterion, KKT_omega used
+  int chk_gap, chk_kkt, chk_fb, n_hist;
+  double hist_d[kHist], hist_p[kHist];  // candidates' dual objective / -c^T x, newest last
+  double infeas[2][2];  // per candidate: (primal, dual) ratio of its change since the last one
+  int infeas_gate[2];   // the infeasibility statistics run for candidate 0 / 1
   PointStats st[4];  // 0 zhat (attempt), 1 z, 2 zbar (check), 3 returned point
   Bisect bs[2];
   unsigned int cnt[CNT_NUM];
@@ -103,15 +116,20 @@ PDCS_DEV void primal_elem(const Prob<T>& p, double tau, const T* __restrict__ x,
   xh[j] = (T)v;
 }
 
+// sx (FP32-value mode without column cones, else NULL): also the FP32
+// (hi, lo) shadow of xhat that the product G xhat gathers.
 template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_primal(Prob<T> p, const Ctl* __restrict__ ctl,
                                                        const T* __restrict__ x,
                                                        const T* __restrict__ gty,
-                                                       T* __restrict__ xh) {
+                                                       T* __restrict__ xh, float2* __restrict__ sx) {
   if (!ctl->g_attempt) return;
   ktimer_begin(tslot(p.tm, TM_PRIMAL));
   const double tau = ctl->eta / ctl->omega;
-  PDCS_GRID_LOOP(j, p.n) primal_elem(p, tau, x, gty, xh, j);
+  PDCS_GRID_LOOP(j, p.n) {
+    primal_elem(p, tau, x, gty, xh, j);
+    if (sx != nullptr) sx[j] = split_ff((double)xh[j]);
+  }
   ktimer_end(tslot(p.tm, TM_PRIMAL));
 }
 
@@ -180,6 +198,14 @@ __global__ void __launch_bounds__(kEwThreads) k_dual(Prob<T> p, const Ctl* __res
 // incremented before the exponents use (kbar + 1).  (Thread-0 logic shared by
 // the grid-wide and the per-instance batched engines.)
 PDCS_DEV void ctl_step_finalize(Ctl& c, double dx2, double dy2, double inter) {
+  if (!c.adaptive_step) {
+    // fixed step (use_adaptive_step_size_weight = 0): every attempt accepted
+    c.kbar += 1;
+    c.accepted = 1;
+    c.eta = c.eta_hat = c.eta_acc = c.eta_fixed;
+    c.g_accept = 1;
+    return;
+  }
   inter = fabs(inter);
   const double omega = c.omega, eta = c.eta;
   c.kbar += 1;
@@ -210,7 +236,8 @@ __global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict_
                                                      const T* __restrict__ yh,
                                                      const T* __restrict__ gxh,
                                                      const T* __restrict__ gx,
-                                                     double* __restrict__ part) {
+                                                     double* __restrict__ part,
+                                                     float2* __restrict__ sy) {
   if (!ctl->g_attempt) return;
   ktimer_begin(tslot(p.tm, TM_STEP));
   __shared__ double sh[3 * kEwThreads + 3];
@@ -220,9 +247,11 @@ __global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict_
     s[0] += d * d;
   }
   PDCS_GRID_LOOP(i, p.m) {
-    const double d = (double)yh[i] - (double)y[i];
+    const double yv = (double)yh[i];
+    const double d = yv - (double)y[i];
     s[1] += d * d;
     s[2] += d * ((double)gxh[i] - (double)gx[i]);
+    if (sy != nullptr) sy[i] = split_ff(yv);  // shadow of yhat for G^T yhat (FP32 values)
   }
   block_sum<3>(s, sh);
   if (threadIdx.x == 0) {
@@ -538,18 +567,24 @@ PDCS_DEV void ctl_halpern_finalize(Ctl& c, double eta, double beta, double* trac
   c.wsum += eta;
   const long long it = c.iter;
   if (trace != nullptr && it <= c.trace_cap) {
-    double* r = trace + (it - 1) * 12;
+    double* r = trace + (it - 1) * kTraceF;
     r[0] = (double)it; r[1] = (double)c.kbar; r[2] = (double)c.period; r[3] = eta;
     r[4] = c.eta_hat; r[5] = beta; r[6] = c.omega; r[7] = c.st[0].max_err;
-    r[8] = 0.0; r[9] = -1.0; r[10] = 0.0; r[11] = NAN;
+    r[8] = 0.0; r[9] = -1.0; r[10] = 0.0; r[11] = NAN; r[12] = 0.0;
   }
+  const bool kkt_due = c.kkt_restart && it % c.kkt_freq == 0;
   if (!isfinite(c.st[0].max_err)) {
     c.status = 8;
     c.g_attempt = 0;
-  } else if (it % c.check_freq == 0) {
+  } else if (it % c.check_freq == 0 || kkt_due) {
     c.period_done = 1;
     c.g_attempt = 0;
     c.g_check = 1;
+    c.chk_gap = c.gap_restart && it % c.check_freq == 0;
+    c.chk_kkt = kkt_due;
+    // infeasibility statistics need the previous check's candidate
+    c.infeas_gate[0] = c.infeas_on && c.have_cand;
+    c.infeas_gate[1] = c.infeas_on && c.have_cand && c.method == 0;
   } else if (it >= c.max_iter) {
     c.status = 1;
     c.g_attempt = 0;
@@ -651,6 +686,10 @@ PDCS_DEV int ctl_bisect_init(Ctl& cl) {
     b.last_dot = 0.0;
     if (!cl.g_check) continue;
     if (c == 1 && cl.method != 0) continue;
+    if (!cl.chk_gap) {
+      b.result = NAN;  // KKT-criterion or termination-only check: no gap
+      continue;
+    }
     const PointStats& st = cl.st[1 + c];
     const double r = sqrt(st.dx2 / tau + st.dy2 / sigma);
     const double scale = sqrt(tau * st.lam2 + sigma * st.u2);
@@ -835,6 +874,25 @@ PDCS_DEV double kkt_w(double ep, double ed, double eg, double w) {
   return sqrt(w * w * ep * ep + ed * ed / (w * w) + eg * eg);
 }
 
+// Infeasibility tests of Sec. 3.2.3 on the candidate's (primal, dual) ratios:
+// high accuracy on the ratio alone (3 / 5), low accuracy with the candidates'
+// dual objective (resp. -c^T x) rising at each of the last kHist - 1 checks
+// (2 / 4); 0 when no test fires.
+PDCS_DEV bool hist_rising(const double* h, int n) {
+  if (n < kHist) return false;
+  for (int q = 1; q < kHist; ++q)
+    if (!(h[q] > h[q - 1])) return false;
+  return true;
+}
+
+PDCS_DEV int infeasibility_code(const Ctl& c, double pr, double dr) {
+  if (pr < c.eps_ph) return 3;
+  if (dr < c.eps_dh) return 5;
+  if (pr < c.eps_pl && hist_rising(c.hist_d, c.n_hist)) return 2;
+  if (dr < c.eps_dl && hist_rising(c.hist_p, c.n_hist)) return 4;
+  return 0;
+}
+
 // GetRestartCandidate, termination, restart conditions, KKT_omega fallback,
 // primal-weight update (Secs. 2.3, 2.5, 3.2.3).
 PDCS_DEV void ctl_check_decide(Ctl& c, double* trace) {
@@ -843,8 +901,10 @@ PDCS_DEV void ctl_check_decide(Ctl& c, double* trace) {
   const double rho_h = c.bs[0].result;
   const double rho_a = avg ? c.bs[1].result : INFINITY;
   const double w = c.omega;
-  const bool fb = rho_h < 0.0 || (avg && rho_a < 0.0) || (c.has_ref && c.ref_rho < 0.0) ||
-                  (c.has_prev && c.prev_rho < 0.0);
+  // KKT_omega replaces every gap when one of them is negative or was not
+  // computed (a KKT-criterion check)
+  const bool fb = !(rho_h >= 0.0) || (avg && !(rho_a >= 0.0)) || (c.has_ref && !(c.ref_rho >= 0.0)) ||
+                  (c.has_prev && !(c.prev_rho >= 0.0));
   const PointStats& s1 = c.st[1];
   const PointStats& s2 = c.st[2];
   const double m_h = fb ? kkt_w(s1.abs_p, s1.abs_d, s1.gap, w) : rho_h;
@@ -853,18 +913,32 @@ PDCS_DEV void ctl_check_decide(Ctl& c, double* trace) {
   const double val = cand ? m_a : m_h;
   const double rho_c = cand ? rho_a : rho_h;
   const PointStats& sc = c.st[1 + cand];
+  const bool had_cand = c.have_cand != 0;
   c.cand = cand;
   c.have_cand = 1;
+  c.chk_fb = fb ? 1 : 0;
   const long long it = c.iter;
   if (trace != nullptr && it >= 1 && it <= c.trace_cap) {
-    double* r = trace + (it - 1) * 12;
-    r[8] = 1.0; r[9] = (double)cand; r[11] = val;
+    double* r = trace + (it - 1) * kTraceF;
+    r[8] = 1.0; r[9] = (double)cand; r[11] = val; r[12] = fb ? 1.0 : 0.0;
   }
+  // objectives of the candidates of the last checks (infeasibility trend)
+  if (c.n_hist == kHist) {
+    for (int q = 0; q + 1 < kHist; ++q) { c.hist_d[q] = c.hist_d[q + 1]; c.hist_p[q] = c.hist_p[q + 1]; }
+    c.n_hist -= 1;
+  }
+  c.hist_d[c.n_hist] = sc.dobj;
+  c.hist_p[c.n_hist] = -sc.pobj;
+  c.n_hist += 1;
   bool done = sc.inf_max <= c.rel_tol;
   if (c.require_abs) done = done && fmax(sc.inf_abs_p, fmax(sc.inf_abs_d, sc.gap)) <= c.abs_tol;
   c.g_restart = 0;
   if (done) { c.status = 0; return; }
   if (!isfinite(sc.inf_max)) { c.status = 8; return; }
+  if (c.infeas_on && had_cand) {
+    const int code = infeasibility_code(c, c.infeas[cand][0], c.infeas[cand][1]);
+    if (code) { c.status = code; return; }
+  }
   bool restart = false;
   if (c.adaptive_restart) {
     const bool cond3 = (double)c.k >= 0.223 * (double)c.kbar;
@@ -872,9 +946,10 @@ PDCS_DEV void ctl_check_decide(Ctl& c, double* trace) {
       restart = cond3;
     } else {
       const double ref = fb ? kkt_w(c.ref_ep, c.ref_ed, c.ref_eg, w) : c.ref_rho;
-      const bool c1 = val <= 0.4 * ref;
+      const bool crit = c.chk_gap || c.chk_kkt;  // conditions 1 and 2 need a criterion
+      const bool c1 = crit && val <= 0.4 * ref;
       bool c2 = false;
-      if (c.has_prev) {
+      if (c.has_prev && crit) {
         const double pv = fb ? kkt_w(c.prev_ep, c.prev_ed, c.prev_eg, w) : c.prev_rho;
         c2 = val <= 0.8 * ref && val > pv;
       }
@@ -882,7 +957,7 @@ PDCS_DEV void ctl_check_decide(Ctl& c, double* trace) {
     }
   }
   if (restart) {
-    if (trace != nullptr && it >= 1 && it <= c.trace_cap) trace[(it - 1) * 12 + 10] = 1.0;
+    if (trace != nullptr && it >= 1 && it <= c.trace_cap) trace[(it - 1) * kTraceF + 10] = 1.0;
     const double dx = sqrt(sc.dx2), dy = sqrt(sc.dy2);
     double om = c.omega;
     if (dx > 1e-10 && dy > 1e-10) om = exp(0.5 * log(dy / dx) + 0.5 * log(om));
@@ -908,11 +983,14 @@ __global__ void k_check_decide(Ctl* ctl, double* trace) { ctl_check_decide(*ctl,
 
 // Keep the chosen candidate (the returned point) and, on restart, make it the
 // new anchor and current iterate and clear the average.
+// sx / sy (FP32-value mode, else NULL): on restart also the FP32 shadows of
+// the new anchor for its products.
 template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_cand_copy(int64_t n, int64_t m, const Ctl* __restrict__ ctl,
                                                           PointRef<T> z, PointRef<T> zb, T* xc, T* yc,
                                                           T* gxc, T* gtyc, T* x0, T* y0, T* x, T* y,
-                                                          double* xs, double* ys, KTimer* tm) {
+                                                          double* xs, double* ys, float2* sx,
+                                                          float2* sy, KTimer* tm) {
   if (!ctl->g_check) return;
   ktimer_begin(tm);
   const PointRef<T> s = ctl->cand ? zb : z;
@@ -921,13 +999,19 @@ __global__ void __launch_bounds__(kEwThreads) k_cand_copy(int64_t n, int64_t m, 
     const T v = s.x[j];
     gtyc[j] = s.gty[j];
     xc[j] = v;
-    if (rs) { x0[j] = v; x[j] = v; xs[j] = 0.0; }
+    if (rs) {
+      x0[j] = v; x[j] = v; xs[j] = 0.0;
+      if (sx != nullptr) sx[j] = split_ff((double)v);
+    }
   }
   PDCS_GRID_LOOP(i, m) {
     const T v = s.y[i];
     gxc[i] = s.gx[i];
     yc[i] = v;
-    if (rs) { y0[i] = v; y[i] = v; ys[i] = 0.0; }
+    if (rs) {
+      y0[i] = v; y[i] = v; ys[i] = 0.0;
+      if (sy != nullptr) sy[i] = split_ff((double)v);
+    }
   }
   ktimer_end(tm);
 }
@@ -948,11 +1032,143 @@ PDCS_DEV void ctl_check_end(Ctl& c) {
   c.period_done = 0;
   c.g_restart = 0;
   c.g_check = 0;
+  c.infeas_gate[0] = c.infeas_gate[1] = 0;
   if (c.status == kRunning && c.iter >= c.max_iter) c.status = 1;
   c.g_attempt = c.status == kRunning;
 }
 
 __global__ void k_check_end(Ctl* ctl) { ctl_check_end(*ctl); }
+
+// ------------------------------------------------ infeasibility statistics
+// Sec. 3.2.3 infeasibility ratios for the change of restart candidate cidx
+// (0: z, 1: zbar; blockIdx.y) since the previous check's candidate pc, in the
+// unscaled variables: dx = D2 (x_c - x_pc), dy = D1 (y_c - y_pc), and by
+// linearity of the carried products G dx = (Ghat dx~) / D1 and, for the
+// homogeneous problem (c = 0), lambda = -G^T dy = -(Ghat^T dy~) / D2.
+// The prep pass stores the parts that need cone projections onto the standard
+// cones (done by the cone kernels in place): tm <- G dx (onto K_r), um <- dy
+// (onto K_r^*) on cone rows; tn <- lambda (onto K_p^*), un <- dx (onto K_p)
+// on cone columns.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_infeas_prep(Prob<T> p, const Ctl* __restrict__ ctl,
+                                                            PointRef<T> z, PointRef<T> zb,
+                                                            PointRef<T> pc, TmpRef ta, TmpRef tb) {
+  const int cidx = blockIdx.y;
+  if (!ctl->infeas_gate[cidx]) return;
+  const PointRef<T> a = cidx == 0 ? z : zb;
+  const TmpRef t = cidx == 0 ? ta : tb;
+  PDCS_GRID_LOOP(i, p.m) {
+    if (p.rk[i] < RK_SOC) continue;
+    const double d1 = p.d1[i];
+    t.tm[i] = ((double)a.gx[i] - (double)pc.gx[i]) / d1;
+    t.um[i] = d1 * ((double)a.y[i] - (double)pc.y[i]);
+  }
+  PDCS_GRID_LOOP(j, p.n) {
+    if (p.ck[j] < CK_SOC) continue;
+    const double d2 = p.d2[j];
+    t.tn[j] = -((double)a.gty[j] - (double)pc.gty[j]) / d2;
+    t.un[j] = d2 * ((double)a.x[j] - (double)pc.x[j]);
+  }
+}
+
+// Projection onto the recession cone of [lo, hi] (by bound finiteness).
+PDCS_DEV double proj_recession(double v, double lo, double hi) {
+  const bool lf = isfinite(lo), uf = isfinite(hi);
+  if (lf && uf) return 0.0;
+  if (lf) return fmax(v, 0.0);
+  if (uf) return fmin(v, 0.0);
+  return v;
+}
+
+constexpr int kInfS = 2, kInfM = 5, kInfK = kInfS + kInfM;
+
+// Ratios of both candidates (after the cone projections of k_infeas_prep's
+// vectors): primal = max(dual error of lambda, dual-cone violation of dy) /
+// (h^T dy + l^T lambda_1^+ - u^T lambda_1^-), dual = max(|G dx - P(G dx)| /
+// (1 + max(|G dx|, |P(G dx)|)), recession-cone violation of dx) / (-c^T dx),
+// infinity norms; +inf when the denominator is not positive.
+template <typename T>
+__global__ void __launch_bounds__(kEwThreads) k_infeas_reduce(Prob<T> p, Ctl* __restrict__ ctl,
+                                                              PointRef<T> z, PointRef<T> zb,
+                                                              PointRef<T> pc, TmpRef ta, TmpRef tb,
+                                                              double* __restrict__ part) {
+  if (!ctl->infeas_gate[0] && !ctl->infeas_gate[1]) return;  // uniform over the grid
+  const int cidx = blockIdx.y;
+  __shared__ double sh[kInfM * kEwThreads + kInfM];
+  // sums: dual objective of dy, -c^T dx; maxima: dual-side violation,
+  // |G dx - P(G dx)|, |G dx|, |P(G dx)|, recession violation of dx
+  double s[kInfS] = {0.0, 0.0};
+  double mx[kInfM] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (ctl->infeas_gate[cidx]) {
+    const PointRef<T> a = cidx == 0 ? z : zb;
+    const TmpRef t = cidx == 0 ? ta : tb;
+    PDCS_GRID_LOOP(i, p.m) {
+      const double d1 = p.d1[i];
+      const double dyt = (double)a.y[i] - (double)pc.y[i];
+      const double g = ((double)a.gx[i] - (double)pc.gx[i]) / d1;
+      const double dy = d1 * dyt;
+      const uint8_t kd = p.rk[i];
+      double pg, ey;
+      if (kd == RK_FREE) { pg = 0.0; ey = 0.0; }                 // {0} and its dual R
+      else if (kd == RK_NONNEG) { pg = fmax(g, 0.0); ey = fmin(dy, 0.0); }
+      else { pg = t.tm[i]; ey = dy - t.um[i]; }
+      mx[0] = fmax(mx[0], fabs(ey));
+      mx[1] = fmax(mx[1], fabs(g - pg));
+      mx[2] = fmax(mx[2], fabs(g));
+      mx[3] = fmax(mx[3], fabs(pg));
+      s[0] += (double)p.h[i] * dyt;  // h^T dy = hhat^T dy~
+    }
+    PDCS_GRID_LOOP(j, p.n) {
+      const double d2 = p.d2[j];
+      const double dxt = (double)a.x[j] - (double)pc.x[j];
+      const double lam = -((double)a.gty[j] - (double)pc.gty[j]) / d2;
+      const double dx = d2 * dxt;
+      const uint8_t kd = p.ck[j];
+      double el, ex;
+      if (kd == CK_BOX) {
+        const double lo = p.lo[j] * d2, hi = p.hi[j] * d2;  // unscaled bounds
+        el = lam - proj_lambda(lam, lo, hi);
+        ex = dx - proj_recession(dx, lo, hi);
+        if (isfinite(lo)) s[0] += lo * fmax(lam, 0.0);
+        if (isfinite(hi)) s[0] -= hi * fmax(-lam, 0.0);
+      } else if (kd == CK_ZERO) {
+        el = 0.0;
+        ex = dx;
+      } else if (kd == CK_NONNEG) {
+        el = fmin(lam, 0.0);
+        ex = fmin(dx, 0.0);
+      } else {
+        el = lam - t.tn[j];
+        ex = dx - t.un[j];
+      }
+      mx[0] = fmax(mx[0], fabs(el));
+      mx[4] = fmax(mx[4], fabs(ex));
+      s[1] -= (double)p.c[j] * dxt;  // -c^T dx = -chat^T dx~
+    }
+  }
+  block_sum<kInfS>(s, sh);
+  block_max<kInfM>(mx, sh);
+  if (threadIdx.x == 0) {
+    double* q = part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kInfK;
+    for (int k = 0; k < kInfS; ++k) q[k] = s[k];
+    for (int k = 0; k < kInfM; ++k) q[kInfS + k] = mx[k];
+  }
+  if (!last_block_done(&ctl->cnt[CNT_INFEAS])) return;
+  double R[2][2];
+  for (int cc = 0; cc < 2; ++cc) {
+    double S[kInfS], M[kInfM];
+    cta_reduce_parts<kInfS, kInfM>(part + (size_t)cc * gridDim.x * kInfK, gridDim.x, kInfK, S, M, sh);
+    const double num_d = fmax(M[1] / (1.0 + fmax(M[2], M[3])), M[4]);
+    R[cc][0] = S[0] > 0.0 ? M[0] / S[0] : INFINITY;
+    R[cc][1] = S[1] > 0.0 ? num_d / S[1] : INFINITY;
+  }
+  if (threadIdx.x != 0) return;
+  ctl->cnt[CNT_INFEAS] = 0u;
+  for (int cc = 0; cc < 2; ++cc) {
+    ctl->infeas[cc][0] = ctl->infeas_gate[cc] ? R[cc][0] : INFINITY;
+    ctl->infeas[cc][1] = ctl->infeas_gate[cc] ? R[cc][1] : INFINITY;
+  }
+}
 
 // ----------------------------------------------------------- init / output
 template <typename T>

@@ -2,9 +2,9 @@
 //
 // The paper has no counterpart: this is a service entry point for callers that
 // must not allocate device memory at the time of the call, for example code
-// running while a caching allocator owns the device's whole memory budget, or
-// a latency-critical path where cudaMalloc's implicit device synchronisation
-// cannot be afforded.  It is a variant of the solver's k_spmv: rows of up to
+// running while a caching allocator (such as PyTorch's) owns the device's whole
+// memory budget, where a cudaMalloc would fail or force the allocator to
+// release its cache.  It is a variant of the solver's k_spmv: rows of up to
 // kNaChunk nonzeros are summed by one warp each; longer rows are split into
 // kNaChunk-nonzero chunks whose partial sums are combined, in chunk order, by
 // the warp that finishes a row's last chunk (the same ticket scheme as k_spmv).
@@ -22,8 +22,10 @@
 //    (two streams, or two host threads, without ordering between them) race
 //    and give wrong results: serialise them;
 //  * the first call on a device looks up the scratch's device address
-//    (cudaGetSymbolAddress, with that device current) and caches it; that
-//    one-time set-up should come before any stream capture.
+//    (cudaGetSymbolAddress, with that device current) and caches it;
+//  * every call synchronises its stream once, to read the size check before
+//    anything is computed, so it cannot run while that stream is being
+//    captured into a graph: it refuses with PDCS_ERR_INVALID then.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,52 +73,68 @@ NaScratch* g_na_addr[kNaMaxDevices] = {};
 std::mutex g_na_mutex;
 
 // One CTA: list the rows longer than kNaChunk in row order, with their chunk
-// ranges.  Thread t owns a contiguous range of rows; a block-wide exclusive
-// scan of the per-thread counts gives each thread its output offsets.
+// ranges.  Warp w owns a contiguous range of rows and reads it 32 rows at a
+// time (lane l takes row r0 + l, so the row-pointer loads coalesce); ballots
+// count and, in a second sweep, place the long rows of each 32-row group in
+// order.  A block-wide exclusive scan of the warps' counts gives every warp
+// its output offsets.
 __global__ void __launch_bounds__(kNaScanThreads) k_na_scan(const int64_t* __restrict__ rp,
                                                             int64_t m, NaScratch* s) {
-  __shared__ long long sh_rows[kNaScanThreads], sh_chunks[kNaScanThreads];
-  const int t = threadIdx.x;
-  const int64_t per = (m + kNaScanThreads - 1) / kNaScanThreads;
-  const int64_t r0 = min(m, (int64_t)t * per), r1 = min(m, r0 + per);
+  constexpr int kWarps = kNaScanThreads / 32;
+  __shared__ long long sh_rows[kWarps], sh_chunks[kWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t per = ((m + kWarps - 1) / kWarps + 31) / 32 * 32;  // whole 32-row groups
+  const int64_t r0 = min(m, (int64_t)w * per), r1 = min(m, r0 + per);
   long long nr = 0, nc = 0;
-  for (int64_t r = r0; r < r1; ++r) {
-    const int64_t len = rp[r + 1] - rp[r];
-    if (len > kNaChunk) {
-      ++nr;
-      nc += (len + kNaChunk - 1) / kNaChunk;
-    }
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int64_t r = base + lane;
+    const int64_t len = r < r1 ? rp[r + 1] - rp[r] : 0;
+    const bool lng = len > kNaChunk;
+    long long ch = lng ? (len + kNaChunk - 1) / kNaChunk : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ch += __shfl_xor_sync(0xffffffffu, ch, o);
+    nr += __popc(__ballot_sync(0xffffffffu, lng));
+    nc += ch;
   }
-  sh_rows[t] = nr;
-  sh_chunks[t] = nc;
+  if (lane == 0) { sh_rows[w] = nr; sh_chunks[w] = nc; }
   __syncthreads();
-  // inclusive Hillis-Steele scan (integers: order does not matter)
-  for (int off = 1; off < kNaScanThreads; off <<= 1) {
-    const long long a = t >= off ? sh_rows[t - off] : 0, b = t >= off ? sh_chunks[t - off] : 0;
-    __syncthreads();
-    sh_rows[t] += a;
-    sh_chunks[t] += b;
-    __syncthreads();
+  long long slot = 0, chunk = 0, tot_rows = 0, tot_chunks = 0;
+  for (int k = 0; k < kWarps; ++k) {  // exclusive scan (integers: order is irrelevant)
+    if (k < w) { slot += sh_rows[k]; chunk += sh_chunks[k]; }
+    tot_rows += sh_rows[k];
+    tot_chunks += sh_chunks[k];
   }
-  const long long tot_rows = sh_rows[kNaScanThreads - 1], tot_chunks = sh_chunks[kNaScanThreads - 1];
   const bool overflow = tot_rows > kNaMaxLongRows || tot_chunks > kNaMaxChunks;
-  if (t == 0) {
+  if (threadIdx.x == 0) {
     s->status.long_rows = tot_rows;
     s->status.chunks = tot_chunks;
     s->status.overflow = overflow ? 1 : 0;
     if (!overflow) s->first[tot_rows] = (int)tot_chunks;
   }
-  if (overflow) return;
-  long long slot = sh_rows[t] - nr, chunk = sh_chunks[t] - nc;
-  for (int64_t r = r0; r < r1; ++r) {
-    const int64_t len = rp[r + 1] - rp[r];
-    if (len <= kNaChunk) continue;
-    const long long k = (len + kNaChunk - 1) / kNaChunk;
-    s->row[slot] = r;
-    s->first[slot] = (int)chunk;
-    for (long long c = 0; c < k; ++c) s->chunk_slot[chunk + c] = (int)slot;
-    ++slot;
-    chunk += k;
+  if (overflow || nr == 0) return;
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int64_t r = base + lane;
+    const int64_t len = r < r1 ? rp[r + 1] - rp[r] : 0;
+    const bool lng = len > kNaChunk;
+    const unsigned bal = __ballot_sync(0xffffffffu, lng);
+    if (bal == 0u) continue;
+    const long long k = lng ? (len + kNaChunk - 1) / kNaChunk : 0;
+    // chunks of the long rows of this group before lane l (inclusive scan - own)
+    long long pre = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long v = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += v;
+    }
+    if (lng) {
+      const long long my_slot = slot + __popc(bal & ((1u << lane) - 1u));
+      const long long my_chunk = chunk + pre - k;
+      s->row[my_slot] = r;
+      s->first[my_slot] = (int)my_chunk;
+      for (long long c = 0; c < k; ++c) s->chunk_slot[my_chunk + c] = (int)my_slot;
+    }
+    slot += __popc(bal);
+    chunk += __shfl_sync(0xffffffffu, pre, 31);
   }
 }
 
@@ -192,6 +210,18 @@ extern "C" int pdcs_spmv_noalloc(int64_t m, int64_t n, const int64_t* row_ptr,
   if (m == 0) return PDCS_OK;
   if (!row_ptr || !y || (n > 0 && (!col_idx || !val || !x)))
     return na_fail(PDCS_ERR_INVALID, "pdcs_spmv_noalloc: NULL array");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // the size check below synchronises the stream, which would invalidate a
+  // capture in progress on it: refuse instead
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return na_fail(PDCS_ERR_CUDA, "pdcs_spmv_noalloc: cannot query the stream's capture state");
+  }
+  if (cap != cudaStreamCaptureStatusNone)
+    return na_fail(PDCS_ERR_INVALID,
+                   "pdcs_spmv_noalloc: the stream is being captured; this call synchronises the "
+                   "stream and cannot be captured");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
     return na_fail(PDCS_ERR_CUDA, "pdcs_spmv_noalloc: no usable current device");
@@ -211,7 +241,6 @@ extern "C" int pdcs_spmv_noalloc(int64_t m, int64_t n, const int64_t* row_ptr,
     }
     s = g_na_addr[dev];
   }
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   k_na_scan<<<1, kNaScanThreads, 0, st>>>(row_ptr, m, s);
   NaStatus hs;
   cudaError_t e = cudaGetLastError();

@@ -177,19 +177,32 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
   return p;
 }
 
-template <typename T, typename Out>
-static void launch_spmv_out(const SpmvPlan& p, const int64_t* rp, const int32_t* ci, const T* vv,
-                            const T* x, const Out& out, const int* gate, cudaStream_t st,
-                            KTimer* tm = nullptr) {
+// V: matrix value type; x: the gathered vector (FP64, or its FP32 (hi, lo)
+// shadow for FP32 values).
+template <typename V, typename Out>
+static void launch_spmv_out(const SpmvPlan& p, const int64_t* rp, const int32_t* ci, const V* vv,
+                            const typename SpmvX<V>::type* x, const Out& out, const int* gate,
+                            cudaStream_t st, KTimer* tm = nullptr) {
   if (p.ntasks == 0) return;
-  k_spmv<T, Out><<<p.ntasks, kSpmvThreads, 0, st>>>(p.tasks, rp, ci, vv, x, out, p.partial,
+  k_spmv<V, Out><<<p.ntasks, kSpmvThreads, 0, st>>>(p.tasks, rp, ci, vv, x, out, p.partial,
                                                     p.counters, gate, tm);
 }
 
-template <typename T>
-static void launch_spmv(const SpmvPlan& p, const int64_t* rp, const int32_t* ci, const T* vv,
-                        const T* x, T* y, const int* gate, cudaStream_t st, KTimer* tm = nullptr) {
-  launch_spmv_out<T>(p, rp, ci, vv, x, StoreOut<T>{y}, gate, st, tm);
+template <typename V>
+static void launch_spmv(const SpmvPlan& p, const int64_t* rp, const int32_t* ci, const V* vv,
+                        const typename SpmvX<V>::type* x, double* y, const int* gate,
+                        cudaStream_t st, KTimer* tm = nullptr) {
+  launch_spmv_out<V>(p, rp, ci, vv, x, StoreOut<double>{y}, gate, st, tm);
+}
+
+// FP32 (hi, lo) shadow of an FP64 vector (the gathered operand of FP32-value
+// products).
+__global__ void k_split(const double* __restrict__ v, float2* __restrict__ out, int64_t n,
+                        const int* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = split_ff(v[i]);
 }
 
 // ------------------------------------------------------------- cone tables
@@ -327,8 +340,13 @@ struct pdcs_handle {
 
 namespace pdcs {
 
-template <typename T>
+// MV: type of the stored matrix values used by the iteration (double: FP64
+// mode; float: FP32 mode, with FP64 vectors and float-float products, and
+// the FP64 values kept for the checks' products).  Vectors are FP64 (T).
+template <typename MV>
 struct Solver : SolverBase {
+  using T = double;
+  static constexpr bool kF32 = std::is_same<MV, float>::value;
   Arena ar;
   cudaStream_t st = nullptr;       // this handle's stream (captured graphs run here)
   cudaStream_t user_st = nullptr;  // caller's stream: work is ordered after it
@@ -338,7 +356,10 @@ struct Solver : SolverBase {
   // matrix (scaled) and its transpose
   int64_t *rp = nullptr, *rpT = nullptr;
   int32_t *ci = nullptr, *ciT = nullptr;
-  T *vv = nullptr, *vvT = nullptr;
+  MV *vv = nullptr, *vvT = nullptr;        // values of the iteration's products
+  double *vv64 = nullptr, *vvT64 = nullptr;  // FP64 values (== vv in FP64 mode)
+  float2 *sx = nullptr, *sy = nullptr;     // FP32 mode: shadows of the gathered vectors
+  double *gxt = nullptr, *gtyt = nullptr;  // FP32 mode: FP64 products of z at checks
   SpmvPlan planG, planGT;
   // problem data
   T *h = nullptr, *c = nullptr;
@@ -348,6 +369,8 @@ struct Solver : SolverBase {
   int64_t *row_rot = nullptr, *col_rot = nullptr;
   int64_t nrow_rot = 0, ncol_rot = 0;
   double eta0 = 1.0, omega0 = 1.0, h1 = 0, c1 = 0, hinf = 0, cinf = 0;
+  double eta_fixed = 1.0;  // step of the non-adaptive mode: 1 / sqrt(||Ghat||_1 ||Ghat||_inf)
+  bool infeas_on = false;
   // state
   T *x, *y, *xh, *yh, *x0, *y0, *gx, *gty, *gxh, *gtyh, *gx0, *gty0;
   T *xb, *yb, *gxb, *gtyb, *xc, *yc, *gxc, *gtyc;
@@ -548,11 +571,23 @@ struct Solver : SolverBase {
     unsigned long long* amax = ar.alloc<unsigned long long>(1);
     CK(cudaMemsetAsync(amax, 0, sizeof(unsigned long long), st));
     rp = drp; ci = dci; rpT = drpT; ciT = dciT;
-    vv = ar.alloc<T>(nnz);
-    vvT = ar.alloc<T>(nnz);
+    vv64 = ar.alloc<double>(nnz);
+    vvT64 = ar.alloc<double>(nnz);
     if (m > 0) {
-      k_apply_scale<T><<<warp_grid(m), 256, 0, st>>>(drp, dci, dv, m, d1, d2, 0, vv, amax);
-      k_apply_scale<T><<<warp_grid(n), 256, 0, st>>>(drpT, dciT, dvT, n, d2, d1, 1, vvT, nullptr);
+      k_apply_scale<double><<<warp_grid(m), 256, 0, st>>>(drp, dci, dv, m, d1, d2, 0, vv64, amax);
+      k_apply_scale<double><<<warp_grid(n), 256, 0, st>>>(drpT, dciT, dvT, n, d2, d1, 1, vvT64, nullptr);
+    }
+    if constexpr (kF32) {
+      // the same scaled values rounded to FP32 (G and G^T stay transposes)
+      vv = ar.alloc<float>(nnz);
+      vvT = ar.alloc<float>(nnz);
+      if (m > 0) {
+        k_apply_scale<float><<<warp_grid(m), 256, 0, st>>>(drp, dci, dv, m, d1, d2, 0, vv, nullptr);
+        k_apply_scale<float><<<warp_grid(n), 256, 0, st>>>(drpT, dciT, dvT, n, d2, d1, 1, vvT, nullptr);
+      }
+    } else {
+      vv = vv64;
+      vvT = vvT64;
     }
     double* sh_ = ar.alloc<double>(m);
     double* sc_ = ar.alloc<double>(n);
@@ -574,11 +609,23 @@ struct Solver : SolverBase {
       CK(cudaStreamSynchronize(st));
       ar.release(tmp);
     }
-    double* nrm = ar.alloc<double>(8);
+    double* nrm = ar.alloc<double>(16);
     k_vec_norms<<<1, 1024, 0, st>>>(sh_, m, d1, nrm);
     k_vec_norms<<<1, 1024, 0, st>>>(sc_, n, d2, nrm + 4);
+    {
+      // largest row / column absolute sums of Ghat (the non-adaptive step)
+      double* rs = ar.alloc<double>(std::max<int64_t>(m, 1));
+      double* cs = ar.alloc<double>(n);
+      if (m > 0) k_row_norms<<<warp_grid(m), 256, 0, st>>>(drp, dci, dv, m, d1, d2, 0, 1, 1.0, rs);
+      k_row_norms<<<warp_grid(n), 256, 0, st>>>(drpT, dciT, dvT, n, d2, d1, 1, 1, 1.0, cs);
+      k_vec_norms<<<1, 1024, 0, st>>>(rs, m, nullptr, nrm + 8);
+      k_vec_norms<<<1, 1024, 0, st>>>(cs, n, nullptr, nrm + 12);
+      CK(cudaStreamSynchronize(st));
+      ar.release(rs);
+      ar.release(cs);
+    }
     CK(cudaGetLastError());
-    double hn[8];
+    double hn[16];
     unsigned long long hamax = 0;
     CK(cudaMemcpyAsync(hn, nrm, sizeof(hn), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&hamax, amax, sizeof(hamax), cudaMemcpyDeviceToHost, st));
@@ -589,6 +636,9 @@ struct Solver : SolverBase {
     double gmax;
     std::memcpy(&gmax, &hamax, sizeof(double));
     eta0 = gmax > 0 ? 1.0 / gmax : 1.0;  // Algorithm 1: 1 / ||G||_inf
+    eta_fixed = (hn[10] > 0 && hn[14] > 0) ? 1.0 / std::sqrt(hn[14] * hn[10]) : 1.0;
+    infeas_on = opt.eps_primal_infeasible_low_acc > 0 || opt.eps_dual_infeasible_low_acc > 0 ||
+                opt.eps_primal_infeasible_high_acc > 0 || opt.eps_dual_infeasible_high_acc > 0;
     ar.release(dv); ar.release(dvT); ar.release(dh); ar.release(dc);
     ar.release(sh_); ar.release(sc_); ar.release(nrm); ar.release(amax); ar.release(derr);
     // ---- kinds, cone tables, plans
@@ -600,7 +650,7 @@ struct Solver : SolverBase {
     copy_in(ck, hck.data(), n, st);
     fill_table(rows, rsoc, rbig, rexp, rexpd, d1, m);
     fill_table(cols, csoc, cbig, cexp, cexpd, d2, n);
-    const int small_g = sizeof(T) == 8 ? 4 : 8;
+    const int small_g = sizeof(MV) == 8 ? 4 : 8;
     planG = build_plan(hrp, ar, st, small_g);
     planGT = build_plan(hrpT, ar, st, small_g);
     alloc_state();
@@ -810,6 +860,15 @@ struct Solver : SolverBase {
       tm[k] = ar.alloc<double>(m); um[k] = ar.alloc<double>(m); py[k] = ar.alloc<double>(m);
       tn[k] = ar.alloc<double>(n); un[k] = ar.alloc<double>(n); px[k] = ar.alloc<double>(n);
     }
+    if constexpr (kF32) {
+      sx = ar.alloc<float2>(n);
+      sy = ar.alloc<float2>(std::max<int64_t>(m, 1));
+      gxt = ar.alloc<double>(std::max<int64_t>(m, 1));
+      gtyt = ar.alloc<double>(n);
+    } else {
+      gxt = gx;
+      gtyt = gty;
+    }
     const int g = ew_grid(std::max(m, n));
     part = ar.alloc<double>((int64_t)g * kStatK * 2 + 64);
     ctl = ar.alloc<Ctl>(1);
@@ -849,13 +908,14 @@ struct Solver : SolverBase {
 
   void get_profile(pdcs_profile* pr) override {
     std::memset(pr, 0, sizeof(*pr));
-    const double vb = (double)sizeof(T);
-    pr->g_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(m + 1) + vb * (double)(n + m);
+    // values + column indices once, row pointers once, the gathered vector
+    // (FP64 or its 8-byte FP32 pair) and the result once
+    const double vb = (double)sizeof(MV);
+    pr->g_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(m + 1) + 8.0 * (double)(n + m);
     // the dual step in the product's epilogue: y, G x, h and the row kind
-    // read, yhat written per row, G xhat - h on the cone rows (FP64)
-    if (dual_in_product)
-      pr->g_bytes += (double)m * (4.0 * vb + 1.0) + (std::is_same<T, double>::value ? 8.0 * (double)cone_rows : 0.0);
-    pr->gt_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(n + 1) + vb * (double)(n + m);
+    // read, yhat written per row, G xhat - h on the cone rows
+    if (dual_in_product) pr->g_bytes += (double)m * (4.0 * 8.0 + 1.0) + 8.0 * (double)cone_rows;
+    pr->gt_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(n + 1) + 8.0 * (double)(n + m);
     pr->nnz_flops = 2.0 * (double)nnz;
     pr->graph_launches = graph_launches;
     if (use_cond)
@@ -902,12 +962,37 @@ struct Solver : SolverBase {
 
   PointRef<T> pz() const { return PointRef<T>{x, y, gx, gty}; }
   PointRef<T> pzb() const { return PointRef<T>{xb, yb, gxb, gtyb}; }
+  // z with the products the checks use (FP64 values; in FP64 mode the carried ones)
+  PointRef<T> pzc() const { return PointRef<T>{x, y, gxt, gtyt}; }
+
+  // Product with the iteration's values: the FP64 vector x, or (FP32 values)
+  // its FP32 shadow xs.  tr selects G^T.
+  template <typename Out>
+  void spmv_it_out(bool tr, const double* xv, const float2* xs, const Out& out, const int* gate,
+                   cudaStream_t s, KTimer* tmr = nullptr) {
+    const SpmvPlan& pl = tr ? planGT : planG;
+    if constexpr (kF32)
+      launch_spmv_out<float>(pl, tr ? rpT : rp, tr ? ciT : ci, tr ? vvT : vv, xs, out, gate, s, tmr);
+    else
+      launch_spmv_out<double>(pl, tr ? rpT : rp, tr ? ciT : ci, tr ? vvT : vv, xv, out, gate, s, tmr);
+  }
+  void spmv_it(bool tr, const double* xv, const float2* xs, double* yv, const int* gate,
+               cudaStream_t s, KTimer* tmr = nullptr) {
+    spmv_it_out(tr, xv, xs, StoreOut<double>{yv}, gate, s, tmr);
+  }
+  // Product with the FP64 values (statistics of the checks).
+  void spmv64(bool tr, const double* xv, double* yv, const int* gate, cudaStream_t s,
+              KTimer* tmr = nullptr) {
+    launch_spmv<double>(tr ? planGT : planG, tr ? rpT : rp, tr ? ciT : ci, tr ? vvT64 : vv64, xv,
+                        yv, gate, s, tmr);
+  }
 
   void rec_attempt(cudaStream_t s, cudaGraphConditionalHandle hA) {
     const Prob<T> p = prob();
     const int gn = ew_grid(n), gm = ew_grid(m), gmx = ew_grid(std::max(m, n));
-    k_primal<T><<<gn, kEwThreads, 0, s>>>(p, ctl, x, gty, xh);
+    k_primal<T><<<gn, kEwThreads, 0, s>>>(p, ctl, x, gty, xh, kF32 && !cols.any() ? sx : nullptr);
     project<T>(cols, xh, xh, 1, d2, 1, 0, &ctl->g_attempt, nullptr, s);
+    if (kF32 && cols.any()) k_split<<<gn, 256, 0, s>>>(xh, sx, n, &ctl->g_attempt);
     // FP64: the dual iterate (onto diag(1/d1) K*) and the primal residual's
     // argument G xhat - h (onto diag(d1) K) are projected in one launch; the
     // residual is then also formed for rejected attempts, where it is unused
@@ -916,10 +1001,9 @@ struct Solver : SolverBase {
     KTimer* tg = timers ? timers + TM_SPMV_G : nullptr;
     if (dual_in_product) {
       // long rows: the dual step rides on the product's epilogue
-      launch_spmv_out<T>(planG, rp, ci, vv, xh, DualOut<T>{p, ctl, y, gx, gxh, yh, res},
-                         &ctl->g_attempt, s, tg);
+      spmv_it_out(false, xh, sx, DualOut<T>{p, ctl, y, gx, gxh, yh, res}, &ctl->g_attempt, s, tg);
     } else {
-      launch_spmv<T>(planG, rp, ci, vv, xh, gxh, &ctl->g_attempt, s, tg);
+      spmv_it(false, xh, sx, gxh, &ctl->g_attempt, s, tg);
       k_dual<T><<<gm, kEwThreads, 0, s>>>(p, ctl, y, gxh, gx, yh, res);
     }
     if (fuse)
@@ -927,8 +1011,8 @@ struct Solver : SolverBase {
                  &ctl->g_attempt, s, true);
     else
       project<T>(rows, yh, yh, 1, d1, 1, 1, &ctl->g_attempt, nullptr, s);
-    k_step<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, xh, y, yh, gxh, gx, part);
-    launch_spmv<T>(planGT, rpT, ciT, vvT, yh, gtyh, &ctl->g_accept, s, timers ? timers + TM_SPMV_GT : nullptr);
+    k_step<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, xh, y, yh, gxh, gx, part, sy);
+    spmv_it(true, yh, sy, gtyh, &ctl->g_accept, s, timers ? timers + TM_SPMV_GT : nullptr);
     const PointRef<T> ph{xh, yh, gxh, gtyh};
     const TmpRef t0{tm[0], tn[0], nullptr, nullptr};
     if (!fuse) {
@@ -951,35 +1035,55 @@ struct Solver : SolverBase {
     KTimer* tmisc = timers ? timers + TM_CHECK_MISC : nullptr;
     KTimer* tchk = timers ? timers + TM_SPMV_CHECK : nullptr;
     k_average<T><<<gmx, kEwThreads, 0, s>>>(n, m, ctl, xs, ys, xb, yb, tmisc);
-    launch_spmv<T>(planG, rp, ci, vv, xb, gxb, g, s, tchk);
-    launch_spmv<T>(planGT, rpT, ciT, vvT, yb, gtyb, g, s, tchk);
+    spmv64(false, xb, gxb, g, s, tchk);
+    spmv64(true, yb, gtyb, g, s, tchk);
+    if constexpr (kF32) {
+      // FP64 products of z: the checks' statistics refer to the FP64 matrix
+      spmv64(false, x, gxt, g, s, tchk);
+      spmv64(true, y, gtyt, g, s, tchk);
+    }
     const TmpRef ta{tm[0], tn[0], um[0], un[0]}, tb{tm[1], tn[1], um[1], un[1]};
-    k_res_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, g, pz(), pzb(), ta, tb);
+    k_res_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, g, pzc(), pzb(), ta, tb);
     project<double>(rows, tm[0], tm[1], 2, d1, 0, 0, g, g, s);
     project<double>(cols, tn[0], tn[1], 2, d2, 0, 1, g, g, s);
     project<double>(rows, um[0], um[1], 2, nullptr, 0, 0, g, g, s);
     project<double>(cols, un[0], un[1], 2, nullptr, 0, 1, g, g, s);
-    k_point_stats<T, true><<<gmx, kEwThreads, 0, s>>>(p, ctl, g, 1, pz(), x0, y0, ta, part);
+    k_point_stats<T, true><<<gmx, kEwThreads, 0, s>>>(p, ctl, g, 1, pzc(), x0, y0, ta, part);
     k_point_stats<T, true><<<gmx, kEwThreads, 0, s>>>(p, ctl, g, 2, pzb(), x0, y0, tb, part + (int64_t)gmx * kStatK);
   }
 
   void rec_probe(cudaStream_t s, cudaGraphConditionalHandle hB) {
     const Prob<T> p = prob();
     const int gmx = ew_grid(std::max(m, n));
-    k_probe_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pz(), pzb(), px[0], py[0], px[1], py[1]);
+    k_probe_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pzc(), pzb(), px[0], py[0], px[1], py[1]);
     project<double>(cols, px[0], px[1], 2, d2, 1, 0, &ctl->bs[0].active, &ctl->bs[1].active, s);
     project<double>(rows, py[0], py[1], 2, d1, 1, 1, &ctl->bs[0].active, &ctl->bs[1].active, s);
-    k_probe_reduce<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pz(), pzb(), px[0], py[0], px[1], py[1], part, hB, use_cond);
+    k_probe_reduce<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pzc(), pzb(), px[0], py[0], px[1], py[1], part, hB, use_cond);
   }
 
   void rec_check_end(cudaStream_t s) {
     const int gmx = ew_grid(std::max(m, n));
+    if (infeas_on) {
+      // infeasibility ratios of both candidates' change since the last candidate
+      const Prob<T> p = prob();
+      const PointRef<T> pc{xc, yc, gxc, gtyc};
+      const TmpRef ta{tm[0], tn[0], um[0], un[0]}, tb{tm[1], tn[1], um[1], un[1]};
+      const int* g0 = &ctl->infeas_gate[0];
+      const int* g1 = &ctl->infeas_gate[1];
+      k_infeas_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pzc(), pzb(), pc, ta, tb);
+      project<double>(rows, tm[0], tm[1], 2, nullptr, 0, 0, g0, g1, s);
+      project<double>(rows, um[0], um[1], 2, nullptr, 0, 1, g0, g1, s);
+      project<double>(cols, tn[0], tn[1], 2, nullptr, 0, 1, g0, g1, s);
+      project<double>(cols, un[0], un[1], 2, nullptr, 0, 0, g0, g1, s);
+      k_infeas_reduce<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pzc(), pzb(), pc, ta, tb, part);
+    }
     k_check_decide<<<1, 1, 0, s>>>(ctl, trace);
     KTimer* tmisc = timers ? timers + TM_CHECK_MISC : nullptr;
     KTimer* tchk = timers ? timers + TM_SPMV_CHECK : nullptr;
-    k_cand_copy<T><<<gmx, kEwThreads, 0, s>>>(n, m, ctl, pz(), pzb(), xc, yc, gxc, gtyc, x0, y0, x, y, xs, ys, tmisc);
-    launch_spmv<T>(planG, rp, ci, vv, x0, gx0, &ctl->g_restart, s, tchk);
-    launch_spmv<T>(planGT, rpT, ciT, vvT, y0, gty0, &ctl->g_restart, s, tchk);
+    k_cand_copy<T><<<gmx, kEwThreads, 0, s>>>(n, m, ctl, pzc(), pzb(), xc, yc, gxc, gtyc, x0, y0, x, y,
+                                              xs, ys, sx, sy, tmisc);
+    spmv_it(false, x0, sx, gx0, &ctl->g_restart, s, tchk);
+    spmv_it(true, y0, sy, gty0, &ctl->g_restart, s, tchk);
     k_copy_products<T><<<gmx, kEwThreads, 0, s>>>(n, m, &ctl->g_restart, gx0, gty0, gx, gty, tmisc);
     k_check_end<<<1, 1, 0, s>>>(ctl);
   }
@@ -1062,6 +1166,17 @@ struct Solver : SolverBase {
     c0.trace_cap = trace ? opt.trace_capacity : 0;
     c0.guard_cap = (int)std::min<int64_t>(4 * c0.check_freq + 16, 1 << 20);
     c0.probe_cap = 256;
+    c0.adaptive_step = opt.use_adaptive_step_size_weight ? 1 : 0;
+    c0.gap_restart = opt.use_duality_gap_restart ? 1 : 0;
+    c0.kkt_restart = opt.use_kkt_restart ? 1 : 0;
+    c0.kkt_freq = std::max<int64_t>(1, opt.kkt_restart_freq);
+    c0.eta_fixed = eta_fixed;
+    if (!c0.adaptive_step) c0.eta = c0.eta_hat = c0.eta_acc = eta_fixed;
+    c0.eps_pl = opt.eps_primal_infeasible_low_acc;
+    c0.eps_dl = opt.eps_dual_infeasible_low_acc;
+    c0.eps_ph = opt.eps_primal_infeasible_high_acc;
+    c0.eps_dh = opt.eps_dual_infeasible_high_acc;
+    c0.infeas_on = infeas_on ? 1 : 0;
   }
 
   void upload_ctl() { CK(cudaMemcpyAsync(ctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, st)); }
@@ -1091,10 +1206,14 @@ struct Solver : SolverBase {
 
   // G x, G^T y, G x0, G^T y0 from the current vectors.
   void refresh_products() {
-    launch_spmv<T>(planG, rp, ci, vv, x, gx, nullptr, st);
-    launch_spmv<T>(planGT, rpT, ciT, vvT, y, gty, nullptr, st);
-    launch_spmv<T>(planG, rp, ci, vv, x0, gx0, nullptr, st);
-    launch_spmv<T>(planGT, rpT, ciT, vvT, y0, gty0, nullptr, st);
+    const int gn = ew_grid(n), gm = ew_grid(m);
+    const double* vs[4] = {x, y, x0, y0};
+    double* ps[4] = {gx, gty, gx0, gty0};
+    for (int k = 0; k < 4; ++k) {
+      const bool tr = (k & 1) != 0;
+      if (kF32) k_split<<<tr ? gm : gn, 256, 0, st>>>(vs[k], tr ? sy : sx, tr ? m : n, nullptr);
+      spmv_it(tr, vs[k], tr ? sy : sx, ps[k], nullptr, st);
+    }
     CK(cudaGetLastError());
   }
 
@@ -1181,6 +1300,8 @@ struct Solver : SolverBase {
     eager_a = eager_b = 0;
     bodies_a0 = hctl->bodies_a;
     bodies_b0 = hctl->bodies_b;
+    long long printed = hctl->iter;
+    const long long pf = std::max<int64_t>(1, opt.print_freq);
     while (true) {
       if (use_cond) CK(cudaGraphLaunch(exec, st));
       else run_period_eager();
@@ -1188,9 +1309,11 @@ struct Solver : SolverBase {
       CK(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       status = hctl->status;
-      if (opt.verbose)
+      if (opt.verbose && (hctl->iter / pf != printed / pf || status != kRunning)) {
+        printed = hctl->iter;
         fprintf(stderr, "[pdcs] iter %lld kbar %lld restarts %lld eta %.3e omega %.3e maxErr %.3e\n",
                 hctl->iter, hctl->kbar, hctl->restarts, hctl->eta_acc, hctl->omega, hctl->st[0].max_err);
+      }
       if (status != kRunning) break;
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (el > opt.time_limit) {
@@ -1206,7 +1329,12 @@ struct Solver : SolverBase {
     const Prob<T> p = prob();
     const int gmx = ew_grid(std::max(m, n));
     const bool cand = hctl->have_cand != 0;
-    const PointRef<T> pr = cand ? PointRef<T>{xc, yc, gxc, gtyc} : pz();
+    if (kF32 && !cand) {
+      // no candidate yet: FP64 products of z for the reported errors
+      spmv64(false, x, gxt, nullptr, st);
+      spmv64(true, y, gtyt, nullptr, st);
+    }
+    const PointRef<T> pr = cand ? PointRef<T>{xc, yc, gxc, gtyc} : pzc();
     // final statistics of the returned point (slot 3); g_check serves as an
     // always-on gate here (no graph runs until the next call re-initialises it)
     int* one = &ctl->g_check;
@@ -1425,7 +1553,6 @@ struct BatchSolver : BatchBase {
         const pdcs_cone& cn = I.row_cones[k];
         rcones.push_back(cn);
         if (cn.type == PDCS_CONE_SOC || cn.type == PDCS_CONE_RSOC) {
-          if (cn.dim > kBatchThreads * kBatchSocEpt) throw Fail{PDCS_ERR_UNSUPPORTED, "batched SOC blocks are limited to 4096 elements"};
           srs.push_back(off); srd.push_back((int32_t)cn.dim);
         } else if (cn.type == PDCS_CONE_EXP || cn.type == PDCS_CONE_DUAL_EXP) {
           ers.push_back(off); erd.push_back(cn.type == PDCS_CONE_DUAL_EXP ? 1 : 0);
@@ -1442,7 +1569,6 @@ struct BatchSolver : BatchBase {
       for (int64_t k = 0; k < I.n_col_cones; ++k) {
         const pdcs_cone& cn = I.col_cones[k];
         if (cn.type == PDCS_CONE_SOC || cn.type == PDCS_CONE_RSOC) {
-          if (cn.dim > kBatchThreads * kBatchSocEpt) throw Fail{PDCS_ERR_UNSUPPORTED, "batched SOC blocks are limited to 4096 elements"};
           scs.push_back(off); scd.push_back((int32_t)cn.dim);
         } else if (cn.type == PDCS_CONE_EXP || cn.type == PDCS_CONE_DUAL_EXP) {
           ecs.push_back(off); ecd.push_back(cn.type == PDCS_CONE_DUAL_EXP ? 1 : 0);
@@ -1476,6 +1602,7 @@ struct BatchSolver : BatchBase {
     dqueue = sv.ar.template alloc<unsigned int>(1);
     dtimes = sv.ar.template alloc<unsigned long long>(2 * cnt);
     sv.init_ctl();
+    sv.hctl->infeas_on = 0;  // the batched engine does not run the infeasibility tests
     CK(cudaMemcpyAsync(dtmpl, sv.hctl, sizeof(Ctl), cudaMemcpyHostToDevice, sv.st));
     int dev = 0, sms = 0, occ = 0;
     CK(cudaGetDevice(&dev));
@@ -1563,9 +1690,9 @@ struct BatchSolver : BatchBase {
   void solve(double* xo, double* yo, double* so, pdcs_result* res, double* finish_s) override {
     sv.order_after_user();
     launch((int32_t)count);
-    const Prob<T> p = sv.prob();
+    const Prob<double> p = sv.prob();
     const int gmx = ew_grid(std::max(sv.m, sv.n));
-    k_unscale<T><<<gmx, 256, 0, sv.st>>>(p, sv.xc, sv.yc, sv.gxc, sv.obuf_n, sv.obuf_m, sv.obuf_s);
+    k_unscale<double><<<gmx, 256, 0, sv.st>>>(p, sv.xc, sv.yc, sv.gxc, sv.obuf_n, sv.obuf_m, sv.obuf_s);
     if (sv.ncol_rot) k_rotate_pairs<<<ew_grid(sv.ncol_rot), 256, 0, sv.st>>>(sv.obuf_n, sv.col_rot, sv.ncol_rot);
     if (sv.nrow_rot) {
       k_rotate_pairs<<<ew_grid(sv.nrow_rot), 256, 0, sv.st>>>(sv.obuf_m, sv.row_rot, sv.nrow_rot);
@@ -1632,6 +1759,15 @@ void pdcs_default_options(pdcs_options* o) {
   o->trace_capacity = 0;
   o->profile = 0;
   o->eager = 0;
+  o->use_adaptive_step_size_weight = 1;
+  o->use_duality_gap_restart = 1;
+  o->use_kkt_restart = 0;
+  o->kkt_restart_freq = 2000;
+  o->print_freq = 2000;
+  o->eps_primal_infeasible_low_acc = 1e-12;
+  o->eps_dual_infeasible_low_acc = 1e-12;
+  o->eps_primal_infeasible_high_acc = 1e-16;
+  o->eps_dual_infeasible_high_acc = 1e-16;
 }
 
 const char* pdcs_last_error(void) { return g_last_error.c_str(); }
@@ -1678,6 +1814,10 @@ int pdcs_setup(pdcs_handle** out, int64_t m, int64_t n, const int64_t* row_ptr,
   if (opt) o = *opt; else pdcs_default_options(&o);
   if (o.precision != 0 && o.precision != 1) return fail(PDCS_ERR_INVALID, "precision must be 0 or 1");
   if (o.check_freq < 1) return fail(PDCS_ERR_INVALID, "check_freq must be >= 1");
+  if (o.use_kkt_restart && o.kkt_restart_freq < 1) return fail(PDCS_ERR_INVALID, "kkt_restart_freq must be >= 1");
+  if (!(o.eps_primal_infeasible_low_acc >= 0) || !(o.eps_dual_infeasible_low_acc >= 0) ||
+      !(o.eps_primal_infeasible_high_acc >= 0) || !(o.eps_dual_infeasible_high_acc >= 0))
+    return fail(PDCS_ERR_INVALID, "infeasibility thresholds must be >= 0");
   if (o.method != 0 && o.method != 1) return fail(PDCS_ERR_INVALID, "method must be 0 or 1");
   if (o.max_iter < 1) return fail(PDCS_ERR_INVALID, "max_iter must be >= 1");
   if (o.ruiz_iters < 0) return fail(PDCS_ERR_INVALID, "ruiz_iters must be >= 0");

@@ -15,8 +15,13 @@
 //           written to a partial buffer and the last chunk CTA of the row (an
 //           atomic ticket, no waiting) adds them in chunk order, so the result
 //           is deterministic.
-// Accumulation: FP64 in FP64 mode (one DFMA per nonzero); in FP32 mode FP32
-// products with a compensated (Kahan) FP32 sum per lane, combined in FP64.
+// Accumulation: in FP64 mode the values are FP64 and each nonzero is one
+// DFMA.  In FP32 mode the values are FP32 and the gathered FP64 vector is read
+// as a (hi, lo) pair of FP32 numbers (a "shadow" written by the kernel that
+// produces the vector): each product v*hi is formed exactly as p + e (FMA
+// error term), v*lo is added to e, and p is summed with an error-free
+// two-sum into a float-float accumulator, so a row sum carries ~2^-48 relative
+// error without using the FP64 pipe, which is the scarce unit of this GPU.
 // Each lane issues the index, value and gather loads of kSpmvUnroll nonzeros
 // before it adds them (in their order, so the sum is the plain strided one):
 // the streams run near the read bandwidth only with that many loads in flight.
@@ -40,7 +45,17 @@ struct SpmvTask {
   int64_t pad;
 };
 
-template <typename T>
+// Element type of the gathered vector for matrix values of type V.
+template <typename V>
+struct SpmvX {
+  using type = double;
+};
+template <>
+struct SpmvX<float> {
+  using type = float2;  // (hi, lo) FP32 split of an FP64 value
+};
+
+template <typename V>
 struct Acc;
 
 template <>
@@ -52,15 +67,25 @@ struct Acc<double> {
 
 template <>
 struct Acc<float> {
-  float s = 0.0f, comp = 0.0f;
-  PDCS_DEV void add(float v, float x) {
-    const float y = __fmaf_rn(v, x, -comp);
-    const float t = __fadd_rn(s, y);
-    comp = __fsub_rn(__fsub_rn(t, s), y);
+  float s = 0.0f, c = 0.0f;  // value s + c
+  PDCS_DEV void add(float v, float2 x) {
+    const float p = __fmul_rn(v, x.x);
+    float e = __fmaf_rn(v, x.x, -p);  // v * hi = p + e exactly
+    e = __fmaf_rn(v, x.y, e);
+    const float t = __fadd_rn(s, p);  // two-sum: s + p = t + err exactly
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
     s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
   }
-  PDCS_DEV double get() const { return (double)s - (double)comp; }
+  PDCS_DEV double get() const { return f64_of_f32(s) + f64_of_f32(c); }
 };
+
+// FP32 (hi, lo) split of an FP64 value for the gathered-vector shadow.
+PDCS_DEV float2 split_ff(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
 
 // Where a row's value goes: by default y[row]; a caller may pass a functor
 // with the same interface that also applies an elementwise update to the
@@ -82,16 +107,17 @@ PDCS_DEV double group_sum(double v) {
   return v;
 }
 
-template <typename T, int G, typename Out>
+template <typename V, int G, typename Out>
 PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
-                              const int32_t* __restrict__ ci, const T* __restrict__ vv,
-                              const T* __restrict__ x, const Out& out) {
+                              const int32_t* __restrict__ ci, const V* __restrict__ vv,
+                              const typename SpmvX<V>::type* __restrict__ x, const Out& out) {
+  using X = typename SpmvX<V>::type;
   const int gid = threadIdx.x / G, lane = threadIdx.x % G, ng = kSpmvThreads / G;
   // every group runs the same number of trips so the shuffles stay converged
   const int64_t trips = (t.b - t.a + ng - 1) / ng;
   for (int64_t q = 0; q < trips; ++q) {
     const int64_t row = t.a + gid + q * ng;
-    Acc<T> acc;
+    Acc<V> acc;
     typename Out::Pre pr{};
     if (lane == 0 && row < t.b) pr = out.pre(row);
     if (row < t.b) {
@@ -100,7 +126,8 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
       int64_t k = s + lane;
       for (; k + (U - 1) * G < e; k += U * G) {
         int32_t c[U];
-        T v[U], xv[U];
+        V v[U];
+        X xv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) c[u] = __ldg(ci + k + u * G);
 #pragma unroll
@@ -117,59 +144,61 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
   }
 }
 
-template <typename T, typename Out>
+template <typename V, typename Out>
 PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci, const T* __restrict__ vv,
-                        const T* __restrict__ x, const Out& out, double* __restrict__ partial,
-                        unsigned int* __restrict__ counters);
+                        const int32_t* __restrict__ ci, const V* __restrict__ vv,
+                        const typename SpmvX<V>::type* __restrict__ x, const Out& out,
+                        double* __restrict__ partial, unsigned int* __restrict__ counters);
 
 // y = A x over the task list, each row's value handed to `out` (StoreOut:
 // y[row]).  When `gate` is non-NULL and *gate == 0 the kernel does nothing
 // (used to skip products inside a captured graph).  partial / counters are the
 // scratch of kind-2 tasks (counters are left at zero).  tm, when non-NULL,
 // accumulates the launch's duration.
-template <typename T, typename Out>
+template <typename V, typename Out>
 __global__ void __launch_bounds__(kSpmvThreads)
 k_spmv(const SpmvTask* __restrict__ tasks, const int64_t* __restrict__ rp,
-       const int32_t* __restrict__ ci, const T* __restrict__ vv, const T* __restrict__ x,
-       Out out, double* __restrict__ partial, unsigned int* __restrict__ counters,
-       const int* __restrict__ gate, KTimer* tm) {
+       const int32_t* __restrict__ ci, const V* __restrict__ vv,
+       const typename SpmvX<V>::type* __restrict__ x, Out out, double* __restrict__ partial,
+       unsigned int* __restrict__ counters, const int* __restrict__ gate, KTimer* tm) {
   if (gate != nullptr && *gate == 0) return;
   ktimer_begin(tm);
-  spmv_task<T, Out>(tasks[blockIdx.x], rp, ci, vv, x, out, partial, counters);
+  spmv_task<V, Out>(tasks[blockIdx.x], rp, ci, vv, x, out, partial, counters);
   ktimer_end(tm);
 }
 
-template <typename T, typename Out>
+template <typename V, typename Out>
 PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci, const T* __restrict__ vv,
-                        const T* __restrict__ x, const Out& out, double* __restrict__ partial,
-                        unsigned int* __restrict__ counters) {
+                        const int32_t* __restrict__ ci, const V* __restrict__ vv,
+                        const typename SpmvX<V>::type* __restrict__ x, const Out& out,
+                        double* __restrict__ partial, unsigned int* __restrict__ counters) {
+  using X = typename SpmvX<V>::type;
   if (t.kind == 0) {
     const int64_t row = t.a + threadIdx.x;
     if (row < t.b) {
       const typename Out::Pre pr = out.pre(row);
       const int64_t s = rp[row], e = rp[row + 1];
-      Acc<T> acc;
+      Acc<V> acc;
       for (int64_t k = s; k < e; ++k) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
       out(row, acc.get(), pr);
     }
     return;
   }
   if (t.kind == 1) {
-    if (t.g == 4) spmv_group_rows<T, 4>(t, rp, ci, vv, x, out);
-    else if (t.g == 8) spmv_group_rows<T, 8>(t, rp, ci, vv, x, out);
-    else spmv_group_rows<T, 32>(t, rp, ci, vv, x, out);
+    if (t.g == 4) spmv_group_rows<V, 4>(t, rp, ci, vv, x, out);
+    else if (t.g == 8) spmv_group_rows<V, 8>(t, rp, ci, vv, x, out);
+    else spmv_group_rows<V, 32>(t, rp, ci, vv, x, out);
     return;
   }
   // kind 2: chunk of a long row
   __shared__ double sh[kSpmvThreads + 1];
-  Acc<T> acc;
+  Acc<V> acc;
   int64_t k = t.c + threadIdx.x;
   constexpr int U = kSpmvUnroll;
   for (; k + (U - 1) * kSpmvThreads < t.d; k += U * kSpmvThreads) {
     int32_t c[U];
-    T v[U], xv[U];
+    V v[U];
+    X xv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) c[u] = __ldg(ci + k + u * kSpmvThreads);
 #pragma unroll

@@ -22,7 +22,7 @@ import time
 
 import numpy as np
 
-from . import Mlp, Solver
+from . import Batch, Mlp, Solver
 
 
 class Standardiser:
@@ -82,6 +82,27 @@ def collect(factories, workers=8, **options):
     return np.array(params), np.array(sols), res
 
 
+def collect_batched(factories, chunk=512, **options):
+    """As collect, but every `chunk` instances are solved together in one
+    persistent launch of the batched engine (pdcs_setup_batch /
+    pdcs_solve_batch; FP64, each instance with its own step sizes, restarts
+    and termination)."""
+    params, sols, res = [], [], []
+    for c0 in range(0, len(factories), chunk):
+        probs = []
+        for f in factories[c0:c0 + chunk]:
+            prob, par = f()
+            probs.append(prob)
+            params.append(par)
+        with Batch(probs, **options) as b:
+            out = b.solve()
+        for r in out:
+            sols.append(np.concatenate([r["x"], r["y"]]))
+            res.append({k: r[k] for k in ("iters", "solve_time_s", "exit_code", "err_rel_p",
+                                          "err_rel_d", "err_rel_gap")})
+    return np.array(params), np.array(sols), res
+
+
 class WarmStart:
     """Network from instance parameters to (x, y), with the standardisers."""
 
@@ -137,6 +158,10 @@ def _main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--data-tol", type=float, default=1e-6)
+    ap.add_argument("--plain-data", action="store_true",
+                    help="generate the training data with one plain solve per instance")
+    ap.add_argument("--chunk", type=int, default=592,
+                    help="instances per batched launch of the data generation")
     args = ap.parse_args()
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
@@ -145,8 +170,11 @@ def _main():
     make = lambda split, i: workloads.portfolio_family_instance(fam, i, split_seed=split)  # noqa: E731
     opts = dict(rel_tol=args.data_tol, time_limit=600.0)
     t0 = time.perf_counter()
-    params, sols, res = collect([(lambda i=i: make(0, i)) for i in range(args.train)],
-                                workers=args.workers, **opts)
+    facs = [(lambda i=i: make(0, i)) for i in range(args.train)]
+    if args.plain_data:
+        params, sols, res = collect(facs, workers=args.workers, **opts)
+    else:
+        params, sols, res = collect_batched(facs, chunk=args.chunk, **opts)
     t_data = time.perf_counter() - t0
     t1 = time.perf_counter()
     ws = WarmStart(params, sols, n=args.n + 1)
@@ -170,10 +198,14 @@ def _main():
     wi = np.array([r["warm_iters"] for r in rows], float)
     cs = np.array([r["cold_s"] for r in rows])
     wsec = np.array([r["warm_s"] for r in rows])
+    data_ok = all(r["exit_code"] == 0 for r in res)
     print(json.dumps({
         "family": "portfolio n=%d k=%d limits=%d" % (args.n, args.k, args.limits),
         "train_instances": args.train, "test_instances": args.test,
         "data_seconds": t_data, "data_mean_iters": float(np.mean([r["iters"] for r in res])),
+        "data_all_reached_tol": bool(data_ok),
+        "data_generation": "one plain solve per instance" if args.plain_data else
+                           "batched engine, %d instances per launch" % args.chunk,
         "train_seconds": t_train, "train_steps": args.steps,
         "loss_first": losses[0], "loss_last": float(np.mean(losses[-20:])),
         "cold_iters_mean": ci.mean(), "warm_iters_mean": wi.mean(),

@@ -57,6 +57,11 @@ def test_default_options_follow_the_paper():
     o = P.default_options()
     assert o.rel_tol == 1e-6 and o.abs_tol == 1e-6 and o.time_limit == 1000.0
     assert o.use_preconditioner == 1 and o.method == 0 and o.use_adaptive_restart == 1
+    # Sec. 3.2.3 direct-API defaults
+    assert o.use_adaptive_step_size_weight == 1 and o.use_duality_gap_restart == 1
+    assert o.use_kkt_restart == 0 and o.kkt_restart_freq == 2000 and o.print_freq == 2000
+    assert o.eps_primal_infeasible_low_acc == 1e-12 and o.eps_dual_infeasible_low_acc == 1e-12
+    assert o.eps_primal_infeasible_high_acc == 1e-16 and o.eps_dual_infeasible_high_acc == 1e-16
 
 
 def _tiny():
@@ -83,6 +88,10 @@ def test_invalid_arguments_rejected_before_device_work(patch, msg):
 def test_invalid_option_rejected():
     with pytest.raises(P.PdcsError, match="precision"):
         P.Solver(_tiny(), precision=3)
+    with pytest.raises(P.PdcsError, match="kkt_restart_freq"):
+        P.Solver(_tiny(), use_kkt_restart=1, kkt_restart_freq=0)
+    with pytest.raises(P.PdcsError, match="thresholds"):
+        P.Solver(_tiny(), eps_dual_infeasible_high_acc=-1.0)
 
 
 def test_entry_point_build_reaches_the_library_build(monkeypatch):

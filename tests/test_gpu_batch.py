@@ -1,13 +1,25 @@
-"""Batched persistent solves (pdcs_setup_batch / pdcs_solve_batch): every
-problem of a mixed batch reaches the tolerance with the objective of its own
-single-problem solve, the outputs are deterministic, and an FP32-bulk batch
-of portfolios of uneven size agrees with FP64 single solves."""
+"""Batched persistent solves (pdcs_setup_batch / pdcs_solve_batch) against the
+FP64 oracle: every problem of a mixed batch is also solved by the oracle; the
+batched point must be a 1e-6 KKT point by the oracle's own measure (Sec.
+3.2.3, on the FP64 data), its objective must agree with the oracle's
+optimum within 1e-5 (relative), and x, y must lie near the oracle's
+solution (the distances are printed).  Outputs are deterministic.  An FP32
+batch (FP32 matrix values, FP64 vectors) is held to the same bar."""
 import numpy as np
 import pytest
 
+import oracle
 import workloads
+from oracle_checks import compare_with_oracle
 
 pytestmark = pytest.mark.gpu
+
+KKT_TOL = 1e-6
+OBJ_TOL = 1e-5
+# x, y of the returned 1e-6 KKT point against the oracle's (strictly
+# complementary or strictly convex instances: the solution is unique, and a
+# 1e-6 point lies within ~1e-6 * condition of it)
+DIST_TOL = 1e-3
 
 
 def _P():
@@ -26,22 +38,40 @@ def _mixed():
     return probs
 
 
-def test_mixed_batch_matches_single_solves_and_is_deterministic():
+def _check_against_oracle(probs, out, label):
+    for k, (prob, r) in enumerate(zip(probs, out)):
+        assert r["exit_code"] == 0, (label, k, r["status"])
+        ref = oracle.solve(oracle.problem_from_dict(prob), max_iter=200000, rel_tol=1e-9)
+        assert ref["exit_code"] == 0, (label, k)
+        e = compare_with_oracle(prob, r, ref)
+        print("%s %d: kkt %.2e obj %.2e x %.2e y %.2e" % (label, k, e["kkt"], e["obj"], e["x"], e["y"]))
+        assert e["kkt"] <= KKT_TOL * 1.01, (label, k, e)
+        assert e["obj"] <= OBJ_TOL, (label, k, e)
+        if prob["meta"].get("kind") != "logistic_l1":  # L1 problems may have many solutions
+            assert e["x"] <= DIST_TOL and e["y"] <= DIST_TOL, (label, k, e)
+
+
+def test_mixed_batch_matches_oracle_and_is_deterministic():
     P = _P()
     probs = _mixed()
     with P.Batch(probs, time_limit=120.0) as b:
         out = b.solve()
         out2 = b.solve()
-    for k, (prob, r) in enumerate(zip(probs, out)):
-        assert r["exit_code"] == 0, (k, r["status"])
-        assert max(r["err_rel_p"], r["err_rel_d"], r["err_rel_gap"]) <= 1e-6, k
-        g = P.solve(prob, time_limit=120.0)
-        assert abs(r["pobj"] - g["pobj"]) <= 1e-5 * (1.0 + abs(g["pobj"])), (k, r["pobj"], g["pobj"])
+    _check_against_oracle(probs, out, "fp64")
+    for k, prob in enumerate(probs):
         if "opt" in prob["meta"]:
-            assert abs(r["pobj"] - prob["meta"]["opt"]) <= 1e-5 * (1.0 + abs(prob["meta"]["opt"]))
+            assert abs(out[k]["pobj"] - prob["meta"]["opt"]) <= 1e-5 * (1.0 + abs(prob["meta"]["opt"]))
     for r, r2 in zip(out, out2):
         assert np.array_equal(r["x"], r2["x"]) and np.array_equal(r["y"], r2["y"])
         assert r["iters"] == r2["iters"]
+
+
+def test_fp32_batch_matches_oracle():
+    P = _P()
+    probs = _mixed()
+    with P.Batch(probs, precision="fp32", time_limit=120.0) as b:
+        out = b.solve()
+    _check_against_oracle(probs, out, "fp32")
 
 
 def test_fp32_batch_of_uneven_portfolios():
@@ -50,7 +80,19 @@ def test_fp32_batch_of_uneven_portfolios():
     with P.Batch(probs, precision="fp32", time_limit=120.0) as b:
         out = b.solve()
     assert all(r["exit_code"] == 0 for r in out), [r["status"] for r in out]
-    for k in (0, 17, 33, 47):
-        g = P.solve(probs[k], time_limit=120.0)
-        assert abs(out[k]["pobj"] - g["pobj"]) <= 1e-4 * (1.0 + abs(g["pobj"])), k
     assert all(r["finish_s"] > 0 for r in out)
+    _check_against_oracle([probs[k] for k in (0, 17, 33, 47)], [out[k] for k in (0, 17, 33, 47)],
+                          "fp32-portfolio")
+
+
+def test_batch_with_soc_blocks_beyond_the_register_tile():
+    """Portfolios whose rotated SOC block has more than 4096 elements are
+    projected by streaming the block from memory on every root-finding pass
+    (the register-tile path holds up to 4096); mixed with small ones in one
+    launch, against the oracle."""
+    P = _P()
+    probs = [workloads.portfolio_small_instance(n, seed) for n, seed in ((4300, 5), (200, 6))]
+    assert max(d for _, d in probs[0]["row_cones"]) > 4096
+    with P.Batch(probs, time_limit=300.0) as b:
+        out = b.solve()
+    _check_against_oracle(probs, out, "big-soc")

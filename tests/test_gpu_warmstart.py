@@ -1,9 +1,12 @@
-"""Learned warm start on a small parameterised portfolio family: solutions
-from the plain solver train the network; held-out instances are solved from
-its prediction unless pdcs_kkt rates the prediction worse than the cold start.
-Checks: every solve reaches 1e-6, the start rule follows the two KKT errors,
-the fallback keeps the iteration count within 10 % of the cold start's on
-average, and the measured gain is printed."""
+"""Learned warm start on a small parameterised portfolio family (n = 300
+assets): 512 training instances are solved by the batched engine, the
+network learns (mu, gamma) -> (x, y), and 16 held-out instances are solved
+from its prediction unless pdcs_kkt rates the prediction worse than the cold
+start (the KKT-judged fallback).  Checks: every solve reaches 1e-6, the start
+rule follows the two KKT errors, the prediction is used on most instances,
+and the learned start saves at least 10 % of the iterations on average; the
+wall time to 1e-6 of both arms (the warm arm including the prediction and the
+two KKT evaluations) is printed."""
 import numpy as np
 import pytest
 
@@ -12,7 +15,7 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 
-def test_warm_start_pipeline_on_a_small_family():
+def test_warm_start_gains_on_a_small_family():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -21,14 +24,14 @@ def test_warm_start_pipeline_on_a_small_family():
 
     fam = workloads.portfolio_family(n=300, k=15, n_limits=3, seed=77)
     make = lambda split, i: workloads.portfolio_family_instance(fam, i, split_seed=split)  # noqa: E731
-    params, sols, res = W.collect([(lambda i=i: make(0, i)) for i in range(96)], workers=8,
-                                  rel_tol=1e-6, time_limit=60.0)
+    params, sols, res = W.collect_batched([(lambda i=i: make(0, i)) for i in range(512)],
+                                          rel_tol=1e-6, time_limit=60.0)
     assert all(r["exit_code"] == 0 for r in res)
     ws = W.WarmStart(params, sols, n=301, hidden=256, n_hidden=3, batch=64, lr=1e-3)
-    losses = ws.fit(400)
+    losses = ws.fit(1500)
     assert np.mean(losses[-20:]) < 0.5 * losses[0]
-    cold, warm, used = [], [], 0
-    for i in range(8):
+    cold, warm, cold_s, warm_s, used = [], [], [], [], 0
+    for i in range(16):
         prob, p = make(1, i)
         with P.Solver(prob, rel_tol=1e-6, time_limit=60.0) as s:
             c = s.solve()
@@ -37,7 +40,12 @@ def test_warm_start_pipeline_on_a_small_family():
         assert w["warm"] == (w["kkt_pred"] <= w["kkt_cold"])
         cold.append(c["iters"])
         warm.append(w["iters"])
+        cold_s.append(c["solve_time_s"])
+        warm_s.append(w["wall_s"])
         used += int(w["warm"])
     ratio = np.mean(warm) / np.mean(cold)
-    print("warm / cold iterations: %.3f (prediction used %d of %d)" % (ratio, used, len(warm)))
-    assert ratio <= 1.10
+    print("warm / cold iterations %.3f, wall %.6f s / %.6f s (ratio %.3f), prediction used %d of %d"
+          % (ratio, np.mean(warm_s), np.mean(cold_s), np.mean(warm_s) / np.mean(cold_s), used,
+             len(warm)))
+    assert used >= 12
+    assert ratio <= 0.90

@@ -330,3 +330,23 @@ def test_option_modes_reach_planted_optimum(opts):
     if opts.get("use_kkt_restart") and opts.get("use_duality_gap_restart", True):
         kkt_only = [r for r in checks if r["iter"] % 64 != 0]
         assert kkt_only and all(r["fallback"] == 1 for r in kkt_only)
+
+
+def test_continuing_from_a_recorded_state_reproduces_the_run():
+    """init_state restarts the loop from a recorded state: the continuation
+    must equal the uninterrupted run bit for bit (same trace, same iterate)."""
+    p = workloads.tiny_conic(seed=4, m_nonneg=10, soc_rows=(4,), nb=20, soc_cols=(3,), density=0.3)
+    prob = oracle.problem_from_dict(p)
+    states = {70: None, 150: None}
+    tr = []
+    oracle.solve(prob, trace=tr, states=states, max_iter=150, check_freq=16)
+    tr2 = []
+    states2 = {150: None}
+    oracle.solve(prob, trace=tr2, states=states2, max_iter=150, check_freq=16,
+                 init_state=states[70])
+    # (the infeasibility record needs the previous check's candidate, which a
+    # continuation does not have)
+    strip = lambda rows: [{k: v for k, v in r.items() if k != "infeas"} for r in rows]  # noqa: E731
+    assert strip(tr2) == strip(tr[70:])
+    assert np.array_equal(states2[150]["x"], states[150]["x"])
+    assert np.array_equal(states2[150]["y"], states[150]["y"])

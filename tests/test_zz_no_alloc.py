@@ -88,3 +88,33 @@ def test_noalloc_product_small_matrix_by_definition():
     got = y.cpu().numpy()
     scale = 1.0 + sp.csr_matrix((np.abs(val), col_idx, row_ptr), shape=(len(lens), n)) @ np.abs(x)
     assert np.max(np.abs(got - ref) / scale) <= 1e-13
+
+
+def test_noalloc_product_refuses_a_capturing_stream():
+    """The call synchronises its stream to read the size check, so it must not
+    run inside a stream capture: it refuses, and the capture stays valid."""
+    P, torch = _env()
+    rp = torch.tensor([0, 1, 2], dtype=torch.int64, device="cuda")
+    ci = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
+    val = torch.tensor([2.0, 3.0], dtype=torch.float64, device="cuda")
+    x = torch.tensor([1.0, 1.0], dtype=torch.float64, device="cuda")
+    y = torch.zeros(2, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            rc = P.lib().pdcs_spmv_noalloc(2, 2, rp.data_ptr(), ci.data_ptr(), val.data_ptr(),
+                                           x.data_ptr(), y.data_ptr(), s.cuda_stream)
+            y.add_(1.0)  # the capture still records work after the refusal
+        finally:
+            g.capture_end()
+    assert rc == -1 and b"captured" in P.lib().pdcs_last_error()
+    g.replay()
+    torch.cuda.synchronize()
+    assert y.tolist() == [1.0, 1.0]
+    # and outside the capture the same call works
+    P.spmv_noalloc(rp, ci, val, x, y)
+    torch.cuda.synchronize()
+    assert y.tolist() == [2.0, 3.0]

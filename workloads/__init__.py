@@ -69,17 +69,31 @@ def _boundary_soc_pair(rng, dim):
     return s, y
 
 
+def _boundary_exp_pair(rng):
+    """Complementary boundary pair of the exponential cone and its dual:
+    p = a (r, 1, e^r) on the boundary of K_exp, q = b (-e^r, e^r (r - 1), 1) on
+    the boundary of K_exp^* (-q_0 exp(q_1 / q_0) = b e = e q_2), p^T q = 0."""
+    r = rng.uniform(-1.0, 1.0)
+    a, b = rng.uniform(0.5, 1.5, size=2)
+    er = np.exp(r)
+    return a * np.array([r, 1.0, er]), b * np.array([-er, er * (r - 1.0), 1.0])
+
+
 def tiny_conic(seed=20260101, m_nonneg=60, soc_rows=(10, 10, 10, 10), nb=150,
-               soc_cols=(10, 10, 10, 10, 10), density=0.05):
+               soc_cols=(10, 10, 10, 10, 10), density=0.05, exp_rows=0, dexp_rows=0,
+               exp_cols=0, dexp_cols=0):
     """Random conic program with a planted primal-dual optimum.
 
     G has N(0,1) entries with the given density.  Rows: m_nonneg nonnegative
-    rows then SOC blocks; columns: nb box [0, inf) then SOC blocks.  A strictly
-    complementary (x*, s*, y*, lambda*) is drawn and h = G x* - s*,
-    c = G^T y* + lambda*, so the optimal value is c^T x* = h^T y*."""
+    rows, SOC blocks, then exp_rows exponential and dexp_rows dual-exponential
+    blocks; columns: nb box [0, inf), SOC blocks, then exp_cols exponential and
+    dexp_cols dual-exponential blocks.  A strictly complementary
+    (x*, s*, y*, lambda*) is drawn (boundary pairs for the cone blocks) and
+    h = G x* - s*, c = G^T y* + lambda*, so the optimal value is
+    c^T x* = h^T y*."""
     rng = np.random.default_rng(seed)
-    m = m_nonneg + sum(soc_rows)
-    n = nb + sum(soc_cols)
+    m = m_nonneg + sum(soc_rows) + 3 * (exp_rows + dexp_rows)
+    n = nb + sum(soc_cols) + 3 * (exp_cols + dexp_cols)
     G = _sparse_normal(rng, m, n, density)
     s = np.zeros(m)
     y = np.zeros(m)
@@ -92,6 +106,11 @@ def tiny_conic(seed=20260101, m_nonneg=60, soc_rows=(10, 10, 10, 10), nb=150,
     for dim in soc_rows:
         s[off:off + dim], y[off:off + dim] = _boundary_soc_pair(rng, dim)
         off += dim
+    for b in range(exp_rows + dexp_rows):
+        p_, q_ = _boundary_exp_pair(rng)
+        # exp rows: s in K_exp, y in K_exp^*; dual-exp rows the other way round
+        s[off:off + 3], y[off:off + 3] = (p_, q_) if b < exp_rows else (q_, p_)
+        off += 3
     x = np.zeros(n)
     lam = np.zeros(n)
     halfc = nb // 2
@@ -103,10 +122,16 @@ def tiny_conic(seed=20260101, m_nonneg=60, soc_rows=(10, 10, 10, 10), nb=150,
     for dim in soc_cols:
         x[off:off + dim], lam[off:off + dim] = _boundary_soc_pair(rng, dim)
         off += dim
+    for b in range(exp_cols + dexp_cols):
+        p_, q_ = _boundary_exp_pair(rng)
+        x[off:off + 3], lam[off:off + 3] = (p_, q_) if b < exp_cols else (q_, p_)
+        off += 3
     h = G @ x - s
     c = G.T @ y + lam
-    row_cones = [(NONNEG, m_nonneg)] + [(SOC, d) for d in soc_rows]
-    col_cones = [(SOC, d) for d in soc_cols]
+    row_cones = ([(NONNEG, m_nonneg)] + [(SOC, d) for d in soc_rows] +
+                 [(EXP, 3)] * exp_rows + [(DUAL_EXP, 3)] * dexp_rows)
+    col_cones = ([(SOC, d) for d in soc_cols] + [(EXP, 3)] * exp_cols +
+                 [(DUAL_EXP, 3)] * dexp_cols)
     meta = dict(kind="tiny_conic", seed=seed, x_star=x, y_star=y, s_star=s, lam_star=lam,
                 opt=float(c @ x))
     return _pack(G, h, c, nb, np.zeros(nb), np.full(nb, np.inf), row_cones, col_cones, meta)
