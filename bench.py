@@ -69,6 +69,13 @@ def _args():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--oracle-procs", type=int, default=8,
                     help="processes of the all-cores oracle leg (independent copies)")
+    ap.add_argument("--overlap", type=int, default=0, choices=[0, 1],
+                    help="programmatic dependent launches in the captured loops (option "
+                         "overlap_launches)")
+    ap.add_argument("--ab", action="store_true",
+                    help="instead of the bench line: time to 1e-6 on the workload for the "
+                         "restart-check period 64 against the paper's 2000, and for the "
+                         "bisection tolerance of Algorithm 3 (1e-6 against 1e-3)")
     return ap.parse_args()
 
 
@@ -362,7 +369,7 @@ def run_ours(args):
     # of a step); the per-kernel times and the roofline come from a second,
     # profiled window over the same number of steps right after it
     opts = dict(precision=args.precision, check_freq=CHECK_FREQ, profile=0, time_limit=3600.0,
-                eager=int(args.eager))
+                eager=int(args.eager), overlap_launches=args.overlap)
 
     def barrier():
         torch.cuda.synchronize()
@@ -550,6 +557,23 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ab(args):
+    """A/B of method options on the workload (one JSON line, not the bench
+    contract line): time and iterations to 1e-6 relative KKT error."""
+    import paper_2603_15504_b300 as P
+    prob, desc = _workload(args, 0)
+    arms = [("check_freq=64 (default)", dict(check_freq=64)),
+            ("check_freq=2000 (paper default)", dict(check_freq=2000)),
+            ("check_freq=64, bisect_rel_tol=1e-3", dict(check_freq=64, bisect_rel_tol=1e-3))]
+    out = []
+    for name, o in arms:
+        opts = dict(precision=args.precision, profile=0, time_limit=3600.0, **o)
+        _, t = _tts(P, prob, opts, args.tts_cap)
+        t["arm"] = name
+        out.append(t)
+    print(json.dumps({"ab": out, "workload": desc, "cap_s": args.tts_cap}))
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -595,5 +619,7 @@ if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.ab:
+        run_ab(a)
     else:
         run_ours(a)

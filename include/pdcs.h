@@ -120,7 +120,11 @@ typedef struct {
                                 KKT_omega (Sec. 2.3).  Checks with neither
                                 criterion test termination and restart
                                 condition 3 only */
-  int32_t pad0;
+  int32_t overlap_launches;  /* 0; 1: kernels of the captured loop bodies use
+                                programmatic dependent launch (each may be
+                                scheduled during its predecessor's last wave and
+                                waits for it on the device).  Measured slower on
+                                the portfolio (1955 against 2069 iterations/s) */
   int64_t kkt_restart_freq;  /* 2000 */
   int64_t print_freq;        /* 2000: with verbose, a line whenever the iteration
                                 count passes a multiple (checked per period) */
@@ -247,10 +251,13 @@ int pdcs_get_trace(pdcs_handle* handle, double* out, int64_t cap, int64_t* count
  * pdcs_resume call (requires options.profile = 1; zero otherwise).  Each launch
  * is timed from the start of its first CTA to the end of its last CTA with the
  * GPU's global nanosecond timer.  bytes_* are the algorithmic bytes of one
- * launch: values and column indices once, row pointers once, the gathered
- * vector and the result vector once each; when the dual step runs in the
- * epilogue of G xhat (problems averaging 16 or more nonzeros per row), g_bytes
- * adds its per-row reads and writes. */
+ * launch: values once (8 bytes, 4 in FP32 mode), column indices once except
+ * in the chunks of long rows (over 4096 nonzeros) that lie wholly inside the
+ * row's column run (its longest stretch of at least 16 nonzeros with
+ * consecutive columns, whose columns the kernel computes), row pointers once,
+ * the gathered vector and the result vector once each; when the dual step
+ * runs in the epilogue of G xhat (problems averaging 16 or more nonzeros per
+ * row), g_bytes adds its per-row reads and writes. */
 typedef struct {
   int64_t g_launches;    /* G xhat products (one per attempt) */
   double g_seconds;

@@ -37,7 +37,7 @@ class PdcsOptions(ctypes.Structure):
                 ("trace_capacity", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("eager", ctypes.c_int32), ("use_adaptive_step_size_weight", ctypes.c_int32),
                 ("use_duality_gap_restart", ctypes.c_int32), ("use_kkt_restart", ctypes.c_int32),
-                ("pad0", ctypes.c_int32), ("kkt_restart_freq", ctypes.c_int64),
+                ("overlap_launches", ctypes.c_int32), ("kkt_restart_freq", ctypes.c_int64),
                 ("print_freq", ctypes.c_int64),
                 ("eps_primal_infeasible_low_acc", ctypes.c_double),
                 ("eps_dual_infeasible_low_acc", ctypes.c_double),

@@ -7,6 +7,17 @@
 
 namespace pdcs {
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialization attribute may be scheduled before its predecessor in
+// the stream has finished: pdl_wait() blocks until the predecessor grid has
+// completed and its memory operations are visible (a no-op for an ordinary
+// launch), so every kernel calls it before reading anything a predecessor
+// wrote; pdl_trigger() allows the successor's CTAs to be scheduled once every
+// CTA of this grid has called it (or exited), which hides the launch gap
+// behind this grid's last wave.
+PDCS_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+PDCS_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 PDCS_DEV double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -123,6 +123,8 @@ __global__ void __launch_bounds__(kEwThreads) k_primal(Prob<T> p, const Ctl* __r
                                                        const T* __restrict__ x,
                                                        const T* __restrict__ gty,
                                                        T* __restrict__ xh, float2* __restrict__ sx) {
+  pdl_wait();
+  pdl_trigger();
   if (!ctl->g_attempt) return;
   ktimer_begin(tslot(p.tm, TM_PRIMAL));
   const double tau = ctl->eta / ctl->omega;
@@ -150,6 +152,7 @@ PDCS_DEV void dual_elem(const Prob<T>& p, double sigma, const T* __restrict__ y,
 // of yhat and of u can run as one launch.  sigma = eta omega of the attempt.
 template <typename T>
 struct DualOut {
+  static constexpr int kMinBlocks = 6;  // resident CTAs per SM of the product (40 registers)
   Prob<T> p;
   const Ctl* ctl;
   const T* y;
@@ -183,6 +186,8 @@ __global__ void __launch_bounds__(kEwThreads) k_dual(Prob<T> p, const Ctl* __res
                                                      const T* __restrict__ gxh,
                                                      const T* __restrict__ gx,
                                                      T* __restrict__ yh, double* __restrict__ res) {
+  pdl_wait();
+  pdl_trigger();
   if (!ctl->g_attempt) return;
   ktimer_begin(tslot(p.tm, TM_DUAL));
   const double sigma = ctl->eta * ctl->omega;
@@ -238,6 +243,8 @@ __global__ void __launch_bounds__(kEwThreads) k_step(Prob<T> p, Ctl* __restrict_
                                                      const T* __restrict__ gx,
                                                      double* __restrict__ part,
                                                      float2* __restrict__ sy) {
+  pdl_wait();
+  pdl_trigger();
   if (!ctl->g_attempt) return;
   ktimer_begin(tslot(p.tm, TM_STEP));
   __shared__ double sh[3 * kEwThreads + 3];
@@ -300,6 +307,8 @@ __global__ void __launch_bounds__(128, 6) k_cone_exp(B* v0, B* v1, const int64_t
                            int dual, int flip1,
                            const int* __restrict__ gate0, const int* __restrict__ gate1,
                            KTimer* tm) {
+  pdl_wait();
+  pdl_trigger();
   B* v = blockIdx.y == 0 ? v0 : v1;
   if (flip1 && blockIdx.y == 1) {
     inv = 1 - inv;
@@ -334,6 +343,8 @@ __global__ void __launch_bounds__(NT) k_cone_soc(B* v0, B* v1, const int64_t* __
                                                  const double* __restrict__ d, int inv, int flip1,
                                                  const int* __restrict__ gate0,
                                                  const int* __restrict__ gate1, KTimer* tm) {
+  pdl_wait();
+  pdl_trigger();
   B* v = blockIdx.y == 0 ? v0 : v1;
   if (flip1 && blockIdx.y == 1) inv = 1 - inv;
   if (!gate_on(gate0) && (gridDim.y == 1 || !gate_on(gate1))) return;  // whole launch idle
@@ -387,6 +398,8 @@ template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_res_prep(Prob<T> p, const int* __restrict__ gate,
                                                          PointRef<T> a, PointRef<T> b,
                                                          TmpRef ta, TmpRef tb) {
+  pdl_wait();
+  pdl_trigger();
   if (gate != nullptr && *gate == 0) return;
   ktimer_begin(tslot(p.tm, TM_RES_PREP));
   const PointRef<T> pt = blockIdx.y == 0 ? a : b;
@@ -519,6 +532,8 @@ __global__ void __launch_bounds__(kEwThreads) k_point_stats(Prob<T> p, Ctl* __re
                                                             PointRef<T> pt, const T* __restrict__ x0,
                                                             const T* __restrict__ y0, TmpRef tr,
                                                             double* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   if (gate != nullptr && *gate == 0) return;
   KTimer* tmr = tslot(p.tm, slot == 0 ? TM_STATS_ATTEMPT : TM_STATS_CHECK);
   ktimer_begin(tmr);
@@ -629,6 +644,8 @@ __global__ void __launch_bounds__(kEwThreads) k_halpern(
     const T* __restrict__ y0, const T* __restrict__ gx0, const T* __restrict__ gty0,
     double* __restrict__ xs, double* __restrict__ ys, double* __restrict__ trace,
     cudaGraphConditionalHandle h, int use_cond) {
+  pdl_wait();
+  pdl_trigger();
   if (!ctl->g_accept) {
     // rejected attempt: only the loop decision
     if (blockIdx.x == 0 && threadIdx.x == 0) loop_ctl(*ctl, h, use_cond);
@@ -649,6 +666,8 @@ __global__ void __launch_bounds__(kEwThreads) k_halpern(
 }
 
 __global__ void k_period_begin(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
+  pdl_wait();
+  pdl_trigger();
   const int go = ctl_period_begin(*ctl);
   if (use_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
@@ -660,6 +679,8 @@ __global__ void __launch_bounds__(kEwThreads) k_average(int64_t n, int64_t m, co
                                                         const double* __restrict__ ys,
                                                         T* __restrict__ xb, T* __restrict__ yb,
                                                         KTimer* tm) {
+  pdl_wait();
+  pdl_trigger();
   if (!ctl->g_check) return;
   ktimer_begin(tm);
   const double w = ctl->wsum;
@@ -708,6 +729,8 @@ PDCS_DEV int ctl_bisect_init(Ctl& cl) {
 }
 
 __global__ void k_bisect_init(Ctl* ctl, cudaGraphConditionalHandle h, int use_cond) {
+  pdl_wait();
+  pdl_trigger();
   const int any = ctl_bisect_init(*ctl);
   if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
@@ -761,6 +784,8 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_prep(Prob<T> p, const Ctl*
                                                            double* __restrict__ py0,
                                                            double* __restrict__ px1,
                                                            double* __restrict__ py1) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.y;
   const Bisect& bs = ctl->bs[c];
   if (!ctl->bs[0].active && !ctl->bs[1].active) return;  // whole launch idle
@@ -840,6 +865,8 @@ __global__ void __launch_bounds__(kEwThreads) k_probe_reduce(Prob<T> p, Ctl* __r
                                                              double* __restrict__ part,
                                                              cudaGraphConditionalHandle h,
                                                              int use_cond) {
+  pdl_wait();
+  pdl_trigger();
   const int c = blockIdx.y;
   const Bisect& bs = ctl->bs[c];
   ktimer_begin(tslot(p.tm, TM_PROBE_REDUCE));
@@ -979,7 +1006,9 @@ PDCS_DEV void ctl_check_decide(Ctl& c, double* trace) {
   }
 }
 
-__global__ void k_check_decide(Ctl* ctl, double* trace) { ctl_check_decide(*ctl, trace); }
+__global__ void k_check_decide(Ctl* ctl, double* trace) {
+  pdl_wait();
+  pdl_trigger(); ctl_check_decide(*ctl, trace); }
 
 // Keep the chosen candidate (the returned point) and, on restart, make it the
 // new anchor and current iterate and clear the average.
@@ -991,6 +1020,8 @@ __global__ void __launch_bounds__(kEwThreads) k_cand_copy(int64_t n, int64_t m, 
                                                           T* gxc, T* gtyc, T* x0, T* y0, T* x, T* y,
                                                           double* xs, double* ys, float2* sx,
                                                           float2* sy, KTimer* tm) {
+  pdl_wait();
+  pdl_trigger();
   if (!ctl->g_check) return;
   ktimer_begin(tm);
   const PointRef<T> s = ctl->cand ? zb : z;
@@ -1020,6 +1051,8 @@ template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_copy_products(int64_t n, int64_t m, const int* __restrict__ gate,
                                                               const T* gx0, const T* gty0, T* gx, T* gty,
                                                               KTimer* tm) {
+  pdl_wait();
+  pdl_trigger();
   if (!*gate) return;
   ktimer_begin(tm);
   PDCS_GRID_LOOP(j, n) gty[j] = gty0[j];
@@ -1037,7 +1070,9 @@ PDCS_DEV void ctl_check_end(Ctl& c) {
   c.g_attempt = c.status == kRunning;
 }
 
-__global__ void k_check_end(Ctl* ctl) { ctl_check_end(*ctl); }
+__global__ void k_check_end(Ctl* ctl) {
+  pdl_wait();
+  pdl_trigger(); ctl_check_end(*ctl); }
 
 // ------------------------------------------------ infeasibility statistics
 // Sec. 3.2.3 infeasibility ratios for the change of restart candidate cidx
@@ -1053,6 +1088,8 @@ template <typename T>
 __global__ void __launch_bounds__(kEwThreads) k_infeas_prep(Prob<T> p, const Ctl* __restrict__ ctl,
                                                             PointRef<T> z, PointRef<T> zb,
                                                             PointRef<T> pc, TmpRef ta, TmpRef tb) {
+  pdl_wait();
+  pdl_trigger();
   const int cidx = blockIdx.y;
   if (!ctl->infeas_gate[cidx]) return;
   const PointRef<T> a = cidx == 0 ? z : zb;
@@ -1092,6 +1129,8 @@ __global__ void __launch_bounds__(kEwThreads) k_infeas_reduce(Prob<T> p, Ctl* __
                                                               PointRef<T> z, PointRef<T> zb,
                                                               PointRef<T> pc, TmpRef ta, TmpRef tb,
                                                               double* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
   if (!ctl->infeas_gate[0] && !ctl->infeas_gate[1]) return;  // uniform over the grid
   const int cidx = blockIdx.y;
   __shared__ double sh[kInfM * kEwThreads + kInfM];
@@ -1465,6 +1504,8 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
     const int64_t* __restrict__ offs, int nblocks, const double* __restrict__ bq,
     const double* __restrict__ bqi, const int* __restrict__ gate0,
     const int* __restrict__ gate1, double* __restrict__ part, GridSync gs, KTimer* tm) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int K = 3 * NV;
   constexpr int RC = kSgSlots;
   constexpr int PS = 3 * kSgProbes;  // probe sums per vector

@@ -101,7 +101,24 @@ struct SpmvPlan {
   int ntasks = 0;
   double* partial = nullptr;
   unsigned int* counters = nullptr;
+  int64_t run_nnz = 0;      // nonzeros of chunks inside column runs (no index read)
 };
+
+// Shortest stretch of consecutive column indices worth a run descriptor.
+constexpr int64_t kMinRun = 16;
+
+// Longest stretch [a, b) of nonzeros in [s, e) with consecutive columns.
+static void longest_run(const std::vector<int32_t>& ci, int64_t s, int64_t e, int64_t& a,
+                        int64_t& b) {
+  a = b = s;
+  int64_t k = s;
+  while (k < e) {
+    int64_t j = k + 1;
+    while (j < e && ci[j] == ci[j - 1] + 1) ++j;
+    if (j - k > b - a) { a = k; b = j; }
+    k = j;
+  }
+}
 
 // Bin rows into SpMV tasks (see spmv.cuh): long rows (> 4096 nonzeros) split
 // into kChunk-nonzero chunks; every other run of consecutive rows becomes a
@@ -110,15 +127,24 @@ struct SpmvPlan {
 // nonzeros, a warp beyond).  Rows of different lengths share tasks, so
 // interleaved short and medium rows (the three rows of an exponential cone)
 // do not fragment the plan into one-row tasks.
-static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream_t st, int small_g) {
+//
+// Column runs (spmv.cuh): each long row's longest stretch of at least kMinRun
+// nonzeros with consecutive columns is recorded in its chunks (ci: the column
+// indices on the host); chunks wholly inside it read no index.
+static SpmvPlan build_plan(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                           Arena& ar, cudaStream_t st, int small_g) {
   const int64_t m = (int64_t)rp.size() - 1;
   std::vector<SpmvTask> tasks;
+  int64_t run_nnz = 0;
   int64_t npart = 0;
   int ncnt = 0;
   int64_t r = 0;
   while (r < m) {
     if (rp[r + 1] - rp[r] > 4096) {
       const int64_t s = rp[r], e = rp[r + 1];
+      int64_t ra, rb;
+      longest_run(ci, s, e, ra, rb);
+      if (rb - ra < kMinRun) ra = rb = 0;
       const int64_t nch = (e - s + kChunk - 1) / kChunk;
       for (int64_t k = 0; k < nch; ++k) {
         SpmvTask t{};
@@ -130,6 +156,10 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
         t.c = s + k * kChunk;
         t.d = std::min(e, s + (k + 1) * kChunk);
         t.pbase = npart;
+        t.ra = ra;
+        t.rb = rb;
+        t.col0 = rb > ra ? ci[ra] : 0;
+        if (rb > ra && ra <= t.c && t.d <= rb) run_nnz += t.d - t.c;
         tasks.push_back(t);
       }
       npart += nch;
@@ -170,6 +200,7 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
     p.tasks = ar.alloc<SpmvTask>(p.ntasks);
     CK(cudaMemcpyAsync(p.tasks, tasks.data(), tasks.size() * sizeof(SpmvTask), cudaMemcpyHostToDevice, st));
   }
+  p.run_nnz = run_nnz;
   p.partial = ar.alloc<double>(std::max<int64_t>(npart, 1));
   p.counters = ar.alloc<unsigned int>(std::max(ncnt, 1));
   CK(cudaMemsetAsync(p.counters, 0, sizeof(unsigned int) * std::max(ncnt, 1), st));
@@ -177,15 +208,35 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, Arena& ar, cudaStream
   return p;
 }
 
+// Launch with, when pdl is set, the programmatic stream-serialization
+// attribute (programmatic dependent launch: the kernel may be scheduled while
+// its predecessor's last wave runs and waits in pdl_wait()).
+template <typename... KArgs, typename... Args>
+static void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, bool pdl,
+                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  CK(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
+
 // V: matrix value type; x: the gathered vector (FP64, or its FP32 (hi, lo)
 // shadow for FP32 values).
 template <typename V, typename Out>
 static void launch_spmv_out(const SpmvPlan& p, const int64_t* rp, const int32_t* ci, const V* vv,
                             const typename SpmvX<V>::type* x, const Out& out, const int* gate,
-                            cudaStream_t st, KTimer* tm = nullptr) {
+                            cudaStream_t st, KTimer* tm = nullptr, bool pdl = false) {
   if (p.ntasks == 0) return;
-  k_spmv<V, Out><<<p.ntasks, kSpmvThreads, 0, st>>>(p.tasks, rp, ci, vv, x, out, p.partial,
-                                                    p.counters, gate, tm);
+  launch_k(k_spmv<V, Out>, dim3(p.ntasks), dim3(kSpmvThreads), st, pdl,
+           (const SpmvTask*)p.tasks, rp, ci, vv, x, out, p.partial,
+           p.counters, gate, tm);
 }
 
 template <typename V>
@@ -199,6 +250,8 @@ static void launch_spmv(const SpmvPlan& p, const int64_t* rp, const int32_t* ci,
 // products).
 __global__ void k_split(const double* __restrict__ v, float2* __restrict__ out, int64_t n,
                         const int* __restrict__ gate) {
+  pdl_wait();
+  pdl_trigger();
   if (gate != nullptr && *gate == 0) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -257,22 +310,26 @@ static const int kSocTierMax[3] = {128, 4096, 8192};
 // 1 - inv).  Zero / nonnegative blocks are handled by the producing kernels.
 template <typename B>
 static void project(const ConeTable& t, B* v0, B* v1, int nvec, const double* d, int inv, int dual,
-                    const int* g0, const int* g1, cudaStream_t st, bool flip1 = false) {
+                    const int* g0, const int* g1, cudaStream_t st, bool flip1 = false,
+                    bool pdl = false) {
   KTimer* tm = t.timers;
   const int fl = flip1 ? 1 : 0;
   if (t.nexp > 0) {
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((t.nexp + 127) / 128, 148 * 8)), nvec);
-    k_cone_exp<B><<<grid, 128, 0, st>>>(v0, v1, t.exp_s, t.exp_isd, t.nexp, d,
-                                         d ? t.dinv : nullptr, inv, dual, fl, g0, g1,
-                                         tm ? tm + TM_EXP : nullptr);
+    launch_k(k_cone_exp<B>, grid, dim3(128), st, pdl, v0, v1, (const int64_t*)t.exp_s,
+             (const uint8_t*)t.exp_isd, t.nexp, d, (const double*)(d ? t.dinv : nullptr), inv, dual,
+             fl, g0, g1, tm ? tm + TM_EXP : (KTimer*)nullptr);
   }
   KTimer* tsc = tm ? tm + TM_SOC_CTA : nullptr;
   if (t.nsoc[0] > 0)
-    k_cone_soc<B, 32, 4><<<dim3((unsigned)t.nsoc[0], nvec), 32, 0, st>>>(v0, v1, t.soc_s[0], t.soc_d[0], d, inv, fl, g0, g1, tsc);
+    launch_k(k_cone_soc<B, 32, 4>, dim3((unsigned)t.nsoc[0], nvec), dim3(32), st, pdl, v0, v1,
+             (const int64_t*)t.soc_s[0], (const int32_t*)t.soc_d[0], d, inv, fl, g0, g1, tsc);
   if (t.nsoc[1] > 0)
-    k_cone_soc<B, 256, 16><<<dim3((unsigned)t.nsoc[1], nvec), 256, 0, st>>>(v0, v1, t.soc_s[1], t.soc_d[1], d, inv, fl, g0, g1, tsc);
+    launch_k(k_cone_soc<B, 256, 16>, dim3((unsigned)t.nsoc[1], nvec), dim3(256), st, pdl, v0, v1,
+             (const int64_t*)t.soc_s[1], (const int32_t*)t.soc_d[1], d, inv, fl, g0, g1, tsc);
   if (t.nsoc[2] > 0)
-    k_cone_soc<B, 512, 16><<<dim3((unsigned)t.nsoc[2], nvec), 512, 0, st>>>(v0, v1, t.soc_s[2], t.soc_d[2], d, inv, fl, g0, g1, tsc);
+    launch_k(k_cone_soc<B, 512, 16>, dim3((unsigned)t.nsoc[2], nvec), dim3(512), st, pdl, v0, v1,
+             (const int64_t*)t.soc_s[2], (const int32_t*)t.soc_d[2], d, inv, fl, g0, g1, tsc);
   if (t.nbig > 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)t.big_grid);
@@ -390,6 +447,7 @@ struct Solver : SolverBase {
   cudaGraph_t graph = nullptr;
   int64_t trace_rows = 0;
   int use_cond = 1;  // 0 in eager mode (kernels launched from the host, no graphs)
+  bool pdl_ = false;  // programmatic dependent launches in the captured loop bodies
   // the dual step runs as the epilogue of G xhat when the rows are long
   // (16 nonzeros or more on average): there it costs the product nothing,
   // while on short rows the epilogue's registers cost the product occupancy
@@ -651,13 +709,20 @@ struct Solver : SolverBase {
     fill_table(rows, rsoc, rbig, rexp, rexpd, d1, m);
     fill_table(cols, csoc, cbig, cexp, cexpd, d2, n);
     const int small_g = sizeof(MV) == 8 ? 4 : 8;
-    planG = build_plan(hrp, ar, st, small_g);
-    planGT = build_plan(hrpT, ar, st, small_g);
+    {
+      // column indices on the host for the run detection of the plans
+      std::vector<int32_t> hci((size_t)nnz);
+      if (nnz > 0) CK(cudaMemcpy(hci.data(), ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+      planG = build_plan(hrp, hci, ar, st, small_g);
+      if (nnz > 0) CK(cudaMemcpy(hci.data(), ciT, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+      planGT = build_plan(hrpT, hci, ar, st, small_g);
+    }
     alloc_state();
     if (opt.eager) {
       use_cond = 0;
       count_eager();
     } else {
+      pdl_ = opt.overlap_launches != 0;
       capture();
     }
   }
@@ -910,12 +975,14 @@ struct Solver : SolverBase {
     std::memset(pr, 0, sizeof(*pr));
     // values + column indices once, row pointers once, the gathered vector
     // (FP64 or its 8-byte FP32 pair) and the result once
+    // (column indices only outside the chunks that lie in column runs)
     const double vb = (double)sizeof(MV);
-    pr->g_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(m + 1) + 8.0 * (double)(n + m);
+    auto idx_bytes = [&](const SpmvPlan& pl) { return 4.0 * (double)(nnz - pl.run_nnz); };
+    pr->g_bytes = (double)nnz * vb + idx_bytes(planG) + 8.0 * (double)(m + 1) + 8.0 * (double)(n + m);
     // the dual step in the product's epilogue: y, G x, h and the row kind
     // read, yhat written per row, G xhat - h on the cone rows
     if (dual_in_product) pr->g_bytes += (double)m * (4.0 * 8.0 + 1.0) + 8.0 * (double)cone_rows;
-    pr->gt_bytes = (double)nnz * (vb + 4.0) + 8.0 * (double)(n + 1) + 8.0 * (double)(n + m);
+    pr->gt_bytes = (double)nnz * vb + idx_bytes(planGT) + 8.0 * (double)(n + 1) + 8.0 * (double)(n + m);
     pr->nnz_flops = 2.0 * (double)nnz;
     pr->graph_launches = graph_launches;
     if (use_cond)
@@ -969,16 +1036,18 @@ struct Solver : SolverBase {
   // its FP32 shadow xs.  tr selects G^T.
   template <typename Out>
   void spmv_it_out(bool tr, const double* xv, const float2* xs, const Out& out, const int* gate,
-                   cudaStream_t s, KTimer* tmr = nullptr) {
+                   cudaStream_t s, KTimer* tmr = nullptr, bool pdl = false) {
     const SpmvPlan& pl = tr ? planGT : planG;
     if constexpr (kF32)
-      launch_spmv_out<float>(pl, tr ? rpT : rp, tr ? ciT : ci, tr ? vvT : vv, xs, out, gate, s, tmr);
+      launch_spmv_out<float>(pl, tr ? rpT : rp, tr ? ciT : ci, tr ? vvT : vv, xs, out, gate, s,
+                             tmr, pdl);
     else
-      launch_spmv_out<double>(pl, tr ? rpT : rp, tr ? ciT : ci, tr ? vvT : vv, xv, out, gate, s, tmr);
+      launch_spmv_out<double>(pl, tr ? rpT : rp, tr ? ciT : ci, tr ? vvT : vv, xv, out, gate, s,
+                              tmr, pdl);
   }
   void spmv_it(bool tr, const double* xv, const float2* xs, double* yv, const int* gate,
-               cudaStream_t s, KTimer* tmr = nullptr) {
-    spmv_it_out(tr, xv, xs, StoreOut<double>{yv}, gate, s, tmr);
+               cudaStream_t s, KTimer* tmr = nullptr, bool pdl = false) {
+    spmv_it_out(tr, xv, xs, StoreOut<double>{yv}, gate, s, tmr, pdl);
   }
   // Product with the FP64 values (statistics of the checks).
   void spmv64(bool tr, const double* xv, double* yv, const int* gate, cudaStream_t s,
@@ -990,42 +1059,44 @@ struct Solver : SolverBase {
   void rec_attempt(cudaStream_t s, cudaGraphConditionalHandle hA) {
     const Prob<T> p = prob();
     const int gn = ew_grid(n), gm = ew_grid(m), gmx = ew_grid(std::max(m, n));
-    k_primal<T><<<gn, kEwThreads, 0, s>>>(p, ctl, x, gty, xh, kF32 && !cols.any() ? sx : nullptr);
-    project<T>(cols, xh, xh, 1, d2, 1, 0, &ctl->g_attempt, nullptr, s);
-    if (kF32 && cols.any()) k_split<<<gn, 256, 0, s>>>(xh, sx, n, &ctl->g_attempt);
-    // FP64: the dual iterate (onto diag(1/d1) K*) and the primal residual's
+    const bool q = pdl_;  // programmatic dependent launches inside the loop body
+    launch_k(k_primal<T>, dim3(gn), dim3(kEwThreads), s, q, p, (const Ctl*)ctl, (const T*)x,
+             (const T*)gty, xh, kF32 && !cols.any() ? sx : (float2*)nullptr);
+    project<T>(cols, xh, xh, 1, d2, 1, 0, &ctl->g_attempt, nullptr, s, false, q);
+    if (kF32 && cols.any())
+      launch_k(k_split, dim3(gn), dim3(256), s, q, (const double*)xh, sx, n,
+               (const int*)&ctl->g_attempt);
+    // the dual iterate (onto diag(1/d1) K*) and the primal residual's
     // argument G xhat - h (onto diag(d1) K) are projected in one launch; the
     // residual is then also formed for rejected attempts, where it is unused
-    const bool fuse = std::is_same<T, double>::value;
-    double* res = fuse ? tm[0] : nullptr;
+    double* res = tm[0];
     KTimer* tg = timers ? timers + TM_SPMV_G : nullptr;
     if (dual_in_product) {
       // long rows: the dual step rides on the product's epilogue
-      spmv_it_out(false, xh, sx, DualOut<T>{p, ctl, y, gx, gxh, yh, res}, &ctl->g_attempt, s, tg);
+      spmv_it_out(false, xh, sx, DualOut<T>{p, ctl, y, gx, gxh, yh, res}, &ctl->g_attempt, s, tg, q);
     } else {
-      spmv_it(false, xh, sx, gxh, &ctl->g_attempt, s, tg);
-      k_dual<T><<<gm, kEwThreads, 0, s>>>(p, ctl, y, gxh, gx, yh, res);
+      spmv_it(false, xh, sx, gxh, &ctl->g_attempt, s, tg, q);
+      launch_k(k_dual<T>, dim3(gm), dim3(kEwThreads), s, q, p, (const Ctl*)ctl, (const T*)y,
+               (const T*)gxh, (const T*)gx, yh, res);
     }
-    if (fuse)
-      project<T>(rows, yh, reinterpret_cast<T*>(tm[0]), 2, d1, 1, 1, &ctl->g_attempt,
-                 &ctl->g_attempt, s, true);
-    else
-      project<T>(rows, yh, yh, 1, d1, 1, 1, &ctl->g_attempt, nullptr, s);
-    k_step<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, xh, y, yh, gxh, gx, part, sy);
-    spmv_it(true, yh, sy, gtyh, &ctl->g_accept, s, timers ? timers + TM_SPMV_GT : nullptr);
+    project<T>(rows, yh, reinterpret_cast<T*>(tm[0]), 2, d1, 1, 1, &ctl->g_attempt,
+               &ctl->g_attempt, s, true, q);
+    launch_k(k_step<T>, dim3(gmx), dim3(kEwThreads), s, q, p, ctl, (const T*)x, (const T*)xh,
+             (const T*)y, (const T*)yh, (const T*)gxh, (const T*)gx, part, sy);
+    spmv_it(true, yh, sy, gtyh, &ctl->g_accept, s, timers ? timers + TM_SPMV_GT : nullptr, q);
     const PointRef<T> ph{xh, yh, gxh, gtyh};
     const TmpRef t0{tm[0], tn[0], nullptr, nullptr};
-    if (!fuse) {
-      k_res_prep<T><<<dim3(gmx, 1), kEwThreads, 0, s>>>(p, &ctl->g_accept, ph, ph, t0, t0);
-      project<double>(rows, tm[0], tm[0], 1, d1, 0, 0, &ctl->g_accept, nullptr, s);
-    } else if (cols.any()) {
+    if (cols.any()) {
       const TmpRef tc{nullptr, tn[0], nullptr, nullptr};
-      k_res_prep<T><<<dim3(gmx, 1), kEwThreads, 0, s>>>(p, &ctl->g_accept, ph, ph, tc, tc);
+      launch_k(k_res_prep<T>, dim3(gmx, 1), dim3(kEwThreads), s, q, p,
+               (const int*)&ctl->g_accept, ph, ph, tc, tc);
     }
-    project<double>(cols, tn[0], tn[0], 1, d2, 0, 1, &ctl->g_accept, nullptr, s);
-    k_point_stats<T, false><<<gmx, kEwThreads, 0, s>>>(p, ctl, &ctl->g_accept, 0, ph, nullptr, nullptr, t0, part);
-    k_halpern<T><<<gmx, kEwThreads, 0, s>>>(p, ctl, x, y, gx, gty, xh, yh, gxh, gtyh, x0, y0, gx0,
-                                            gty0, xs, ys, trace, hA, use_cond);
+    project<double>(cols, tn[0], tn[0], 1, d2, 0, 1, &ctl->g_accept, nullptr, s, false, q);
+    launch_k(k_point_stats<T, false>, dim3(gmx), dim3(kEwThreads), s, q, p, ctl,
+             (const int*)&ctl->g_accept, 0, ph, (const T*)nullptr, (const T*)nullptr, t0, part);
+    launch_k(k_halpern<T>, dim3(gmx), dim3(kEwThreads), s, q, p, ctl, x, y, gx, gty,
+             (const T*)xh, (const T*)yh, (const T*)gxh, (const T*)gtyh, (const T*)x0,
+             (const T*)y0, (const T*)gx0, (const T*)gty0, xs, ys, trace, hA, use_cond);
   }
 
   void rec_check_stats(cudaStream_t s) {
@@ -1055,10 +1126,16 @@ struct Solver : SolverBase {
   void rec_probe(cudaStream_t s, cudaGraphConditionalHandle hB) {
     const Prob<T> p = prob();
     const int gmx = ew_grid(std::max(m, n));
-    k_probe_prep<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pzc(), pzb(), px[0], py[0], px[1], py[1]);
-    project<double>(cols, px[0], px[1], 2, d2, 1, 0, &ctl->bs[0].active, &ctl->bs[1].active, s);
-    project<double>(rows, py[0], py[1], 2, d1, 1, 1, &ctl->bs[0].active, &ctl->bs[1].active, s);
-    k_probe_reduce<T><<<dim3(gmx, 2), kEwThreads, 0, s>>>(p, ctl, pzc(), pzb(), px[0], py[0], px[1], py[1], part, hB, use_cond);
+    const bool q = pdl_;
+    launch_k(k_probe_prep<T>, dim3(gmx, 2), dim3(kEwThreads), s, q, p, (const Ctl*)ctl, pzc(),
+             pzb(), px[0], py[0], px[1], py[1]);
+    project<double>(cols, px[0], px[1], 2, d2, 1, 0, &ctl->bs[0].active, &ctl->bs[1].active, s,
+                    false, q);
+    project<double>(rows, py[0], py[1], 2, d1, 1, 1, &ctl->bs[0].active, &ctl->bs[1].active, s,
+                    false, q);
+    launch_k(k_probe_reduce<T>, dim3(gmx, 2), dim3(kEwThreads), s, q, p, ctl, pzc(), pzb(),
+             (const double*)px[0], (const double*)py[0], (const double*)px[1],
+             (const double*)py[1], part, hB, use_cond);
   }
 
   void rec_check_end(cudaStream_t s) {
@@ -1762,6 +1839,7 @@ void pdcs_default_options(pdcs_options* o) {
   o->use_adaptive_step_size_weight = 1;
   o->use_duality_gap_restart = 1;
   o->use_kkt_restart = 0;
+  o->overlap_launches = 0;
   o->kkt_restart_freq = 2000;
   o->print_freq = 2000;
   o->eps_primal_infeasible_low_acc = 1e-12;

@@ -42,8 +42,16 @@ struct SpmvTask {
   int64_t a, b;     // kinds 0/1: rows [a, b); kind 2: row a, chunk index b
   int64_t c, d;     // kind 2: nonzero range [c, d)
   int64_t pbase;    // kind 2: first partial slot of this long row
-  int64_t pad;
+  int64_t ra, rb;   // kind 2: the row's column run (nonzeros [ra, rb), see below)
+  int32_t col0;     // kind 2: column of nonzero ra
+  int32_t pad2;
 };
+
+// Column runs.  A long row's longest stretch of nonzeros whose column indices
+// are consecutive (ci[k + 1] = ci[k] + 1; the dense blocks a CSR matrix may
+// hold, such as a factor model's loadings) is described by its first nonzero
+// and first column; a chunk that lies wholly inside it reads no column index
+// and its gathers are contiguous.
 
 // Element type of the gathered vector for matrix values of type V.
 template <typename V>
@@ -93,6 +101,7 @@ PDCS_DEV float2 split_ff(double v) {
 // latency overlaps it; the call then finishes the row.
 template <typename T>
 struct StoreOut {
+  static constexpr int kMinBlocks = 8;  // resident CTAs per SM (32 registers)
   T* y;
   struct Pre {};
   PDCS_DEV Pre pre(int64_t) const { return Pre{}; }
@@ -107,11 +116,38 @@ PDCS_DEV double group_sum(double v) {
   return v;
 }
 
+// A lane's share of nonzeros [k0, e), stride S: trips of kSpmvUnroll nonzeros
+// issue their index, value and gather loads together, then the rest go one
+// per step (the plain strided order of additions).  RUN: the nonzeros lie in
+// a column run and the column of nonzero k is cb + k (no index is loaded).
+template <typename V, int S, bool RUN>
+PDCS_DEV void spmv_lane(Acc<V>& acc, int64_t k, int64_t e, const int32_t* __restrict__ ci,
+                        const V* __restrict__ vv, const typename SpmvX<V>::type* __restrict__ x,
+                        int64_t cb) {
+  using X = typename SpmvX<V>::type;
+  constexpr int U = kSpmvUnroll;
+  for (; k + (int64_t)(U - 1) * S < e; k += (int64_t)U * S) {
+    int32_t c[U];
+    V v[U];
+    X xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      c[u] = RUN ? (int32_t)(cb + k) + u * S : __ldg(ci + k + (int64_t)u * S);
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = __ldg(vv + k + (int64_t)u * S);
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc.add(v[u], xv[u]);
+  }
+  for (; k < e; k += S)
+    acc.add(__ldg(vv + k), __ldg(x + (RUN ? (int32_t)(cb + k) : __ldg(ci + k))));
+}
+
 template <typename V, int G, typename Out>
 PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
                               const int32_t* __restrict__ ci, const V* __restrict__ vv,
                               const typename SpmvX<V>::type* __restrict__ x, const Out& out) {
-  using X = typename SpmvX<V>::type;
   const int gid = threadIdx.x / G, lane = threadIdx.x % G, ng = kSpmvThreads / G;
   // every group runs the same number of trips so the shuffles stay converged
   const int64_t trips = (t.b - t.a + ng - 1) / ng;
@@ -122,22 +158,7 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
     if (lane == 0 && row < t.b) pr = out.pre(row);
     if (row < t.b) {
       const int64_t s = rp[row], e = rp[row + 1];
-      constexpr int U = kSpmvUnroll;
-      int64_t k = s + lane;
-      for (; k + (U - 1) * G < e; k += U * G) {
-        int32_t c[U];
-        V v[U];
-        X xv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) c[u] = __ldg(ci + k + u * G);
-#pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = __ldg(vv + k + u * G);
-#pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc.add(v[u], xv[u]);
-      }
-      for (; k < e; k += G) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
+      spmv_lane<V, G, false>(acc, s + lane, e, ci, vv, x, 0);
     }
     const double r = group_sum<G>(acc.get());
     if (lane == 0 && row < t.b) out(row, r, pr);
@@ -146,21 +167,27 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
 
 template <typename V, typename Out>
 PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci, const V* __restrict__ vv,
-                        const typename SpmvX<V>::type* __restrict__ x, const Out& out,
-                        double* __restrict__ partial, unsigned int* __restrict__ counters);
+                        const int32_t* __restrict__ ci,
+                        const V* __restrict__ vv, const typename SpmvX<V>::type* __restrict__ x,
+                        const Out& out, double* __restrict__ partial,
+                        unsigned int* __restrict__ counters);
 
 // y = A x over the task list, each row's value handed to `out` (StoreOut:
 // y[row]).  When `gate` is non-NULL and *gate == 0 the kernel does nothing
 // (used to skip products inside a captured graph).  partial / counters are the
 // scratch of kind-2 tasks (counters are left at zero).  tm, when non-NULL,
 // accumulates the launch's duration.
+// (Out::kMinBlocks resident CTAs per SM: the product is bound by memory
+// latency, and the highest occupancy the epilogue's registers allow keeps the
+// most loads in flight)
 template <typename V, typename Out>
-__global__ void __launch_bounds__(kSpmvThreads)
+__global__ void __launch_bounds__(kSpmvThreads, Out::kMinBlocks)
 k_spmv(const SpmvTask* __restrict__ tasks, const int64_t* __restrict__ rp,
        const int32_t* __restrict__ ci, const V* __restrict__ vv,
        const typename SpmvX<V>::type* __restrict__ x, Out out, double* __restrict__ partial,
        unsigned int* __restrict__ counters, const int* __restrict__ gate, KTimer* tm) {
+  pdl_wait();
+  pdl_trigger();
   if (gate != nullptr && *gate == 0) return;
   ktimer_begin(tm);
   spmv_task<V, Out>(tasks[blockIdx.x], rp, ci, vv, x, out, partial, counters);
@@ -169,10 +196,10 @@ k_spmv(const SpmvTask* __restrict__ tasks, const int64_t* __restrict__ rp,
 
 template <typename V, typename Out>
 PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci, const V* __restrict__ vv,
-                        const typename SpmvX<V>::type* __restrict__ x, const Out& out,
-                        double* __restrict__ partial, unsigned int* __restrict__ counters) {
-  using X = typename SpmvX<V>::type;
+                        const int32_t* __restrict__ ci,
+                        const V* __restrict__ vv, const typename SpmvX<V>::type* __restrict__ x,
+                        const Out& out, double* __restrict__ partial,
+                        unsigned int* __restrict__ counters) {
   if (t.kind == 0) {
     const int64_t row = t.a + threadIdx.x;
     if (row < t.b) {
@@ -193,22 +220,11 @@ PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
   // kind 2: chunk of a long row
   __shared__ double sh[kSpmvThreads + 1];
   Acc<V> acc;
-  int64_t k = t.c + threadIdx.x;
-  constexpr int U = kSpmvUnroll;
-  for (; k + (U - 1) * kSpmvThreads < t.d; k += U * kSpmvThreads) {
-    int32_t c[U];
-    V v[U];
-    X xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) c[u] = __ldg(ci + k + u * kSpmvThreads);
-#pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = __ldg(vv + k + u * kSpmvThreads);
-#pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) acc.add(v[u], xv[u]);
-  }
-  for (; k < t.d; k += kSpmvThreads) acc.add(__ldg(vv + k), __ldg(x + __ldg(ci + k)));
+  if (t.ra <= t.c && t.d <= t.rb)  // the whole chunk inside the row's column run
+    spmv_lane<V, kSpmvThreads, true>(acc, t.c + threadIdx.x, t.d, ci, vv, x,
+                                     (int64_t)t.col0 - t.ra);
+  else
+    spmv_lane<V, kSpmvThreads, false>(acc, t.c + threadIdx.x, t.d, ci, vv, x, 0);
   double r[1] = {acc.get()};
   block_sum<1>(r, sh);
   if (t.nchunks == 1) {

@@ -60,6 +60,7 @@ def test_default_options_follow_the_paper():
     # Sec. 3.2.3 direct-API defaults
     assert o.use_adaptive_step_size_weight == 1 and o.use_duality_gap_restart == 1
     assert o.use_kkt_restart == 0 and o.kkt_restart_freq == 2000 and o.print_freq == 2000
+    assert o.overlap_launches == 0
     assert o.eps_primal_infeasible_low_acc == 1e-12 and o.eps_dual_infeasible_low_acc == 1e-12
     assert o.eps_primal_infeasible_high_acc == 1e-16 and o.eps_dual_infeasible_high_acc == 1e-16
 
