@@ -98,7 +98,8 @@ typedef struct {
   int32_t precision;         /* 0 = FP64 throughout, 1 = FP32 bulk with FP64
                                 residuals, decisions, averages and exp Newton */
   int32_t require_abs;       /* 0: relative criterion only; 1: also abs_tol */
-  double bisect_rel_tol;     /* 1e-6: Algorithm 3 stops when t_r - t_l <= tol * t_r */
+  double bisect_rel_tol;     /* 1e-3: Algorithm 3 stops when t_r - t_l <= tol * t_r
+                                (the paper leaves the tolerance open) */
   int32_t verbose;           /* 0 silent, 1 one line per check period on stderr */
   int32_t trace_capacity;    /* >0: record one trace row per accepted iteration */
   int32_t profile;           /* 1: time every kernel launch on the device (see

@@ -25,8 +25,9 @@ Readings where the paper is silent or inconsistent (listed in the design notes):
   c8  in the first restart period there is no reference gap: only condition 3.
   c9  bisection: t0 = r / sqrt(tau ||b1||^2 + sigma ||b2||^2) (the unconstrained
       step reaching radius r), at most 64 doublings, bisection until
-      t_right - t_left <= 1e-6 t_right (at most 64 halvings); the value is
-      returned at the last probe; r = 0 or b = 0 give 0.
+      t_right - t_left <= bisect_rel_tol * t_right (default 1e-3; at most 64
+      halvings); the value is returned at the last probe; r = 0 or b = 0
+      give 0.
   c10 if any gap value used at a check is negative, every gap at that check is
       replaced by KKT_omega.
   c11 beta / maxErr / KKT_omega / rho^N use the rescaled problem; termination
@@ -181,7 +182,7 @@ class Options:
         self.method = "average"
         self.use_adaptive_restart = True
         self.check_freq = 64                 # duality-gap restart / termination period
-        self.bisect_rel_tol = 1e-6
+        self.bisect_rel_tol = 1e-3          # reading c9
         self.use_adaptive_step_size_weight = True
         self.use_duality_gap_restart = True
         self.use_kkt_restart = False

@@ -101,8 +101,36 @@ struct SpmvPlan {
   int ntasks = 0;
   double* partial = nullptr;
   unsigned int* counters = nullptr;
-  int64_t run_nnz = 0;      // nonzeros of chunks inside column runs (no index read)
+  int32_t* runlen = nullptr;  // per row: length of the leading column run (see runs_first)
+  int64_t run_nnz = 0;        // nonzeros whose column index the products do not read
+  int64_t run_rows = 0;       // rows whose run length (and first column) they read
 };
+
+// Rows of up to 4096 nonzeros are stored with their column run first: a row
+// whose longest stretch of consecutive columns has at least kMinRun nonzeros is
+// rotated (run, then the nonzeros before it, then those after it); the
+// products then take the run's columns from its first index.  One warp per
+// row; roff / rlen: offset of the run within the row and its length (0: the
+// row is copied as it is).
+__global__ void k_run_first(const int64_t* __restrict__ rp, const int32_t* __restrict__ roff,
+                            const int32_t* __restrict__ rlen, int64_t rows,
+                            const int32_t* __restrict__ ci, const double* __restrict__ v64,
+                            const float* __restrict__ v32, int32_t* __restrict__ ci2,
+                            double* __restrict__ w64, float* __restrict__ w32) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < rows; r += nwarps) {
+    const int64_t s = rp[r], len = rp[r + 1] - s, L = rlen[r], off = roff[r];
+    for (int64_t j = lane; j < len; j += 32) {
+      int64_t src = j;
+      if (L > 0) src = j < L ? off + j : (j - L < off ? j - L : j);
+      ci2[s + j] = ci[s + src];
+      w64[s + j] = v64[s + src];
+      if (v32 != nullptr) w32[s + j] = v32[s + src];
+    }
+  }
+}
 
 // Shortest stretch of consecutive column indices worth a run descriptor.
 constexpr int64_t kMinRun = 16;
@@ -132,10 +160,11 @@ static void longest_run(const std::vector<int32_t>& ci, int64_t s, int64_t e, in
 // nonzeros with consecutive columns is recorded in its chunks (ci: the column
 // indices on the host); chunks wholly inside it read no index.
 static SpmvPlan build_plan(const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
-                           Arena& ar, cudaStream_t st, int small_g) {
+                           const std::vector<int32_t>& runlen, int32_t* runlen_dev, Arena& ar,
+                           cudaStream_t st, int small_g) {
   const int64_t m = (int64_t)rp.size() - 1;
   std::vector<SpmvTask> tasks;
-  int64_t run_nnz = 0;
+  int64_t run_nnz = 0, run_rows = 0;
   int64_t npart = 0;
   int ncnt = 0;
   int64_t r = 0;
@@ -191,6 +220,15 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, const std::vector<int
     t.g = maxlen <= 512 ? small_g : 32;
     t.a = r;
     t.b = e;
+    if (t.kind == 1 && runlen_dev != nullptr) {
+      int64_t rn = 0;
+      for (int64_t q = r; q < e; ++q) rn += runlen[(size_t)q];
+      if (rn > 0) {
+        t.runs = 1;
+        run_nnz += rn;
+        run_rows += e - r;
+      }
+    }
     tasks.push_back(t);
     r = e;
   }
@@ -201,6 +239,8 @@ static SpmvPlan build_plan(const std::vector<int64_t>& rp, const std::vector<int
     CK(cudaMemcpyAsync(p.tasks, tasks.data(), tasks.size() * sizeof(SpmvTask), cudaMemcpyHostToDevice, st));
   }
   p.run_nnz = run_nnz;
+  p.run_rows = run_rows;
+  p.runlen = runlen_dev;
   p.partial = ar.alloc<double>(std::max<int64_t>(npart, 1));
   p.counters = ar.alloc<unsigned int>(std::max(ncnt, 1));
   CK(cudaMemsetAsync(p.counters, 0, sizeof(unsigned int) * std::max(ncnt, 1), st));
@@ -235,7 +275,7 @@ static void launch_spmv_out(const SpmvPlan& p, const int64_t* rp, const int32_t*
                             cudaStream_t st, KTimer* tm = nullptr, bool pdl = false) {
   if (p.ntasks == 0) return;
   launch_k(k_spmv<V, Out>, dim3(p.ntasks), dim3(kSpmvThreads), st, pdl,
-           (const SpmvTask*)p.tasks, rp, ci, vv, x, out, p.partial,
+           (const SpmvTask*)p.tasks, rp, ci, (const int32_t*)p.runlen, vv, x, out, p.partial,
            p.counters, gate, tm);
 }
 
@@ -710,12 +750,15 @@ struct Solver : SolverBase {
     fill_table(cols, csoc, cbig, cexp, cexpd, d2, n);
     const int small_g = sizeof(MV) == 8 ? 4 : 8;
     {
-      // column indices on the host for the run detection of the plans
-      std::vector<int32_t> hci((size_t)nnz);
+      // column indices on the host for the run detection of the plans; rows
+      // of up to 4096 nonzeros are then stored run first (k_run_first)
+      std::vector<int32_t> hci((size_t)nnz), hrl;
       if (nnz > 0) CK(cudaMemcpy(hci.data(), ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
-      planG = build_plan(hrp, hci, ar, st, small_g);
+      int32_t* rl = runs_first(hrp, hci, ci, vv64, kF32 ? (float*)vv : nullptr, hrl);
+      planG = build_plan(hrp, hci, hrl, rl, ar, st, small_g);
       if (nnz > 0) CK(cudaMemcpy(hci.data(), ciT, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
-      planGT = build_plan(hrpT, hci, ar, st, small_g);
+      rl = runs_first(hrpT, hci, ciT, vvT64, kF32 ? (float*)vvT : nullptr, hrl);
+      planGT = build_plan(hrpT, hci, hrl, rl, ar, st, small_g);
     }
     alloc_state();
     if (opt.eager) {
@@ -725,6 +768,53 @@ struct Solver : SolverBase {
       pdl_ = opt.overlap_launches != 0;
       capture();
     }
+  }
+
+  // Store every row of up to 4096 nonzeros whose longest column run has at
+  // least kMinRun nonzeros with that run first (k_run_first), in the column
+  // indices and in both value arrays (v32 may be NULL); the long rows keep
+  // their order (their chunks use the run in place).  hci: the column indices
+  // before the rotation.  Returns the device array of run lengths (NULL when
+  // no row qualifies) and fills hrl with it.
+  int32_t* runs_first(const std::vector<int64_t>& hrp, const std::vector<int32_t>& hci,
+                      int32_t* dci, double* v64, float* v32, std::vector<int32_t>& hrl) {
+    const int64_t rows = (int64_t)hrp.size() - 1;
+    hrl.assign((size_t)std::max<int64_t>(rows, 0), 0);
+    std::vector<int32_t> hoff((size_t)std::max<int64_t>(rows, 0), 0);
+    bool any = false;
+    for (int64_t r = 0; r < rows; ++r) {
+      const int64_t len = hrp[r + 1] - hrp[r];
+      if (len > 4096 || len < kMinRun) continue;
+      int64_t a, b;
+      longest_run(hci, hrp[r], hrp[r + 1], a, b);
+      if (b - a < kMinRun) continue;
+      hrl[(size_t)r] = (int32_t)(b - a);
+      hoff[(size_t)r] = (int32_t)(a - hrp[r]);
+      any = true;
+    }
+    if (!any) return nullptr;
+    int32_t* drl = ar.alloc<int32_t>(rows);
+    int32_t* doff = ar.alloc<int32_t>(rows);
+    copy_in(drl, hrl.data(), rows, st);
+    copy_in(doff, hoff.data(), rows, st);
+    const int64_t nz = hrp[rows];
+    int32_t* c2 = ar.alloc<int32_t>(nz);
+    double* w64 = ar.alloc<double>(nz);
+    float* w32 = v32 ? ar.alloc<float>(nz) : nullptr;
+    int64_t* drp_ = ar.alloc<int64_t>(rows + 1);
+    copy_in(drp_, hrp.data(), rows + 1, st);
+    k_run_first<<<warp_grid(rows), 256, 0, st>>>(drp_, doff, drl, rows, dci, v64, v32, c2, w64, w32);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dci, c2, sizeof(int32_t) * nz, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(v64, w64, sizeof(double) * nz, cudaMemcpyDeviceToDevice, st));
+    if (v32) CK(cudaMemcpyAsync(v32, w32, sizeof(float) * nz, cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    ar.release(c2);
+    ar.release(w64);
+    if (w32) ar.release(w32);
+    ar.release(drp_);
+    ar.release(doff);
+    return drl;
   }
 
   // Per-element kinds and cone tables from an ordered cone list starting at off.
@@ -977,7 +1067,10 @@ struct Solver : SolverBase {
     // (FP64 or its 8-byte FP32 pair) and the result once
     // (column indices only outside the chunks that lie in column runs)
     const double vb = (double)sizeof(MV);
-    auto idx_bytes = [&](const SpmvPlan& pl) { return 4.0 * (double)(nnz - pl.run_nnz); };
+    // (a row stored run first costs its run length and its first index)
+    auto idx_bytes = [&](const SpmvPlan& pl) {
+      return 4.0 * (double)(nnz - pl.run_nnz) + 8.0 * (double)pl.run_rows;
+    };
     pr->g_bytes = (double)nnz * vb + idx_bytes(planG) + 8.0 * (double)(m + 1) + 8.0 * (double)(n + m);
     // the dual step in the product's epilogue: y, G x, h and the row kind
     // read, yhat written per row, G xhat - h on the cone rows
@@ -1831,7 +1924,7 @@ void pdcs_default_options(pdcs_options* o) {
   o->check_freq = 64;
   o->precision = 0;
   o->require_abs = 0;
-  o->bisect_rel_tol = 1e-6;
+  o->bisect_rel_tol = 1e-3;
   o->verbose = 0;
   o->trace_capacity = 0;
   o->profile = 0;

@@ -44,7 +44,7 @@ struct SpmvTask {
   int64_t pbase;    // kind 2: first partial slot of this long row
   int64_t ra, rb;   // kind 2: the row's column run (nonzeros [ra, rb), see below)
   int32_t col0;     // kind 2: column of nonzero ra
-  int32_t pad2;
+  int32_t runs;     // kind 1: rows start with their column run (see runlen)
 };
 
 // Column runs.  A long row's longest stretch of nonzeros whose column indices
@@ -146,7 +146,8 @@ PDCS_DEV void spmv_lane(Acc<V>& acc, int64_t k, int64_t e, const int32_t* __rest
 
 template <typename V, int G, typename Out>
 PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
-                              const int32_t* __restrict__ ci, const V* __restrict__ vv,
+                              const int32_t* __restrict__ ci, const int32_t* __restrict__ runlen,
+                              const V* __restrict__ vv,
                               const typename SpmvX<V>::type* __restrict__ x, const Out& out) {
   const int gid = threadIdx.x / G, lane = threadIdx.x % G, ng = kSpmvThreads / G;
   // every group runs the same number of trips so the shuffles stay converged
@@ -158,7 +159,15 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
     if (lane == 0 && row < t.b) pr = out.pre(row);
     if (row < t.b) {
       const int64_t s = rp[row], e = rp[row + 1];
-      spmv_lane<V, G, false>(acc, s + lane, e, ci, vv, x, 0);
+      // rows of run tasks start with their column run (runlen[row] nonzeros,
+      // columns ci[s], ci[s] + 1, ...); the rest follow with their indices
+      int64_t re = s, cb = 0;
+      if (t.runs) {
+        re = s + __ldg(runlen + row);
+        if (re > s) cb = (int64_t)__ldg(ci + s) - s;
+      }
+      spmv_lane<V, G, true>(acc, s + lane, re, ci, vv, x, cb);
+      spmv_lane<V, G, false>(acc, re + lane, e, ci, vv, x, 0);
     }
     const double r = group_sum<G>(acc.get());
     if (lane == 0 && row < t.b) out(row, r, pr);
@@ -167,7 +176,7 @@ PDCS_DEV void spmv_group_rows(const SpmvTask& t, const int64_t* __restrict__ rp,
 
 template <typename V, typename Out>
 PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci,
+                        const int32_t* __restrict__ ci, const int32_t* __restrict__ runlen,
                         const V* __restrict__ vv, const typename SpmvX<V>::type* __restrict__ x,
                         const Out& out, double* __restrict__ partial,
                         unsigned int* __restrict__ counters);
@@ -183,20 +192,20 @@ PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
 template <typename V, typename Out>
 __global__ void __launch_bounds__(kSpmvThreads, Out::kMinBlocks)
 k_spmv(const SpmvTask* __restrict__ tasks, const int64_t* __restrict__ rp,
-       const int32_t* __restrict__ ci, const V* __restrict__ vv,
-       const typename SpmvX<V>::type* __restrict__ x, Out out, double* __restrict__ partial,
+       const int32_t* __restrict__ ci, const int32_t* __restrict__ runlen,
+       const V* __restrict__ vv, const typename SpmvX<V>::type* __restrict__ x, Out out, double* __restrict__ partial,
        unsigned int* __restrict__ counters, const int* __restrict__ gate, KTimer* tm) {
   pdl_wait();
   pdl_trigger();
   if (gate != nullptr && *gate == 0) return;
   ktimer_begin(tm);
-  spmv_task<V, Out>(tasks[blockIdx.x], rp, ci, vv, x, out, partial, counters);
+  spmv_task<V, Out>(tasks[blockIdx.x], rp, ci, runlen, vv, x, out, partial, counters);
   ktimer_end(tm);
 }
 
 template <typename V, typename Out>
 PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
-                        const int32_t* __restrict__ ci,
+                        const int32_t* __restrict__ ci, const int32_t* __restrict__ runlen,
                         const V* __restrict__ vv, const typename SpmvX<V>::type* __restrict__ x,
                         const Out& out, double* __restrict__ partial,
                         unsigned int* __restrict__ counters) {
@@ -212,9 +221,9 @@ PDCS_DEV void spmv_task(const SpmvTask& t, const int64_t* __restrict__ rp,
     return;
   }
   if (t.kind == 1) {
-    if (t.g == 4) spmv_group_rows<V, 4>(t, rp, ci, vv, x, out);
-    else if (t.g == 8) spmv_group_rows<V, 8>(t, rp, ci, vv, x, out);
-    else spmv_group_rows<V, 32>(t, rp, ci, vv, x, out);
+    if (t.g == 4) spmv_group_rows<V, 4>(t, rp, ci, runlen, vv, x, out);
+    else if (t.g == 8) spmv_group_rows<V, 8>(t, rp, ci, runlen, vv, x, out);
+    else spmv_group_rows<V, 32>(t, rp, ci, runlen, vv, x, out);
     return;
   }
   // kind 2: chunk of a long row

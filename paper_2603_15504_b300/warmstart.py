@@ -82,13 +82,18 @@ def collect(factories, workers=8, **options):
     return np.array(params), np.array(sols), res
 
 
-def collect_batched(factories, chunk=512, **options):
+def _progress(**kw):
+    print(json.dumps(kw), file=sys.stderr, flush=True)
+
+
+def collect_batched(factories, chunk=512, verbose=False, **options):
     """As collect, but every `chunk` instances are solved together in one
     persistent launch of the batched engine (pdcs_setup_batch /
     pdcs_solve_batch; FP64, each instance with its own step sizes, restarts
     and termination)."""
     params, sols, res = [], [], []
     for c0 in range(0, len(factories), chunk):
+        t0 = time.perf_counter()
         probs = []
         for f in factories[c0:c0 + chunk]:
             prob, par = f()
@@ -100,6 +105,9 @@ def collect_batched(factories, chunk=512, **options):
             sols.append(np.concatenate([r["x"], r["y"]]))
             res.append({k: r[k] for k in ("iters", "solve_time_s", "exit_code", "err_rel_p",
                                           "err_rel_d", "err_rel_gap")})
+        if verbose:
+            _progress(stage="data", done=len(res), chunk_s=time.perf_counter() - t0,
+                      reached=int(sum(r["exit_code"] == 0 for r in res[-len(out):])))
     return np.array(params), np.array(sols), res
 
 
@@ -174,12 +182,14 @@ def _main():
     if args.plain_data:
         params, sols, res = collect(facs, workers=args.workers, **opts)
     else:
-        params, sols, res = collect_batched(facs, chunk=args.chunk, **opts)
+        params, sols, res = collect_batched(facs, chunk=args.chunk, verbose=True, **opts)
     t_data = time.perf_counter() - t0
     t1 = time.perf_counter()
     ws = WarmStart(params, sols, n=args.n + 1)
     losses = ws.fit(args.steps)
     t_train = time.perf_counter() - t1
+    _progress(stage="train", seconds=t_train, loss_first=losses[0],
+              loss_last=float(np.mean(losses[-20:])))
     rows = []
     for i in range(args.test):
         prob, p = make(1, i)
@@ -189,6 +199,8 @@ def _main():
         x0, y0 = ws.predict(p)
         ex = np.linalg.norm(x0[0] - c["x"]) / max(1e-300, np.linalg.norm(c["x"]))
         ey = np.linalg.norm(y0[0] - c["y"]) / max(1e-300, np.linalg.norm(c["y"]))
+        _progress(stage="test", i=i, cold_iters=c["iters"], warm_iters=w["iters"],
+                  warm=bool(w["warm"]), cold_s=c["solve_time_s"], warm_s=w["wall_s"])
         rows.append(dict(cold_iters=c["iters"], cold_s=c["solve_time_s"], warm_iters=w["iters"],
                          err_x=ex, err_y=ey,
                          warm_s=w["wall_s"], warm=bool(w["warm"]), kkt_pred=w["kkt_pred"],
