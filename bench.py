@@ -38,10 +38,21 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-6 rel. KKT & PDHG iters/s; batched and warm-start vs plain FP64"
 UNIT = "PDHG iterations/s"
 CHECK_FREQ = 64
-# DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
-# (workload, precision, source digest of spmv.cuh at capture time); None when
-# the kernel changed after the counters were taken.
-NCU_TRAFFIC = {}
+# FP64 peak from unit counts and clocks: 148 SMs x 2 DFMA per SM per cycle
+# (ncu's sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained on this
+# part) x 2 flops x 2.032 GHz maximum SM clock = 1.203 TFLOP/s (nominal 1.25)
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+# DRAM bytes per launch of the two products (G xhat with the dual step, G^T
+# yhat) from one ncu capture, keyed by (workload, precision, source digest of
+# spmv.cuh at capture time); missing (traffic null) once the kernel changed.
+# The capture ran the n = 100,000 portfolio (20,250,124 nonzeros); traffic
+# grows with the nonzeros, so it is scaled by 40,600,072 / 20,250,124 to the
+# n = 200,000 workload.
+_NNZ_SCALE = 40_600_072 / 20_250_124
+NCU_TRAFFIC = {
+    ("portfolio", "fp64", "ecbed7b9c912708a"): (170.266e6 * _NNZ_SCALE, 197.234e6 * _NNZ_SCALE),
+    ("portfolio", "fp32", "ecbed7b9c912708a"): (88.285e6 * _NNZ_SCALE, 99.905e6 * _NNZ_SCALE),
+}
 
 
 def _args():
@@ -421,20 +432,37 @@ def run_ours(args):
     sp_bytes = prof["g_bytes"] * prof["g_launches"] + prof["gt_bytes"] * prof["gt_launches"]
     launches = prof["g_launches"] + prof["gt_launches"]
     achieved = sp_bytes / sp_time / 1e9 if sp_time > 0 else None
-    traffic = NCU_TRAFFIC.get((args.workload, args.precision, _spmv_digest()))
-    roofline = {"bound": "hbm", "kernel": "k_spmv (G xhat and G^T yhat)",
-                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"] if achieved else None,
-                "traffic": traffic, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": sp_bytes / launches if launches else None,
-                "avg_launch_us": 1e6 * sp_time / launches if launches else None,
-                "launches": launches,
-                "spmv_time_share": sp_time / elapsed_prof if elapsed_prof else None,
-                "window": "profiled window of %d steps after the timed one (in-kernel timers, "
-                          "first CTA start to last CTA end per launch)" % args.steps}
-    if args.precision == "fp64":
-        # each nonzero costs one FP64 FMA; context for the FP64 ALU bound
-        roofline["fp64_fma_per_s"] = (prof["nnz_flops"] / 2 * launches / sp_time) if sp_time else None
+    tr = NCU_TRAFFIC.get((args.workload, args.precision, _spmv_digest()))
+    traffic = ((tr[0] * prof["g_launches"] + tr[1] * prof["gt_launches"]) / launches
+               if tr and launches else None)
+    hbm = {"bound": "hbm", "kernel": "k_spmv (G xhat and G^T yhat)",
+           "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": achieved / peaks["hbm_gbs"] if achieved else None,
+           "traffic": traffic, "peak_source": peak_kind,
+           "algorithmic_bytes_per_launch": sp_bytes / launches if launches else None,
+           "avg_launch_us": 1e6 * sp_time / launches if launches else None,
+           "launches": launches,
+           "spmv_time_share": sp_time / elapsed_prof if elapsed_prof else None,
+           "window": "profiled window of %d steps after the timed one (in-kernel timers, "
+                     "first CTA start to last CTA end per launch)" % args.steps}
+    roofline = hbm
+    if args.precision == "fp64" and sp_time > 0:
+        # one FP64 FMA per nonzero: against the FP64 rate of the part (derived
+        # above from its DFMA units and clock), the product is closer to its
+        # arithmetic bound than to HBM once the column runs drop most index
+        # bytes
+        flops = prof["nnz_flops"] * launches / sp_time / 1e12
+        alu = dict(hbm, bound="alu", achieved=flops, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                   frac=flops / FP64_PEAK_TFLOPS,
+                   peak_source="derived: 148 SMs x 2 DFMA/cycle x 2 flops x 2.032 GHz "
+                               "(no measured FP64 peak)")
+        if alu["frac"] > (hbm["frac"] or 0.0):
+            roofline = alu
+            roofline["hbm"] = {k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "traffic",
+                                                   "peak_source")}
+        else:
+            roofline["fp64_alu"] = {k: alu[k] for k in ("achieved", "peak", "unit", "frac",
+                                                        "peak_source")}
 
     # end to end through the public API: set-up from pinned host arrays (H2D
     # inside the timed region), K periods from a cold start, solution back to

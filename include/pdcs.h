@@ -392,27 +392,36 @@ int pdcs_kkt(pdcs_handle* handle, const double* x, const double* y, pdcs_result*
  *   cuda_stream: the stream the work is ordered on (NULL: legacy default).
  * Scratch: one fixed device array of about 0.8 MB inside the library, sized
  * for at most 4096 rows with more than 4096 nonzeros and at most 65536
- * chunks of 4096 nonzeros among them; a matrix beyond either limit is
- * rejected with PDCS_ERR_INVALID before anything is computed.  Rows of up to
- * 4096 nonzeros have no limit.
- * The call synchronises cuda_stream once (to read that size check) and then
- * enqueues the product; y is ready when the stream reaches it.  Because of
- * that synchronisation it cannot be called while cuda_stream is being
- * captured into a graph: it returns PDCS_ERR_INVALID then, and the capture
- * is left intact.  It allocates no device memory and, when it succeeds, no
- * host memory either; a rejected call stores its message for
- * pdcs_last_error.
- * The first call on a device looks up the scratch's device address with that
- * device current and caches it.  The scratch's tickets must be zero when a
- * call starts: they are zero when the library is loaded and every completed
- * call leaves them zero (a call cut short by a device error does not).  All
- * calls on one device share the scratch, so calls that overlap in time race:
- * serialise them.  Results are deterministic (fixed summation order) but
- * round differently from the solver's own product.
- * Returns PDCS_OK, PDCS_ERR_INVALID (sizes, NULL or host pointers, scratch
- * limits, a capturing stream) or PDCS_ERR_CUDA. */
+ * chunks of 4096 nonzeros among them.  Rows of up to 4096 nonzeros have no
+ * limit.  The call checks the matrix against those limits on the device: a
+ * matrix beyond either is rejected there (nothing computed, y left as it
+ * was) and counted, and pdcs_spmv_noalloc_status reports the count.
+ * The call never synchronises: it enqueues two kernels on cuda_stream and
+ * returns; y is ready when the stream reaches them.  It may be captured into
+ * a graph, except the first call on a device (it looks up the scratch's
+ * device address with that device current, then caches it), which returns
+ * PDCS_ERR_INVALID inside a capture and leaves the capture intact.  It
+ * allocates no device memory and, when it succeeds, no host memory either; a
+ * rejected call stores its message for pdcs_last_error.
+ * The scratch's tickets must be zero when a call starts: they are zero when
+ * the library is loaded and every completed call leaves them zero (a call
+ * cut short by a device error does not).  All calls on one device share the
+ * scratch, so calls that overlap in time race: serialise them.  Results are
+ * deterministic (fixed summation order) but round differently from the
+ * solver's own product.
+ * Returns PDCS_OK, PDCS_ERR_INVALID (sizes, NULL or host pointers, a first
+ * call inside a capture) or PDCS_ERR_CUDA. */
 int pdcs_spmv_noalloc(int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                       const double* val, const double* x, double* y, void* cuda_stream);
+
+/* How many pdcs_spmv_noalloc calls on the current device were rejected on
+ * the device (matrix beyond the scratch's limits) since the previous query;
+ * the count is then reset to zero.  Synchronises cuda_stream (the stream the
+ * calls were ordered on, so that the count includes them); it therefore
+ * returns PDCS_ERR_INVALID, without touching the count, while cuda_stream is
+ * being captured.  rejected: host int64, written (0 on error).
+ * Returns PDCS_OK, PDCS_ERR_INVALID or PDCS_ERR_CUDA. */
+int pdcs_spmv_noalloc_status(void* cuda_stream, int64_t* rejected);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ Paper passages followed (section / equation / algorithm):
   * rescaling and unscaling, Algorithm 2 (Sec. 2.6);
   * termination, eq. PDCS_terminate_tolerance_rel (Sec. 3.2.3), exit codes Table 1.
 
-Readings where the paper is silent or inconsistent (listed in the design notes):
+Readings where the paper is silent or inconsistent:
   c3  kbar is incremented at the start of every attempt (accepted or rejected)
       before the step-size formula uses (kbar + 1).
   c4  eta_bar = +inf when (Delta y)^T G (Delta x) = 0.

@@ -102,7 +102,7 @@ EXPORTS = ("pdcs_default_options", "pdcs_setup", "pdcs_solve", "pdcs_resume", "p
            "pdcs_mlp_default_config", "pdcs_mlp_create", "pdcs_mlp_train_step",
            "pdcs_mlp_gradients", "pdcs_mlp_predict", "pdcs_mlp_get_layer", "pdcs_mlp_set_layer",
            "pdcs_mlp_free", "pdcs_kkt", "pdcs_setup_batch", "pdcs_solve_batch",
-           "pdcs_spmv_noalloc")
+           "pdcs_spmv_noalloc", "pdcs_spmv_noalloc_status")
 
 _LIB = None
 
@@ -151,6 +151,8 @@ def lib():
     L.pdcs_last_error.restype = ctypes.c_char_p
     L.pdcs_spmv_noalloc.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp]
     L.pdcs_spmv_noalloc.restype = ctypes.c_int
+    L.pdcs_spmv_noalloc_status.argtypes = [vp, ctypes.POINTER(i64)]
+    L.pdcs_spmv_noalloc_status.restype = ctypes.c_int
     L.pdcs_setup_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PdcsInstance), i64,
                                    ctypes.POINTER(PdcsOptions), vp]
     L.pdcs_setup_batch.restype = ctypes.c_int
@@ -377,9 +379,11 @@ class Solver:
 
 
 def spmv_noalloc(row_ptr, col_idx, val, x, y, n=None, stream=None):
-    """y = G x through pdcs_spmv_noalloc (no allocation in the call).  All
-    arrays are CUDA tensors on the current device (int64, int32, float64,
-    float64, float64); stream: a torch.cuda.Stream (default: the current one)."""
+    """y = G x through pdcs_spmv_noalloc (no allocation, no synchronisation in
+    the call).  All arrays are CUDA tensors on the current device (int64,
+    int32, float64, float64, float64); stream: a torch.cuda.Stream (default:
+    the current one).  A matrix beyond the scratch's limits is rejected on the
+    device, leaving y as it was: spmv_noalloc_status() counts such calls."""
     import torch
     m = row_ptr.numel() - 1
     n = x.numel() if n is None else int(n)
@@ -387,6 +391,16 @@ def spmv_noalloc(row_ptr, col_idx, val, x, y, n=None, stream=None):
     _check(lib().pdcs_spmv_noalloc(int(m), n, _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(x),
                                    _ptr(y), ctypes.c_void_p(st.cuda_stream)))
     return y
+
+
+def spmv_noalloc_status(stream=None):
+    """Number of spmv_noalloc calls rejected on the device since the previous
+    query (then reset); synchronises `stream` (default: the current one)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_int64(0)
+    _check(lib().pdcs_spmv_noalloc_status(ctypes.c_void_p(st.cuda_stream), ctypes.byref(out)))
+    return int(out.value)
 
 
 class Batch:

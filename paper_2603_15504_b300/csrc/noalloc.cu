@@ -23,9 +23,12 @@
 //    and give wrong results: serialise them;
 //  * the first call on a device looks up the scratch's device address
 //    (cudaGetSymbolAddress, with that device current) and caches it;
-//  * every call synchronises its stream once, to read the size check before
-//    anything is computed, so it cannot run while that stream is being
-//    captured into a graph: it refuses with PDCS_ERR_INVALID then.
+//  * a call never synchronises: the size check runs on the device, and a
+//    matrix beyond the scratch makes the product kernel return without
+//    writing y and adds one to a sticky count of rejected calls, which
+//    pdcs_spmv_noalloc_status reads (synchronising then) and clears.  So
+//    the call can be captured into a graph, except the first one on a
+//    device, which looks up the scratch's address.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,7 +56,7 @@ struct NaStatus {
   long long long_rows;  // rows longer than kNaChunk
   long long chunks;     // their chunks
   int overflow;         // 1: more than the scratch holds (nothing computed)
-  int pad;
+  unsigned int rejected;  // calls rejected since the last status query (sticky)
 };
 
 // Everything a call needs beyond the caller's arrays (about 0.8 MB).
@@ -109,6 +112,7 @@ __global__ void __launch_bounds__(kNaScanThreads) k_na_scan(const int64_t* __res
     s->status.long_rows = tot_rows;
     s->status.chunks = tot_chunks;
     s->status.overflow = overflow ? 1 : 0;
+    if (overflow) s->status.rejected += 1u;  // one thread, ordered by the stream
     if (!overflow) s->first[tot_rows] = (int)tot_chunks;
   }
   if (overflow || nr == 0) return;
@@ -147,6 +151,7 @@ __global__ void __launch_bounds__(256) k_na_spmv(const int64_t* __restrict__ rp,
                                                  const double* __restrict__ x, double* __restrict__ y,
                                                  int64_t m, NaScratch* s) {
   const int lane = threadIdx.x & 31;
+  if (s->status.overflow) return;  // rejected by the scan: y stays as it was
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = wid; r < m; r += nw) {
@@ -201,6 +206,38 @@ bool na_device_ptr(const void* p, int dev) {
   return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
+// Device address of the scratch on the current device; the first lookup on a
+// device may load the module, so it is refused inside a stream capture.
+int na_scratch(bool capturing, NaScratch** out, int* dev_out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
+    return na_fail(PDCS_ERR_CUDA, "pdcs_spmv_noalloc: no usable current device");
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_addr[dev]) {
+    if (capturing)
+      return na_fail(PDCS_ERR_INVALID,
+                     "pdcs_spmv_noalloc: the first call on a device cannot be captured (it "
+                     "looks up the scratch's address); make one call before capturing");
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess) return na_fail(PDCS_ERR_CUDA, cudaGetErrorString(e));
+    g_na_addr[dev] = static_cast<NaScratch*>(p);
+  }
+  *out = g_na_addr[dev];
+  *dev_out = dev;
+  return PDCS_OK;
+}
+
+int na_capturing(cudaStream_t st, bool* capturing) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return na_fail(PDCS_ERR_CUDA, "pdcs_spmv_noalloc: cannot query the stream's capture state");
+  }
+  *capturing = cap != cudaStreamCaptureStatusNone;
+  return PDCS_OK;
+}
+
 }  // namespace
 
 extern "C" int pdcs_spmv_noalloc(int64_t m, int64_t n, const int64_t* row_ptr,
@@ -211,54 +248,50 @@ extern "C" int pdcs_spmv_noalloc(int64_t m, int64_t n, const int64_t* row_ptr,
   if (!row_ptr || !y || (n > 0 && (!col_idx || !val || !x)))
     return na_fail(PDCS_ERR_INVALID, "pdcs_spmv_noalloc: NULL array");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  // the size check below synchronises the stream, which would invalidate a
-  // capture in progress on it: refuse instead
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
-    cudaGetLastError();
-    return na_fail(PDCS_ERR_CUDA, "pdcs_spmv_noalloc: cannot query the stream's capture state");
-  }
-  if (cap != cudaStreamCaptureStatusNone)
-    return na_fail(PDCS_ERR_INVALID,
-                   "pdcs_spmv_noalloc: the stream is being captured; this call synchronises the "
-                   "stream and cannot be captured");
+  bool capturing = false;
+  int rc = na_capturing(st, &capturing);
+  if (rc != PDCS_OK) return rc;
+  NaScratch* s = nullptr;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
-    return na_fail(PDCS_ERR_CUDA, "pdcs_spmv_noalloc: no usable current device");
+  rc = na_scratch(capturing, &s, &dev);
+  if (rc != PDCS_OK) return rc;
   if (!na_device_ptr(row_ptr, dev) || !na_device_ptr(y, dev) ||
       (n > 0 && (!na_device_ptr(col_idx, dev) || !na_device_ptr(val, dev) ||
                  !na_device_ptr(x, dev))))
     return na_fail(PDCS_ERR_INVALID,
                    "pdcs_spmv_noalloc: every array must be device memory of the current device");
-  NaScratch* s = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_addr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
-      if (e != cudaSuccess) return na_fail(PDCS_ERR_CUDA, cudaGetErrorString(e));
-      g_na_addr[dev] = static_cast<NaScratch*>(p);
-    }
-    s = g_na_addr[dev];
-  }
-  k_na_scan<<<1, kNaScanThreads, 0, st>>>(row_ptr, m, s);
-  NaStatus hs;
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, &s->status, sizeof(hs), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return na_fail(PDCS_ERR_CUDA, cudaGetErrorString(e));
-  if (hs.overflow)
-    return na_fail(PDCS_ERR_INVALID,
-                   "pdcs_spmv_noalloc: more than 4096 rows with over 4096 nonzeros, or more than "
-                   "65536 chunks of 4096 nonzeros in them: beyond the fixed scratch");
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
     sms = 148;
-  const int64_t warps = m + hs.chunks;
-  const int64_t blocks = std::min<int64_t>((warps + 7) / 8, (int64_t)sms * 16);
-  k_na_spmv<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(row_ptr, col_idx, val, x, y,
-                                                                    m, s);
-  e = cudaGetLastError();
+  // the chunk count is known only on the device: 16 CTAs per SM stride over
+  // the short rows and then the chunks
+  const int64_t blocks = (int64_t)sms * 16;
+  k_na_scan<<<1, kNaScanThreads, 0, st>>>(row_ptr, m, s);
+  k_na_spmv<<<(unsigned)blocks, 256, 0, st>>>(row_ptr, col_idx, val, x, y, m, s);
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(PDCS_ERR_CUDA, cudaGetErrorString(e));
+  return PDCS_OK;
+}
+
+extern "C" int pdcs_spmv_noalloc_status(void* cuda_stream, int64_t* rejected) {
+  if (!rejected) return na_fail(PDCS_ERR_INVALID, "pdcs_spmv_noalloc_status: NULL output");
+  *rejected = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  bool capturing = false;
+  int rc = na_capturing(st, &capturing);
+  if (rc != PDCS_OK) return rc;
+  if (capturing)
+    return na_fail(PDCS_ERR_INVALID,
+                   "pdcs_spmv_noalloc_status: synchronises its stream, which is being captured");
+  NaScratch* s = nullptr;
+  int dev = 0;
+  rc = na_scratch(false, &s, &dev);
+  if (rc != PDCS_OK) return rc;
+  unsigned int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, &s->status.rejected, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&s->status.rejected, 0, sizeof(h), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return na_fail(PDCS_ERR_CUDA, cudaGetErrorString(e));
+  *rejected = (int64_t)h;
   return PDCS_OK;
 }

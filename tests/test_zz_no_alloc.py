@@ -57,10 +57,19 @@ def test_noalloc_product_rejects_what_its_scratch_cannot_hold():
     col_idx = np.tile(np.arange(width, dtype=np.int32), rows)
     val = np.ones(rows * width)
     y = torch.full((rows,), 7.0, dtype=torch.float64, device="cuda")
-    with pytest.raises(P.PdcsError, match="beyond the fixed scratch"):
-        P.spmv_noalloc(_dev(torch, row_ptr), _dev(torch, col_idx), _dev(torch, val),
-                       torch.ones(n, dtype=torch.float64, device="cuda"), y)
-    assert bool((y == 7.0).all())  # nothing written
+    assert P.spmv_noalloc_status() == 0  # no earlier call was rejected
+    P.spmv_noalloc(_dev(torch, row_ptr), _dev(torch, col_idx), _dev(torch, val),
+                   torch.ones(n, dtype=torch.float64, device="cuda"), y)
+    # rejected on the device: counted once, nothing written, the count reset
+    assert P.spmv_noalloc_status() == 1
+    assert P.spmv_noalloc_status() == 0
+    assert bool((y == 7.0).all())
+    # one long row fewer fits, and the next call computes
+    P.spmv_noalloc(_dev(torch, row_ptr[:rows]), _dev(torch, col_idx[:(rows - 1) * width]),
+                   _dev(torch, val[:(rows - 1) * width]),
+                   torch.ones(n, dtype=torch.float64, device="cuda"), y[:rows - 1])
+    assert P.spmv_noalloc_status() == 0
+    assert bool((y[:rows - 1] == float(width)).all()) and float(y[-1]) == 7.0
     # host arrays are rejected (staging copies would allocate)
     yh = np.full(2, 7.0)
     rc = P.lib().pdcs_spmv_noalloc(2, 2, row_ptr[:3].ctypes.data, col_idx.ctypes.data,
@@ -90,31 +99,45 @@ def test_noalloc_product_small_matrix_by_definition():
     assert np.max(np.abs(got - ref) / scale) <= 1e-13
 
 
-def test_noalloc_product_refuses_a_capturing_stream():
-    """The call synchronises its stream to read the size check, so it must not
-    run inside a stream capture: it refuses, and the capture stays valid."""
+def test_noalloc_product_is_captured_into_a_graph_and_replayed():
+    """The call never synchronises, so after a first plain call on the device
+    it can be captured: the replayed graph recomputes y from the current x."""
     P, torch = _env()
-    rp = torch.tensor([0, 1, 2], dtype=torch.int64, device="cuda")
-    ci = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
-    val = torch.tensor([2.0, 3.0], dtype=torch.float64, device="cuda")
+    rp = torch.tensor([0, 1, 3, 3], dtype=torch.int64, device="cuda")
+    ci = torch.tensor([0, 0, 1], dtype=torch.int32, device="cuda")
+    val = torch.tensor([2.0, 3.0, -1.0], dtype=torch.float64, device="cuda")
     x = torch.tensor([1.0, 1.0], dtype=torch.float64, device="cuda")
-    y = torch.zeros(2, dtype=torch.float64, device="cuda")
-    s = torch.cuda.Stream()
+    y = torch.full((3,), 9.0, dtype=torch.float64, device="cuda")
+    P.spmv_noalloc(rp, ci, val, x, y)  # the first call on the device, outside capture
     torch.cuda.synchronize()
+    assert y.tolist() == [2.0, 2.0, 0.0]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(s):
         g.capture_begin()
         try:
-            rc = P.lib().pdcs_spmv_noalloc(2, 2, rp.data_ptr(), ci.data_ptr(), val.data_ptr(),
-                                           x.data_ptr(), y.data_ptr(), s.cuda_stream)
-            y.add_(1.0)  # the capture still records work after the refusal
+            P.spmv_noalloc(rp, ci, val, x, y, stream=s)
         finally:
             g.capture_end()
-    assert rc == -1 and b"captured" in P.lib().pdcs_last_error()
+    torch.cuda.current_stream().wait_stream(s)
+    x.copy_(torch.tensor([0.5, -2.0], dtype=torch.float64))
     g.replay()
     torch.cuda.synchronize()
-    assert y.tolist() == [1.0, 1.0]
-    # and outside the capture the same call works
-    P.spmv_noalloc(rp, ci, val, x, y)
+    assert y.tolist() == [1.0, 3.5, 0.0]
+    # the status query synchronises, so it refuses a capturing stream
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g2.capture_begin()
+        try:
+            out = P.ctypes.c_int64(5)
+            rc = P.lib().pdcs_spmv_noalloc_status(P.ctypes.c_void_p(s.cuda_stream),
+                                                  P.ctypes.byref(out))
+            y.add_(1.0)
+        finally:
+            g2.capture_end()
+    assert rc == -1 and b"captured" in P.lib().pdcs_last_error() and out.value == 0
+    g2.replay()
     torch.cuda.synchronize()
-    assert y.tolist() == [2.0, 3.0]
+    assert y.tolist() == [2.0, 4.5, 1.0]
+    assert P.spmv_noalloc_status() == 0
