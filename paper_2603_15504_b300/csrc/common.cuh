@@ -59,25 +59,24 @@ PDCS_DEV double warp_max(double v) {
 }
 
 // Block reductions.  FP64 instructions are scarce on this GPU (one FP64 pipe
-// slot serves a handful of lanes per cycle), so the trees avoid redundant FP64
-// work: every thread stages its K values in shared memory, warp 0 alone adds
-// them (lane l takes threads l, l+32, ... in order, then a fixed butterfly), and
-// the totals are broadcast back.  Deterministic.  `sh` must hold
-// K * blockDim.x + K doubles.
+// slot serves a handful of lanes per cycle, and a single warp's dependent FP64
+// chain is slow), so the trees avoid redundant FP64 work and spread what is
+// left over the SM's four schedulers: every thread stages its K values in
+// shared memory, then warp w adds values w, w + nwarps, ... (lane l takes
+// threads l, l+32, ... in order, then a fixed butterfly), and the totals are
+// broadcast back.  Deterministic, and the same sums whichever warp adds them.
+// `sh` must hold K * blockDim.x + K doubles.
 template <int K>
 PDCS_DEV void block_sum(double (&v)[K], double* sh) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, nw = nt >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) sh[k * nt + tid] = v[k];
   __syncthreads();
-  if (tid < 32) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      for (int t = tid; t < nt; t += 32) s += sh[k * nt + t];
-      s = warp_sum(s);
-      if (tid == 0) sh[K * nt + k] = s;
-    }
+  for (int k = tid >> 5; k < K; k += nw) {
+    double s = 0.0;
+    for (int t = lane; t < nt; t += 32) s += sh[k * nt + t];
+    s = warp_sum(s);
+    if (lane == 0) sh[K * nt + k] = s;
   }
   __syncthreads();
 #pragma unroll
@@ -100,19 +99,16 @@ PDCS_DEV double warp_max_nonneg(double v) {
 
 template <int K>
 PDCS_DEV void block_max(double (&v)[K], double* sh) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, nw = nt >> 5;
   long long* shl = reinterpret_cast<long long*>(sh);
 #pragma unroll
   for (int k = 0; k < K; ++k) shl[k * nt + tid] = __double_as_longlong(v[k]);
   __syncthreads();
-  if (tid < 32) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      long long s = 0;
-      for (int t = tid; t < nt; t += 32) s = max(s, shl[k * nt + t]);
-      s = warp_max_bits(s);
-      if (tid == 0) shl[K * nt + k] = s;
-    }
+  for (int k = tid >> 5; k < K; k += nw) {
+    long long s = 0;
+    for (int t = lane; t < nt; t += 32) s = max(s, shl[k * nt + t]);
+    s = warp_max_bits(s);
+    if (lane == 0) shl[K * nt + k] = s;
   }
   __syncthreads();
 #pragma unroll

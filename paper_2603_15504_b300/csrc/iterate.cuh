@@ -198,6 +198,28 @@ __global__ void __launch_bounds__(kEwThreads) k_dual(Prob<T> p, const Ctl* __res
   ktimer_end(tslot(p.tm, TM_DUAL));
 }
 
+// (kb1)^-0.3 and (kb1)^-0.6 for a count kb1 >= 2 (the exponents of Function
+// 1).  A library FP64 pow is a long dependent chain of FP64 operations, and
+// on this part every dependent FP64 operation of a thread costs ~64 cycles
+// (the pair of pows took ~5.7 us of the step's critical path).  Instead: an
+// FP32 seed (relative error ~1e-7), then two Newton steps in FP64 on
+// f(p) = kb1^3 p^10 - 1, p <- p - p (q - 1) / (10 q) with q = kb1^3 p^10 and
+// 1 / q expanded to second order around 1 (|q - 1| is a few 1e-6), which
+// square the error twice: the result is within a few units in the last place
+// of the exact power; (kb1)^-0.6 is its square.
+PDCS_DEV void step_powers(double kb1, double& p3, double& p6) {
+  double p = (double)powf((float)kb1, -0.3f);
+  const double K = kb1 * kb1 * kb1;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double p2 = p * p, p4 = p2 * p2, p8 = p4 * p4;
+    const double e = p8 * p2 * K - 1.0;
+    p = p - 0.1 * p * (e * (1.0 - e));
+  }
+  p3 = p;
+  p6 = p * p;
+}
+
 // Step-size test of Function 1 (eq. adaptive_step_size) from the reduced
 // ||dx||^2, ||dy||^2 and dy^T G dx.  kbar counts every attempt and is
 // incremented before the exponents use (kbar + 1).  (Thread-0 logic shared by
@@ -217,7 +239,9 @@ PDCS_DEV void ctl_step_finalize(Ctl& c, double dx2, double dy2, double inter) {
   const double kb1 = (double)(c.kbar + 1);
   const double num = 0.5 * (omega * dx2 + dy2 / omega);
   const double eta_bar = inter > 0.0 ? num / inter : INFINITY;
-  const double eta_p = fmin((1.0 - pow(kb1, -0.3)) * eta_bar, (1.0 + pow(kb1, -0.6)) * eta);
+  double p3, p6;
+  step_powers(kb1, p3, p6);
+  const double eta_p = fmin((1.0 - p3) * eta_bar, (1.0 + p6) * eta);
   const int acc = eta < eta_bar ? 1 : 0;
   c.accepted = acc;
   if (acc) {
@@ -418,9 +442,28 @@ PDCS_DEV double proj_lambda(double lam, double lo, double hi) {
   return lam;
 }
 
-PDCS_DEV void finish_stats(const Ctl* ctl, PointStats& st, const double* s, const double* mx) {
-  st.abs_p = sqrt(s[0]);
-  st.abs_d = sqrt(s[1]);
+// The square roots and quotients of the statistics, in six independent
+// groups (k = 0..5) so that one point's groups can run on separate warps:
+// q[0..1] abs_p, rel_p; q[2..3] abs_d, rel_d; q[4] rel_gap; q[5] inf_rel_p;
+// q[6] inf_rel_d; q[7] inf_rel_gap.
+constexpr int kStatGroups = 6;
+PDCS_DEV void stats_quotients(const Ctl* ctl, int k, const double* s, const double* mx,
+                              double* q) {
+  switch (k) {
+    case 0: q[0] = sqrt(s[0]); q[1] = q[0] / (1.0 + ctl->h1); break;
+    case 1: q[2] = sqrt(s[1]); q[3] = q[2] / (1.0 + ctl->c1); break;
+    case 2: q[4] = fabs(s[2] - s[3]) / (1.0 + fabs(s[2]) + fabs(s[3])); break;
+    case 3: q[5] = mx[0] / (1.0 + fmax(ctl->hinf, fmax(mx[1], mx[2]))); break;
+    case 4: q[6] = mx[3] / (1.0 + fmax(ctl->cinf, mx[4])); break;
+    case 5: q[7] = fabs(s[2] - s[3]) / (1.0 + fmax(fabs(s[2]), fabs(s[3]))); break;
+    default: break;
+  }
+}
+static_assert(kEwThreads / 32 >= kStatGroups, "one warp per quotient group");
+
+PDCS_DEV void finish_stats_q(PointStats& st, const double* s, const double* mx, const double* q) {
+  st.abs_p = q[0];
+  st.abs_d = q[2];
   st.pobj = s[2];
   st.dobj = s[3];
   st.u2 = s[4];
@@ -428,30 +471,38 @@ PDCS_DEV void finish_stats(const Ctl* ctl, PointStats& st, const double* s, cons
   st.dx2 = s[6];
   st.dy2 = s[7];
   st.gap = fabs(st.pobj - st.dobj);
-  st.rel_p = st.abs_p / (1.0 + ctl->h1);
-  st.rel_d = st.abs_d / (1.0 + ctl->c1);
-  st.rel_gap = st.gap / (1.0 + fabs(st.pobj) + fabs(st.dobj));
+  st.rel_p = q[1];
+  st.rel_d = q[3];
+  st.rel_gap = q[4];
   st.max_err = fmax(st.rel_p, fmax(st.rel_d, st.rel_gap));
   st.inf_abs_p = mx[0];
   st.inf_abs_d = mx[3];
-  st.inf_rel_p = mx[0] / (1.0 + fmax(ctl->hinf, fmax(mx[1], mx[2])));
-  st.inf_rel_d = mx[3] / (1.0 + fmax(ctl->cinf, mx[4]));
-  st.inf_rel_gap = st.gap / (1.0 + fmax(fabs(st.pobj), fabs(st.dobj)));
+  st.inf_rel_p = q[5];
+  st.inf_rel_d = q[6];
+  st.inf_rel_gap = q[7];
   st.inf_max = fmax(st.inf_rel_p, fmax(st.inf_rel_d, st.inf_rel_gap));
+}
+
+PDCS_DEV void finish_stats(const Ctl* ctl, PointStats& st, const double* s, const double* mx) {
+  double q[8];
+  for (int k = 0; k < kStatGroups; ++k) stats_quotients(ctl, k, s, mx, q);
+  finish_stats_q(st, s, mx, q);
+}
+
+// Reflection parameter beta (eq. adaptive_reflection) from maxErr.
+PDCS_DEV void ctl_set_beta(Ctl& c) {
+  const double me = c.st[0].max_err;
+  double beta = me > 0.0 ? -0.1 * log10(me) + 0.2 : 1.0;
+  beta = fmin(1.0, fmax(0.0, beta));
+  if (isnan(me)) beta = 0.0;
+  c.beta = beta;
 }
 
 // Statistics of one point from its reduced sums / maxima; slot 0 also sets the
 // reflection parameter beta (eq. adaptive_reflection) from maxErr.
 PDCS_DEV void ctl_stats_finalize(Ctl& c, int slot, const double* S, const double* M) {
-  PointStats& st = c.st[slot];
-  finish_stats(&c, st, S, M);
-  if (slot == 0) {
-    const double me = st.max_err;
-    double beta = me > 0.0 ? -0.1 * log10(me) + 0.2 : 1.0;
-    beta = fmin(1.0, fmax(0.0, beta));
-    if (isnan(me)) beta = 0.0;
-    c.beta = beta;
-  }
+  finish_stats(&c, c.st[slot], S, M);
+  if (slot == 0) ctl_set_beta(c);
 }
 
 // Per-element contributions to the point statistics (row i / column j).
@@ -556,9 +607,14 @@ __global__ void __launch_bounds__(kEwThreads) k_point_stats(Prob<T> p, Ctl* __re
   if (!last_block_done(&ctl->cnt[CNT_STATS0 + slot])) return;
   double S[kStatSums], M[kStatMax];
   cta_reduce_parts<kStatSums, kStatMax>(part, gridDim.x, kStatK, S, M, sh);
+  // the quotient groups on separate warps (schedulers), then thread 0
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0 && w < kStatGroups) stats_quotients(ctl, w, S, M, sh);
+  __syncthreads();
   if (threadIdx.x != 0) return;
   ctl->cnt[CNT_STATS0 + slot] = 0u;
-  ctl_stats_finalize(*ctl, slot, S, M);
+  finish_stats_q(ctl->st[slot], S, M, sh);
+  if (slot == 0) ctl_set_beta(*ctl);
 }
 
 // ------------------------------------------------------- Halpern + average

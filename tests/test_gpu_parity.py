@@ -327,9 +327,12 @@ def test_kkt_omega_fallback_branch_on_a_negative_gap():
     P = _gpu()
     prob = workloads.tiny_conic(seed=0, m_nonneg=20, soc_rows=(5, 5), nb=40, soc_cols=(4, 4),
                                 density=0.15)
+    # the recorded trajectory is the one of Algorithm 3 bisected to 1e-6 (with
+    # the default 1e-3 the solve restarts elsewhere and keeps no previous gap
+    # at iteration 1979)
     states = {1979: None}
     oracle.solve(oracle.problem_from_dict(prob), states=states, max_iter=1979, check_freq=64,
-                 rel_tol=1e-13)
+                 rel_tol=1e-13, bisect_rel_tol=1e-6)
     st = dict(states[1979])
     assert st["has_prev"]
     st["prev"] = (-1e-12,) + tuple(st["prev"][1:])  # a negative stored gap
@@ -337,12 +340,12 @@ def test_kkt_omega_fallback_branch_on_a_negative_gap():
     ostates = {k: None for k in ks[1:] + [ks[-1] + 1]}
     otr = []
     oracle.solve(oracle.problem_from_dict(prob), trace=otr, states=ostates, max_iter=ks[-1] + 1,
-                 check_freq=64, rel_tol=1e-13, init_state=st)
+                 check_freq=64, rel_tol=1e-13, init_state=st, bisect_rel_tol=1e-6)
     orow = {r["iter"]: r for r in otr}
     assert orow[1984]["check"] == 1 and orow[1984]["fallback"] == 1
     ostates[1979] = st
     with P.Solver(prob, trace_capacity=ks[-1] + 1, check_freq=64, time_limit=60.0,
-                  rel_tol=1e-13) as s:
+                  rel_tol=1e-13, bisect_rel_tol=1e-6) as s:
         s.set_state(_to_gpu_state(st))
         for k in ks:
             if k > ks[0]:
