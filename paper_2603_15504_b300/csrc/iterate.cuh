@@ -1463,32 +1463,62 @@ PDCS_DEV void grid_totals(GridPart p, int K, int KS, unsigned f32mask, double* o
   __syncthreads();
 }
 
-// After the pass-0 barrier: the FP64 totals (warps < K64, as grid_totals)
-// and, at the same time, the FP32 totals of the S probe slots (the remaining
-// threads, (blockDim.x - 32 K64) / S per slot, each a strided run of CTAs,
-// then a fixed-order sum), so that all loads are in flight together.
-// scratch holds blockDim.x floats.
-PDCS_DEV void grid_totals_pass0(GridPart p, int K64, int KS, int S, float* scratch, double* out,
-                                float* outp) {
-  const int G = gridDim.x, t = threadIdx.x;
-  const int t0 = 32 * K64, tps = S > 0 ? (blockDim.x - t0) / S : 0;
-  if (t >= t0 && S > 0) {
-    const int u = t - t0, sl = u / tps, sub = u - sl * tps;
-    float acc = 0.0f;
+// After the pass-0 barrier: the FP32 totals of the S probe slots, warp w
+// taking slots w, w + nwarps, ... (at most kSgSlotsPerWarp; lane l adds CTAs
+// l, l + 32, ... and a fixed butterfly follows, as grid_totals), with the
+// loads of all its slots issued before the first add, so that one L2 round
+// trip serves them; then the FP64 totals (warps < K64, grid_totals).
+constexpr int kSgSlotsPerWarp = 3;
+static_assert(kSgSlotsPerWarp * (512 / 32) >= kSgF32Slots, "probe slots per warp");
+PDCS_DEV void grid_totals_pass0(GridPart p, int K64, int KS, int S, double* out, float* outp) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const unsigned G = gridDim.x;
+  float acc[kSgSlotsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kSgSlotsPerWarp; ++r) {
+    const int sl = w + r * nw;
+    float a = 0.0f;
     if (sl < S) {
       const float* src = p.f + (size_t)sl * G;
-#pragma unroll 16
-      for (int b = sub; b < G; b += tps) acc += __ldcg(src + b);
+#pragma unroll
+      for (int j = 0; j < kMaxGridParts / 32; ++j) {
+        const unsigned bb = lane + 32u * j;
+        if (bb < G) a += __ldcg(src + bb);
+      }
     }
-    scratch[u] = acc;
+    acc[r] = a;
+  }
+#pragma unroll
+  for (int r = 0; r < kSgSlotsPerWarp; ++r) {
+    const int sl = w + r * nw;
+    const float sm = warp_sum_f(acc[r]);
+    if (lane == 0 && sl < S) outp[sl] = sm;
   }
   grid_totals(p, K64, KS, 0u, out, nullptr);  // ends with __syncthreads
-  if (t < S) {
-    float a = 0.0f;
-    for (int k = 0; k < tps; ++k) a += scratch[t * tps + k];
-    outp[t] = a;
+}
+
+// One element's terms of the FP64 phase (the sums soc_secular_terms forms,
+// for a = vv^2 b): f0 and f1 in FP64; f2 in FP32, since it only enters the
+// second-order term of a Halley step, multiplied by F, which vanishes at the
+// root (an FP32 f2 changes a step of size d by ~1e-7 |F F''| / F'^2 of d).
+// vv is the normalised tail element and b its squared scale.  a r^2 is
+// formed as (vv r)^2 b, and the FP32 copies come from the integer pipes:
+// 10 FP64 operations per element instead of 14 (the phase is bound by them).
+PDCS_DEV void soc_terms_f64(bool pos, double vv, double b, double x, double& f0, double& f1,
+                            float& f2) {
+  const double r = pos ? rcp_nr(fma(2.0, x, b)) : rcp_nr(fma(b, x, 1.0));
+  const double tv = vv * r;
+  const double ar2 = tv * tv * b;
+  f0 += ar2;
+  const float rf = f32_trunc(r), af = f32_trunc(ar2);
+  if (pos) {
+    f1 = fma(ar2, r, f1);
+    f2 = fmaf(af * rf, rf, f2);
+  } else {
+    const float bf = f32_trunc(b);
+    f1 = fma(ar2 * b, r, f1);
+    f2 = fmaf(af * bf * bf * rf, rf, f2);
   }
-  __syncthreads();
 }
 
 // Per-vector scalar state of the grid-wide SOC root-finding.  Warp 0 of every
@@ -1515,7 +1545,7 @@ enum : int {
 // of that distance: Halley's cubic convergence leaves an error of order
 // (1e-4)^3 of the distance after such a step, far below what the FP64 sums
 // resolve.
-constexpr double kSgF32Tol = 1e-5;
+constexpr double kSgF32Tol = 1e-2;
 constexpr int kSgF32Max = 40;
 constexpr double kSgF64Tol = 1e-4;
 constexpr int kSgF64Max = 200;
@@ -1569,7 +1599,6 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
   __shared__ float redf[32 * K];
   __shared__ float pa[RC * 512], pb[RC * 512];
   __shared__ float pred[16 * PS];
-  __shared__ float scratch[512];
   __shared__ float ptot[NV * PS];
   __shared__ double tot[8];
   __shared__ float totf[8];
@@ -1714,12 +1743,15 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
       }
       cta_rows_f64<K>(r0, 2 * NV, (1u << K) - 1u, red, gp0);
       grid_sync(gs);
-      grid_totals_pass0(gp0, K, 2 * NV, probes_ok ? NV * PS : 0, scratch, tot, ptot);
+      grid_totals_pass0(gp0, K, 2 * NV, probes_ok ? NV * PS : 0, tot, ptot);
       flip ^= 1;
     }
-    if (w == 0) {
+    // one warp per vector, so that the vectors' scalar work runs on separate
+    // schedulers (the same code one warp would run for each in turn)
+    if (w < NV) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
+        if (q != w) continue;  // warp-uniform
         SocGridVec& g = sv[q];
         // e0^2 is the head's precomputed squared scale (exactly e0 * e0)
         const double e02 = (FLIP1 && q == 1) ? b0i : b0;
@@ -1873,6 +1905,11 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
         } else if (mode[q] == SG_F32) {
           work = true;
           m32 |= 7u << (3 * q);
+        } else if (mode[q] == SG_F64) {
+          // f0, f1 in FP64; f2 (see soc_terms_f64) in FP32
+          work = true;
+          m64 |= 3u << (3 * q);
+          m32 |= 4u << (3 * q);
         } else if (mode[q] != SG_DONE) {
           work = true;
           m64 |= 7u << (3 * q);
@@ -1908,20 +1945,18 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
             fv[3 * q + 2] += pos ? ar2 * r * r : ar2 * bf * bf * r * r;
           }
         } else if (mode[q] == SG_F64) {
-          double f[3] = {0.0, 0.0, 0.0};
+          double f0 = 0.0, f1 = 0.0;
+          float f2 = 0.0f;
 #pragma unroll
           for (int k = 0; k < RC; ++k) {
             if (cbeg + t + k * nt >= cend) continue;
-            const double vv = vc[q][k] * g.sc, b = SG_BD(q, k);
-            soc_secular_terms(pos, vv * vv * b, b, g.x, f);
+            soc_terms_f64(pos, vc[q][k] * g.sc, SG_BD(q, k), g.x, f0, f1, f2);
           }
-          for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt) {
-            const double b = SG_BM(q, i), vv = (double)vp[q][s + i] * g.sc;
-            soc_secular_terms(pos, vv * vv * b, b, g.x, f);
-          }
-          dv[3 * q] = f[0];
-          dv[3 * q + 1] = f[1];
-          dv[3 * q + 2] = f[2];
+          for (int64_t i = cbeg + t + RC * nt; i < cend; i += nt)
+            soc_terms_f64(pos, (double)vp[q][s + i] * g.sc, SG_BM(q, i), g.x, f0, f1, f2);
+          dv[3 * q] = f0;
+          dv[3 * q + 1] = f1;
+          fv[3 * q + 2] = f2;
         } else if (mode[q] == SG_ZERO_HEAD) {
           // |new tail / e|^2 with new v_i = v_i b_i / (b_i + e0^2)
           double wv = 0.0;
@@ -1944,9 +1979,11 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
       grid_sync(gs);
       grid_totals(gp, K, K, m32, tot, totf);
       flip ^= 1;
-      if (t == 0) {
+      // lane 0 of warp q takes vector q's step (separate schedulers)
+      if (lane == 0 && w < NV) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
+          if (q != w) continue;
           SocGridVec& g = sv[q];
           if (g.mode >= SG_WRITE_ZERO) { g.mode = SG_DONE; continue; }
           if (g.mode == SG_ZERO_HEAD) {
@@ -1984,7 +2021,9 @@ __global__ void __launch_bounds__(512, 2) k_cone_soc_grid(
             continue;
           }
           if (g.mode != SG_F64) continue;
-          const double f[3] = {tot[3 * q], tot[3 * q + 1], tot[3 * q + 2]};
+          // an FP32 f2 out of range (extreme scales) drops the curvature term
+          const double f2 = (double)totf[3 * q + 2];
+          const double f[3] = {tot[3 * q], tot[3 * q + 1], fabs(f2) < INFINITY ? f2 : 0.0};
           const double dist = fmin(g.x, g.top - g.x);
           const double step = soc_halley_step(pos, f, g.c0, g.e02, g.x, g.lo, g.hi);
           bool small = step == 0.0;
