@@ -324,9 +324,9 @@ PDCS_DEV void b_attempt(const BatchArgs<T>& a, const BInst& I, Ctl& sc, double* 
   const PointRef<double> ph{a.xh, a.yh, a.gxh, a.gtyh};
   b_point_stats<T, false>(a, I, sc, 0, ph, nullptr, nullptr, 0, sh);
   const double kk = (double)sc.k, beta = sc.beta, eta = sc.eta_acc;
-  const double ca = (kk + 1.0) / (kk + 2.0), cb = 1.0 / (kk + 2.0);
-  PDCS_BLOCK_LOOP(j, c0, c1) halpern_elem(ca, cb, beta, eta, a.x, a.gty, a.xh, a.gtyh, a.x0, a.gty0, a.xs, j);
-  PDCS_BLOCK_LOOP(i, r0, r1) halpern_elem(ca, cb, beta, eta, a.y, a.gx, a.yh, a.gxh, a.y0, a.gx0, a.ys, i);
+  const HalpernCoefs hc = halpern_coefs(kk, beta);
+  PDCS_BLOCK_LOOP(j, c0, c1) halpern_elem(hc, eta, a.x, a.gty, a.xh, a.gtyh, a.x0, a.gty0, a.xs, j);
+  PDCS_BLOCK_LOOP(i, r0, r1) halpern_elem(hc, eta, a.y, a.gx, a.yh, a.gxh, a.y0, a.gx0, a.ys, i);
   __syncthreads();
   if (threadIdx.x == 0) ctl_halpern_finalize(sc, eta, beta, nullptr);
   __syncthreads();
