@@ -51,6 +51,7 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 _NNZ_SCALE = 40_600_072 / 20_250_124
 NCU_TRAFFIC = {
     ("portfolio", "fp64", "ecbed7b9c912708a"): (170.266e6 * _NNZ_SCALE, 197.234e6 * _NNZ_SCALE),
+    ("portfolio", "fp32", "ecbed7b9c912708a"): (88.481e6 * _NNZ_SCALE, 100.594e6 * _NNZ_SCALE),
 }
 
 
