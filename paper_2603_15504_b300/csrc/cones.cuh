@@ -436,8 +436,20 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
     }
   }
   block_sum<2>(s, red);
-  if (sqrt(s[0]) <= v0 / e0) return;  // inside
-  if (sqrt(s[1]) <= -e0 * v0) {       // polar
+  // Scalar set-up by thread 0, broadcast through sh: FP64 square roots and
+  // divisions are long chains on this part, and every warp running them
+  // would queue them on its scheduler's FP64 pipe (same values either way).
+  if (tid == 0) {
+    double mode = 0.0;
+    if (sqrt(s[0]) <= v0 / e0) mode = 1.0;         // inside
+    else if (sqrt(s[1]) <= -e0 * v0) mode = 2.0;   // polar
+    sh[2] = mode;
+  }
+  __syncthreads();
+  const double mode = sh[2];
+  __syncthreads();
+  if (mode == 1.0) return;  // inside
+  if (mode == 2.0) {        // polar
 #pragma unroll
     for (int k = 0; k < EPT; ++k) v[k] = 0.0;
     return;
@@ -467,12 +479,19 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
     if (i >= 1 && i < dim) mx[0] = fmax(mx[0], fabs(v[k]));
   }
   block_max<1>(mx, red);
-  const double sc = mx[0] > 0.0 ? 1.0 / mx[0] : 1.0;
-  const double c0 = (v0 * sc) * (v0 * sc) * e02;
   const bool pos = v0 > 0.0;
-  double lo = 0.0, hi = pos ? 0.5 * e02 : 1.0 / e02;
+  if (tid == 0) {
+    sh[2] = mx[0] > 0.0 ? 1.0 / mx[0] : 1.0;
+    sh[3] = pos ? 0.5 * e02 : 1.0 / e02;
+    sh[4] = soc_initial_guess(s[0], s[1], v0, e0);
+  }
+  __syncthreads();
+  const double sc = sh[2];
+  const double c0 = (v0 * sc) * (v0 * sc) * e02;
+  double lo = 0.0, hi = sh[3];
   const double top = hi;
-  double x = soc_initial_guess(s[0], s[1], v0, e0);
+  double x = sh[4];
+  __syncthreads();
   // Halley steps until one is below kSocStepTol of x's distance to the ends
   // of (0, top): cubic convergence leaves an error of order kSocStepTol^3 of
   // that distance after it, below what the FP64 sums resolve
@@ -486,14 +505,29 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
         soc_secular_terms(pos, a, b, x, f);
       }
     }
-    // block sums of the three terms and the scalar step with two barriers:
-    // warp 0 adds the staged values, thread 0 steps and publishes x, the
-    // bracket and the stop flag (the next iteration's staging happens after
-    // every thread has read them)
+    // block sums of the three terms and the scalar step: the staged values
+    // of term k are added by warp k (warp 0 alone in a one-warp CTA; the
+    // same order either way), thread 0 steps and publishes x, the bracket
+    // and the stop flag (the next iteration's staging happens after every
+    // thread has read them)
 #pragma unroll
     for (int k = 0; k < 3; ++k) red[k * NT + tid] = f[k];
     __syncthreads();
-    if (tid < 32) {
+    if (NT >= 96) {
+      const int w = tid >> 5, lane = tid & 31;
+      if (w < 3) {
+        double a = 0.0;
+        for (int t = lane; t < NT; t += 32) a += red[w * NT + t];
+        a = warp_sum(a);
+        if (lane == 0) red[3 * NT + w] = a;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        f[0] = red[3 * NT];
+        f[1] = red[3 * NT + 1];
+        f[2] = red[3 * NT + 2];
+      }
+    } else if (tid < 32) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         double a = 0.0;
@@ -515,12 +549,13 @@ __device__ __forceinline__ void soc_proj_cta(double (&v)[EPT], const double (&e)
         if ((inside && fabs(step) <= kSocStepTol * dist) || hi - lo <= 1e-15 * hi) stop = 1;
       }
       sh[2] = x; sh[3] = lo; sh[4] = hi; sh[5] = (double)stop;
+      sh[6] = pos ? 2.0 * x : 1.0 / x;  // 2 mu at x
     }
     __syncthreads();
     x = sh[2]; lo = sh[3]; hi = sh[4];
     if (sh[5] != 0.0) break;
   }
-  const double mu2 = pos ? 2.0 * x : 1.0 / x;  // 2 mu
+  const double mu2 = sh[6];  // 2 mu
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const int i = tid + k * NT;
