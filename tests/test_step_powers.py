@@ -31,7 +31,7 @@ def test_newton_refined_powers_are_within_a_few_ulps():
             p3, p6 = _refine(kb1, np.float64(seed32) * (1.0 + rel))
             worst3 = max(worst3, abs(p3 - exact3) / exact3)
             worst6 = max(worst6, abs(p6 - exact6) / exact6)
-    assert worst3 <= 6e-16, worst3  # three units in the last place (2^-53 = 1.1e-16)
+    assert worst3 <= 6e-16, worst3  # a few units of 2^-53 (1.1e-16)
     assert worst6 <= 1.2e-15, worst6
 
 
