@@ -590,9 +590,9 @@ def run_ab(args):
     contract line): time and iterations to 1e-6 relative KKT error."""
     import paper_2603_15504_b300 as P
     prob, desc = _workload(args, 0)
-    arms = [("check_freq=64 (default)", dict(check_freq=64)),
-            ("check_freq=2000 (paper default)", dict(check_freq=2000)),
-            ("check_freq=64, bisect_rel_tol=1e-3", dict(check_freq=64, bisect_rel_tol=1e-3))]
+    arms = [("check_freq=64, bisect_rel_tol=1e-3 (defaults)", dict(check_freq=64)),
+            ("check_freq=2000 (the paper's restart frequency)", dict(check_freq=2000)),
+            ("check_freq=64, bisect_rel_tol=1e-6", dict(check_freq=64, bisect_rel_tol=1e-6))]
     out = []
     for name, o in arms:
         opts = dict(precision=args.precision, profile=0, time_limit=3600.0, **o)
